@@ -1,0 +1,656 @@
+/*
+ * epr_oracle.c -- FP64 CPU oracle for fast eikonal phase retrieval (EPR),
+ * arXiv 2601.22793 ("Fast Eikonal Phase Retrieval for High-Throughput
+ * Beamlines", Mirone et al.).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * definition that the CUDA library is checked against.  Only the test suite,
+ * the package smoke check and the CPU-baseline leg of the benchmark may load
+ * it.  It shares no source, header, table or helper with the CUDA path.
+ *
+ * Everything is double precision, single threaded, with plain loops in the
+ * order the paper states the steps.  Arrays are row-major [ny][nx] with y the
+ * row index, as in the paper's P_s(y, x).
+ *
+ * Readings of points the paper leaves open (each one is listed in the design
+ * notes of the repository, with the reason):
+ *   R1  discrete gradient of the thickness: central differences in the
+ *       interior, first-order one-sided at the edges (numpy.gradient with
+ *       unit spacing), in thickness units per pixel.
+ *   R2  phase of line s: phi_s = -k_s delta_s tau (Eq. 6 with Eq. 7), so the
+ *       shift is Delta_s = -L delta_s grad(tau) and, in pixels,
+ *       u_s = -(L delta_s / p^2) * G[tau]   (Eq. 2 in pixel units).
+ *   R3  splat targets outside the detector grid are dropped (counted in
+ *       `dropped`); the adjoint reads zero outside the grid.
+ *   R4  the preconditioner is periodic, without padding, with the continuous
+ *       symbol H_s(q) = mu_s / (mu_s + L delta_s |q|^2), |q|^2 =
+ *       4 pi^2 (fx^2 + fy^2), fx = numpy.fft.fftfreq(nx, p).
+ *   R5  residual split: r_s = r * P_s / P where P > 1e-30, else r * f_s.
+ *   R6  projection to one thickness: least squares in the log domain with
+ *       weights f_s: tau' = -sum f_s mu_s ln(I'_s/f_s) / sum f_s mu_s^2.
+ *   R7  update: I'_s = max(I_s + omega * h_s, eps_I * f_s).
+ *   R8  stop when kappa = |tau' - tau| / |tau'| <= tol, or after n_iter.
+ *   R9  mu_s = 2 k_s beta_s, k_s = 2 pi / lambda_s, lambda_s = hc / E_s.
+ *   R10 local stencils: D_i central (one-sided at edges), D_ii the compact
+ *       [1, -2, 1] with replicated edges, D_ij = D_i D_j for i != j.
+ *
+ * Parity unpinned: the residual split of R5.  The paper only says the
+ * weights are "positivity-weighted"; P_s / P and f_s agree at the flat-field
+ * start and at every fixed point, so no fact the paper fixes tells them
+ * apart.  Every other step is pinned by the CPU tests.
+ */
+#include <complex.h>
+#undef I /* the object intensity is called I below; the imaginary unit is _Complex_I */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_HC_EV_M 1.2398419843320026e-6 /* h c in eV m */
+#define ORC_PI 3.14159265358979323846
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 3 };
+enum { ORC_MODEL_NONLOCAL = 0, ORC_MODEL_LOCAL1 = 1, ORC_MODEL_LOCAL2 = 2 };
+
+#define IDX(y, x) ((size_t)(y) * (size_t)nx + (size_t)(x))
+
+/* ------------------------------------------------------------------------ */
+/* Per-line physical constants.                                             */
+/* ------------------------------------------------------------------------ */
+
+/* lambda_s = hc/E_s, k_s = 2 pi/lambda_s ("Local forward model summary":
+ * k = 2 pi / lambda), mu_s = 2 k_s beta_s (attenuation of the intensity
+ * |U|^2 for n = 1 - delta + i beta), f_s = weights normalised to sum 1
+ * (Eq. 7, I_s already carries its spectral weight), shift coefficient
+ * c_s = -L delta_s / p^2 (reading R2), eps_s = L / k_s (Eq. 2). */
+int orc_line_params(int n_lines, const double* E_keV, const double* delta,
+                    const double* beta, const double* weights, double L,
+                    double p, double* f, double* mu, double* k, double* cshift,
+                    double* eps)
+{
+    if (n_lines <= 0 || L < 0.0 || !(p > 0.0)) return ORC_EINVAL;
+    double wsum = 0.0;
+    for (int s = 0; s < n_lines; ++s) {
+        if (!(E_keV[s] > 0.0) || weights[s] < 0.0) return ORC_EINVAL;
+        wsum += weights[s];
+    }
+    if (!(wsum > 0.0)) return ORC_EINVAL;
+    for (int s = 0; s < n_lines; ++s) {
+        double lam = ORC_HC_EV_M / (E_keV[s] * 1e3);
+        k[s] = 2.0 * ORC_PI / lam;
+        mu[s] = 2.0 * k[s] * beta[s];
+        f[s] = weights[s] / wsum;
+        cshift[s] = -L * delta[s] / (p * p);
+        eps[s] = L / k[s];
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Discrete derivatives (readings R1, R10).                                 */
+/* ------------------------------------------------------------------------ */
+
+/* d/dx with unit spacing: central inside, one-sided at x = 0 and x = nx-1. */
+static void d_x(int ny, int nx, const double* a, double* out)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double v;
+            if (x == 0) v = a[IDX(y, 1)] - a[IDX(y, 0)];
+            else if (x == nx - 1) v = a[IDX(y, nx - 1)] - a[IDX(y, nx - 2)];
+            else v = 0.5 * (a[IDX(y, x + 1)] - a[IDX(y, x - 1)]);
+            out[IDX(y, x)] = v;
+        }
+}
+
+/* d/dy with unit spacing: central inside, one-sided at y = 0 and y = ny-1. */
+static void d_y(int ny, int nx, const double* a, double* out)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double v;
+            if (y == 0) v = a[IDX(1, x)] - a[IDX(0, x)];
+            else if (y == ny - 1) v = a[IDX(ny - 1, x)] - a[IDX(ny - 2, x)];
+            else v = 0.5 * (a[IDX(y + 1, x)] - a[IDX(y - 1, x)]);
+            out[IDX(y, x)] = v;
+        }
+}
+
+/* d2/dx2: [1, -2, 1] with the edge value replicated outside the grid. */
+static void d_xx(int ny, int nx, const double* a, double* out)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double l = a[IDX(y, x > 0 ? x - 1 : 0)];
+            double r = a[IDX(y, x < nx - 1 ? x + 1 : nx - 1)];
+            out[IDX(y, x)] = l - 2.0 * a[IDX(y, x)] + r;
+        }
+}
+
+/* d2/dy2: [1, -2, 1] with the edge value replicated outside the grid. */
+static void d_yy(int ny, int nx, const double* a, double* out)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double b = a[IDX(y > 0 ? y - 1 : 0, x)];
+            double t = a[IDX(y < ny - 1 ? y + 1 : ny - 1, x)];
+            out[IDX(y, x)] = b - 2.0 * a[IDX(y, x)] + t;
+        }
+}
+
+/* G[tau] = (d tau/dy, d tau/dx) per pixel (reading R1). */
+void orc_gradient(int ny, int nx, const double* T, double* gy, double* gx)
+{
+    d_y(ny, nx, T, gy);
+    d_x(ny, nx, T, gx);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Non-local transport: bilinear redistribution and its adjoint.            */
+/* ------------------------------------------------------------------------ */
+
+/* Forward WKB0 transport of one line (Eq. 3), discretised as the paper's
+ * conservative bilinear redistribution ("Discrete implementation" in the
+ * non-local Methods subsection): source pixel (y, x) with mass I(y, x) goes
+ * to (x_t, y_t) = (x + u_x, y + u_y); with x0 = floor(x_t), y0 = floor(y_t),
+ * d_x = x_t - x0, d_y = y_t - y0 the weights are
+ *   w00 = (1-d_x)(1-d_y) -> (y0,   x0)     w10 = d_x(1-d_y) -> (y0,   x0+1)
+ *   w01 = (1-d_x) d_y    -> (y0+1, x0)     w11 = d_x d_y    -> (y0+1, x0+1).
+ * P is ACCUMULATED (+=).  Mass whose corner lies outside the grid is added to
+ * *dropped (reading R3), so sum(P) + dropped = sum(I). */
+void orc_splat(int ny, int nx, const double* I, const double* uy,
+               const double* ux, double* P, double* dropped)
+{
+    double lost = 0.0;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double m = I[IDX(y, x)];
+            double xt = (double)x + ux[IDX(y, x)];
+            double yt = (double)y + uy[IDX(y, x)];
+            double fx0 = floor(xt), fy0 = floor(yt);
+            double dx = xt - fx0, dy = yt - fy0;
+            double w[4] = {(1.0 - dx) * (1.0 - dy), dx * (1.0 - dy),
+                           (1.0 - dx) * dy, dx * dy};
+            int ox[4] = {0, 1, 0, 1}, oy[4] = {0, 0, 1, 1};
+            for (int c = 0; c < 4; ++c) {
+                double cx = fx0 + ox[c], cy = fy0 + oy[c];
+                if (cx >= 0.0 && cx < (double)nx && cy >= 0.0 && cy < (double)ny)
+                    P[IDX((int)cy, (int)cx)] += m * w[c];
+                else
+                    lost += m * w[c];
+            }
+        }
+    if (dropped) *dropped += lost;
+}
+
+/* Exact adjoint of orc_splat (Eq. 4): for every object pixel, the bilinear
+ * combination of the detector values e at the same four corners with the
+ * same four weights; corners outside the grid contribute 0 (reading R3). */
+void orc_gather(int ny, int nx, const double* e, const double* uy,
+                const double* ux, double* g)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double xt = (double)x + ux[IDX(y, x)];
+            double yt = (double)y + uy[IDX(y, x)];
+            double fx0 = floor(xt), fy0 = floor(yt);
+            double dx = xt - fx0, dy = yt - fy0;
+            double w[4] = {(1.0 - dx) * (1.0 - dy), dx * (1.0 - dy),
+                           (1.0 - dx) * dy, dx * dy};
+            int ox[4] = {0, 1, 0, 1}, oy[4] = {0, 0, 1, 1};
+            double acc = 0.0;
+            for (int c = 0; c < 4; ++c) {
+                double cx = fx0 + ox[c], cy = fy0 + oy[c];
+                if (cx >= 0.0 && cx < (double)nx && cy >= 0.0 && cy < (double)ny)
+                    acc += w[c] * e[IDX((int)cy, (int)cx)];
+            }
+            g[IDX(y, x)] = acc;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Discrete Fourier transforms.                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Textbook O(n^2) DFT: X[k] = sum_j x[j] exp(sign 2 pi i j k / n). */
+void orc_dft_naive(int n, const double* re, const double* im, double* ore,
+                   double* oim, int sign)
+{
+    for (int k = 0; k < n; ++k) {
+        double sr = 0.0, si = 0.0;
+        for (int j = 0; j < n; ++j) {
+            double a = sign * 2.0 * ORC_PI * (double)(((long long)j * k) % n) / n;
+            double c = cos(a), s = sin(a);
+            sr += re[j] * c - im[j] * s;
+            si += re[j] * s + im[j] * c;
+        }
+        ore[k] = sr;
+        oim[k] = si;
+    }
+}
+
+/* Recursive decimation-in-time FFT for any n: split off the smallest prime
+ * factor r of n (r = n when n is prime, which makes that level a plain DFT),
+ * transform the r decimated subsequences x[q + r j] of length m = n / r, and
+ * combine  X[k] = sum_q W^(q k) Y_q[k mod m],  W = exp(sign 2 pi i / n).
+ * `w` holds exp(sign 2 pi i t / N) for the top-level length N, and
+ * `wstride` = N / n maps this level's twiddles into it. */
+static void fft_rec(int n, const double complex* in, int stride,
+                    double complex* out, double complex* tmp,
+                    const double complex* w, int wstride)
+{
+    if (n == 1) {
+        out[0] = in[0];
+        return;
+    }
+    int r = n;
+    for (int d = 2; d * d <= n; ++d)
+        if (n % d == 0) {
+            r = d;
+            break;
+        }
+    int m = n / r;
+    for (int q = 0; q < r; ++q)
+        fft_rec(m, in + (size_t)q * stride, stride * r, tmp + (size_t)q * m,
+                out + (size_t)q * m, w, wstride * r);
+    for (int k = 0; k < n; ++k) {
+        double complex acc = 0.0;
+        for (int q = 0; q < r; ++q) {
+            long long t = ((long long)q * k) % n;
+            acc += w[t * wstride] * tmp[(size_t)q * m + (k % m)];
+        }
+        out[k] = acc;
+    }
+    /* tmp is scratch for this level only; the caller's copy is in out. */
+}
+
+/* In-place unnormalised 1-D FFT, sign -1 forward (numpy.fft.fft), +1 inverse
+ * without the 1/n factor. */
+int orc_fft(int n, double* re, double* im, int sign)
+{
+    if (n <= 0) return ORC_EINVAL;
+    double complex* a = malloc(sizeof(double complex) * (size_t)n);
+    double complex* b = malloc(sizeof(double complex) * (size_t)n);
+    double complex* c = malloc(sizeof(double complex) * (size_t)n);
+    double complex* w = malloc(sizeof(double complex) * (size_t)n);
+    if (!a || !b || !c || !w) {
+        free(a); free(b); free(c); free(w);
+        return ORC_ENOMEM;
+    }
+    for (int t = 0; t < n; ++t) {
+        double ang = sign * 2.0 * ORC_PI * (double)t / n;
+        w[t] = cos(ang) + _Complex_I * sin(ang);
+        a[t] = re[t] + _Complex_I * im[t];
+    }
+    fft_rec(n, a, 1, b, c, w, 1);
+    for (int t = 0; t < n; ++t) {
+        re[t] = creal(b[t]);
+        im[t] = cimag(b[t]);
+    }
+    free(a); free(b); free(c); free(w);
+    return ORC_OK;
+}
+
+/* 2-D transform: all rows, then all columns (separable DFT). */
+int orc_fft2(int ny, int nx, double* re, double* im, int sign)
+{
+    int nmax = nx > ny ? nx : ny;
+    double* lr = malloc(sizeof(double) * (size_t)nmax);
+    double* li = malloc(sizeof(double) * (size_t)nmax);
+    if (!lr || !li) {
+        free(lr); free(li);
+        return ORC_ENOMEM;
+    }
+    int st = ORC_OK;
+    for (int y = 0; y < ny && st == ORC_OK; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            lr[x] = re[IDX(y, x)];
+            li[x] = im[IDX(y, x)];
+        }
+        st = orc_fft(nx, lr, li, sign);
+        for (int x = 0; x < nx; ++x) {
+            re[IDX(y, x)] = lr[x];
+            im[IDX(y, x)] = li[x];
+        }
+    }
+    for (int x = 0; x < nx && st == ORC_OK; ++x) {
+        for (int y = 0; y < ny; ++y) {
+            lr[y] = re[IDX(y, x)];
+            li[y] = im[IDX(y, x)];
+        }
+        st = orc_fft(ny, lr, li, sign);
+        for (int y = 0; y < ny; ++y) {
+            re[IDX(y, x)] = lr[y];
+            im[IDX(y, x)] = li[y];
+        }
+    }
+    free(lr); free(li);
+    return st;
+}
+
+/* numpy.fft.fftfreq(n, d)[k]: k / (n d) for k < (n + 1) / 2, else (k - n) / (n d). */
+static double fftfreq(int n, double d, int k)
+{
+    int kk = (k < (n + 1) / 2) ? k : k - n;
+    return (double)kk / ((double)n * d);
+}
+
+/* FFT-diagonal Paganin-type preconditioner P_{1,s}^{-1} ("Linear term and
+ * relation to Paganin"; "Iteration structure"): g <- Re F^-1[ H F[g] ] with
+ * H(q) = mu / (mu + L delta |q|^2) (reading R4), in place. */
+int orc_paganin(int ny, int nx, double p, double mu, double Ldelta, double* g)
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    double* im = calloc(n, sizeof(double));
+    if (!im) return ORC_ENOMEM;
+    int st = orc_fft2(ny, nx, g, im, -1);
+    if (st == ORC_OK) {
+        for (int y = 0; y < ny; ++y) {
+            double fy = fftfreq(ny, p, y);
+            for (int x = 0; x < nx; ++x) {
+                double fx = fftfreq(nx, p, x);
+                double q2 = 4.0 * ORC_PI * ORC_PI * (fx * fx + fy * fy);
+                double H = mu / (mu + Ldelta * q2);
+                g[IDX(y, x)] *= H;
+                im[IDX(y, x)] *= H;
+            }
+        }
+        st = orc_fft2(ny, nx, g, im, +1);
+        for (size_t i = 0; i < n; ++i) g[i] /= (double)n;
+    }
+    free(im);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward models.                                                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int n_lines;
+    double p, L;
+    double *f, *mu, *k, *c, *eps, *delta;
+} orc_lines;
+
+static int lines_init(orc_lines* ln, int n_lines, const double* E_keV,
+                      const double* delta, const double* beta,
+                      const double* weights, double L, double p)
+{
+    memset(ln, 0, sizeof(*ln));
+    ln->n_lines = n_lines;
+    ln->p = p;
+    ln->L = L;
+    size_t b = sizeof(double) * (size_t)(n_lines > 0 ? n_lines : 1);
+    ln->f = malloc(b); ln->mu = malloc(b); ln->k = malloc(b);
+    ln->c = malloc(b); ln->eps = malloc(b); ln->delta = malloc(b);
+    if (!ln->f || !ln->mu || !ln->k || !ln->c || !ln->eps || !ln->delta)
+        return ORC_ENOMEM;
+    for (int s = 0; s < n_lines; ++s) ln->delta[s] = delta[s];
+    return orc_line_params(n_lines, E_keV, delta, beta, weights, L, p, ln->f,
+                           ln->mu, ln->k, ln->c, ln->eps);
+}
+
+static void lines_free(orc_lines* ln)
+{
+    free(ln->f); free(ln->mu); free(ln->k);
+    free(ln->c); free(ln->eps); free(ln->delta);
+}
+
+/* Local O(L^2) closure of one line (Eq. 1 in pixel units, reading R10):
+ *   P = I - D_i(I u_i)                                             (m = 1)
+ *       + 1/2 D_i D_j (I u_i u_j) - eps^2/(4 p^4) D_i(I D_i Q)    (m = 2)
+ * with Q = (D_xx + D_yy) sqrt(I) / sqrt(I) (Q of Eq. 1 in pixel units).
+ * The physical derivative is D/p and eps grad(phi) = p u, which turns the
+ * eps and eps^2/2 terms of Eq. 1 into the pixel forms above and leaves
+ * eps^2 / (4 p^4) in front of the diffraction-pressure term. */
+static int local_line(int ny, int nx, int order, const double* I,
+                      const double* uy, const double* ux, double eps, double p,
+                      double* P)
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    double* a = malloc(sizeof(double) * n);
+    double* b = malloc(sizeof(double) * n);
+    double* t = malloc(sizeof(double) * n);
+    double* q = malloc(sizeof(double) * n);
+    if (!a || !b || !t || !q) {
+        free(a); free(b); free(t); free(q);
+        return ORC_ENOMEM;
+    }
+    for (size_t i = 0; i < n; ++i) P[i] = I[i];
+    /* - D_x(I u_x) - D_y(I u_y) */
+    for (size_t i = 0; i < n; ++i) a[i] = I[i] * ux[i];
+    d_x(ny, nx, a, b);
+    for (size_t i = 0; i < n; ++i) P[i] -= b[i];
+    for (size_t i = 0; i < n; ++i) a[i] = I[i] * uy[i];
+    d_y(ny, nx, a, b);
+    for (size_t i = 0; i < n; ++i) P[i] -= b[i];
+    if (order >= 2) {
+        /* + 1/2 [ D_xx(I ux^2) + 2 D_x D_y(I ux uy) + D_yy(I uy^2) ] */
+        for (size_t i = 0; i < n; ++i) a[i] = I[i] * ux[i] * ux[i];
+        d_xx(ny, nx, a, b);
+        for (size_t i = 0; i < n; ++i) P[i] += 0.5 * b[i];
+        for (size_t i = 0; i < n; ++i) a[i] = I[i] * uy[i] * uy[i];
+        d_yy(ny, nx, a, b);
+        for (size_t i = 0; i < n; ++i) P[i] += 0.5 * b[i];
+        for (size_t i = 0; i < n; ++i) a[i] = I[i] * ux[i] * uy[i];
+        d_y(ny, nx, a, t);
+        d_x(ny, nx, t, b);
+        for (size_t i = 0; i < n; ++i) P[i] += b[i];
+        /* - eps^2/(4 p^4) [ D_x(I D_x Q) + D_y(I D_y Q) ] */
+        for (size_t i = 0; i < n; ++i) a[i] = sqrt(I[i]);
+        d_xx(ny, nx, a, b);
+        d_yy(ny, nx, a, t);
+        for (size_t i = 0; i < n; ++i) q[i] = (a[i] > 0.0) ? (b[i] + t[i]) / a[i] : 0.0;
+        double coef = eps * eps / (4.0 * p * p * p * p);
+        d_x(ny, nx, q, a);
+        for (size_t i = 0; i < n; ++i) a[i] *= I[i];
+        d_x(ny, nx, a, b);
+        for (size_t i = 0; i < n; ++i) P[i] -= coef * b[i];
+        d_y(ny, nx, q, a);
+        for (size_t i = 0; i < n; ++i) a[i] *= I[i];
+        d_y(ny, nx, a, b);
+        for (size_t i = 0; i < n; ++i) P[i] -= coef * b[i];
+    }
+    free(a); free(b); free(t); free(q);
+    return ORC_OK;
+}
+
+/* Polychromatic forward (Eq. 5): P = sum_s F_s[I_s] with I_s = f_s exp(-mu_s
+ * tau) (Eq. 7) and u_s = c_s G[tau] (reading R2).  F_s is the bilinear
+ * redistribution for model 0 and the local closure of order m for models 1, 2.
+ * Ps (n_lines maps, may be NULL) and dropped (n_lines values, may be NULL)
+ * receive the per-line predictions and the per-line mass that left the grid. */
+static int forward_impl(int ny, int nx, const orc_lines* ln, int model,
+                        const double* T, double* P, double* Ps, double* dropped,
+                        double* gy, double* gx, double* uy, double* ux,
+                        double* I, double* Pl)
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    orc_gradient(ny, nx, T, gy, gx);
+    for (size_t i = 0; i < n; ++i) P[i] = 0.0;
+    for (int s = 0; s < ln->n_lines; ++s) {
+        for (size_t i = 0; i < n; ++i) {
+            uy[i] = ln->c[s] * gy[i];
+            ux[i] = ln->c[s] * gx[i];
+            I[i] = ln->f[s] * exp(-ln->mu[s] * T[i]);
+            Pl[i] = 0.0;
+        }
+        double lost = 0.0;
+        if (model == ORC_MODEL_NONLOCAL) {
+            orc_splat(ny, nx, I, uy, ux, Pl, &lost);
+        } else {
+            int st = local_line(ny, nx, model, I, uy, ux, ln->eps[s], ln->p, Pl);
+            if (st != ORC_OK) return st;
+        }
+        for (size_t i = 0; i < n; ++i) P[i] += Pl[i];
+        if (Ps) memcpy(Ps + (size_t)s * n, Pl, sizeof(double) * n);
+        if (dropped) dropped[s] = lost;
+    }
+    return ORC_OK;
+}
+
+static double* alloc_n(size_t n) { return malloc(sizeof(double) * (n ? n : 1)); }
+
+int orc_forward(int ny, int nx, double p, double L, int n_lines,
+                const double* E_keV, const double* delta, const double* beta,
+                const double* weights, int model, const double* T, double* P,
+                double* Ps, double* dropped)
+{
+    if (ny < 2 || nx < 2 || model < 0 || model > 2) return ORC_EINVAL;
+    orc_lines ln;
+    int st = lines_init(&ln, n_lines, E_keV, delta, beta, weights, L, p);
+    size_t n = (size_t)nx * (size_t)ny;
+    double *gy = alloc_n(n), *gx = alloc_n(n), *uy = alloc_n(n), *ux = alloc_n(n),
+           *I = alloc_n(n), *Pl = alloc_n(n);
+    if (st == ORC_OK && (!gy || !gx || !uy || !ux || !I || !Pl)) st = ORC_ENOMEM;
+    if (st == ORC_OK)
+        st = forward_impl(ny, nx, &ln, model, T, P, Ps, dropped, gy, gx, uy, ux, I, Pl);
+    free(gy); free(gx); free(uy); free(ux); free(I); free(Pl);
+    lines_free(&ln);
+    return st;
+}
+
+/* Adjoint of the non-local forward for one line and fixed tau: the gather of
+ * the detector map e at the line's mapped coordinates (Eq. 4). */
+int orc_adjoint(int ny, int nx, double p, double L, int n_lines,
+                const double* E_keV, const double* delta, const double* beta,
+                const double* weights, int line, const double* T,
+                const double* e, double* g)
+{
+    if (ny < 2 || nx < 2 || line < 0 || line >= n_lines) return ORC_EINVAL;
+    orc_lines ln;
+    int st = lines_init(&ln, n_lines, E_keV, delta, beta, weights, L, p);
+    size_t n = (size_t)nx * (size_t)ny;
+    double *gy = alloc_n(n), *gx = alloc_n(n), *uy = alloc_n(n), *ux = alloc_n(n);
+    if (st == ORC_OK && (!gy || !gx || !uy || !ux)) st = ORC_ENOMEM;
+    if (st == ORC_OK) {
+        orc_gradient(ny, nx, T, gy, gx);
+        for (size_t i = 0; i < n; ++i) {
+            uy[i] = ln.c[line] * gy[i];
+            ux[i] = ln.c[line] * gx[i];
+        }
+        orc_gather(ny, nx, e, uy, ux, g);
+    }
+    free(gy); free(gx); free(uy); free(ux);
+    lines_free(&ln);
+    return st;
+}
+
+/* Preconditioner of one line on a real map, in place (reading R4). */
+int orc_precondition(int ny, int nx, double p, double L, int n_lines,
+                     const double* E_keV, const double* delta,
+                     const double* beta, const double* weights, int line,
+                     double* g)
+{
+    if (ny < 1 || nx < 1 || line < 0 || line >= n_lines) return ORC_EINVAL;
+    orc_lines ln;
+    int st = lines_init(&ln, n_lines, E_keV, delta, beta, weights, L, p);
+    if (st == ORC_OK) st = orc_paganin(ny, nx, p, ln.mu[line], L * ln.delta[line], g);
+    lines_free(&ln);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Iterative inversion ("Iterative inversion (local and non-local)").       */
+/* ------------------------------------------------------------------------ */
+
+/* One projection.  Per iteration n, in the order of "Iteration structure":
+ *   1. per-line predictions P_s and their sum P (forward_impl);
+ *   2. detector residual r = D - P, rho_n = |r| / |D|;
+ *   3. split across lines, r_s = r P_s / P (reading R5);
+ *   4. back-transport: g_s = M_s^* r_s (Eq. 4) for the non-local model, the
+ *      identity for the local closure;
+ *   5. preconditioner h_s = P_{1,s}^{-1} g_s (reading R4);
+ *   6. update I'_s = max(I_s + omega h_s, eps_I f_s) (reading R7) and
+ *      projection to the single-thickness form of Eq. 7 (reading R6);
+ *   7. kappa_n = |tau' - tau| / |tau'|; stop when kappa_n <= tol (R8).
+ * T holds the initial thickness on entry (zeros = start from flat field) and
+ * the result on return.  rho and kappa (n_iter values each, may be NULL)
+ * receive the history; *iters the number of iterations run. */
+int orc_solve(int ny, int nx, double p, double L, int n_lines,
+              const double* E_keV, const double* delta, const double* beta,
+              const double* weights, int model, const double* D, double* T,
+              int n_iter, double omega, double tol, double eps_I, double* rho,
+              double* kappa, int* iters)
+{
+    if (ny < 2 || nx < 2 || model < 0 || model > 2 || n_iter < 0) return ORC_EINVAL;
+    orc_lines ln;
+    int st = lines_init(&ln, n_lines, E_keV, delta, beta, weights, L, p);
+    size_t n = (size_t)nx * (size_t)ny;
+    int ns = n_lines;
+    double *gy = alloc_n(n), *gx = alloc_n(n), *uy = alloc_n(n), *ux = alloc_n(n),
+           *I = alloc_n(n), *Pl = alloc_n(n), *P = alloc_n(n), *r = alloc_n(n),
+           *rs = alloc_n(n), *g = alloc_n(n), *num = alloc_n(n),
+           *Ps = alloc_n(n * (size_t)ns);
+    if (st == ORC_OK && (!gy || !gx || !uy || !ux || !I || !Pl || !P || !r ||
+                         !rs || !g || !num || !Ps))
+        st = ORC_ENOMEM;
+    double den = 0.0;
+    if (st == ORC_OK)
+        for (int s = 0; s < ns; ++s) den += ln.f[s] * ln.mu[s] * ln.mu[s];
+    if (st == ORC_OK && !(den > 0.0)) st = ORC_EINVAL;
+    double dnorm = 0.0;
+    for (size_t i = 0; st == ORC_OK && i < n; ++i) dnorm += D[i] * D[i];
+    dnorm = sqrt(dnorm);
+    int it = 0;
+    for (; st == ORC_OK && it < n_iter; ++it) {
+        /* 1. forward */
+        st = forward_impl(ny, nx, &ln, model, T, P, Ps, NULL, gy, gx, uy, ux, I, Pl);
+        if (st != ORC_OK) break;
+        /* 2. residual */
+        double rr = 0.0;
+        for (size_t i = 0; i < n; ++i) {
+            r[i] = D[i] - P[i];
+            rr += r[i] * r[i];
+        }
+        if (rho) rho[it] = dnorm > 0.0 ? sqrt(rr) / dnorm : sqrt(rr);
+        for (size_t i = 0; i < n; ++i) num[i] = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            if (ln.f[s] == 0.0) continue; /* a line without weight carries nothing */
+            const double* P_s = Ps + (size_t)s * n;
+            /* 3. split */
+            for (size_t i = 0; i < n; ++i)
+                rs[i] = (P[i] > 1e-30) ? r[i] * P_s[i] / P[i] : r[i] * ln.f[s];
+            /* 4. back-transport (shift of this line recomputed from tau) */
+            if (model == ORC_MODEL_NONLOCAL) {
+                for (size_t i = 0; i < n; ++i) {
+                    uy[i] = ln.c[s] * gy[i];
+                    ux[i] = ln.c[s] * gx[i];
+                }
+                orc_gather(ny, nx, rs, uy, ux, g);
+            } else {
+                memcpy(g, rs, sizeof(double) * n);
+            }
+            /* 5. preconditioner */
+            st = orc_paganin(ny, nx, p, ln.mu[s], L * ln.delta[s], g);
+            if (st != ORC_OK) break;
+            /* 6. update of the line and its share of the projection */
+            for (size_t i = 0; i < n; ++i) {
+                double Is = ln.f[s] * exp(-ln.mu[s] * T[i]);
+                double In = Is + omega * g[i];
+                double fl = eps_I * ln.f[s];
+                if (In < fl) In = fl;
+                num[i] += ln.f[s] * ln.mu[s] * log(In / ln.f[s]);
+            }
+        }
+        if (st != ORC_OK) break;
+        double dd = 0.0, tt = 0.0;
+        for (size_t i = 0; i < n; ++i) {
+            double tn = -num[i] / den;
+            dd += (tn - T[i]) * (tn - T[i]);
+            tt += tn * tn;
+            T[i] = tn;
+        }
+        /* 7. convergence */
+        double kap = tt > 0.0 ? sqrt(dd / tt) : sqrt(dd);
+        if (kappa) kappa[it] = kap;
+        if (kap <= tol) {
+            ++it;
+            break;
+        }
+    }
+    if (iters) *iters = it;
+    free(gy); free(gx); free(uy); free(ux); free(I); free(Pl); free(P);
+    free(r); free(rs); free(g); free(num); free(Ps);
+    lines_free(&ln);
+    return st;
+}
