@@ -1,0 +1,165 @@
+/*
+ * epr.h -- C ABI of the GB300 fast eikonal phase retrieval library (libepr).
+ *
+ * The library implements the iterative solver of arXiv 2601.22793 ("Fast
+ * Eikonal Phase Retrieval for High-Throughput Beamlines"): per projection and
+ * per spectral line, the eikonal ray shift from the thickness map (Eq. 2 with
+ * the single-material phase of Eqs. 6-7), the mass-conserving bilinear
+ * redistribution of the object intensity onto the detector (Eq. 3 and its
+ * "Discrete implementation" paragraph), the polychromatic sum (Eq. 5), the
+ * exact adjoint by bilinear interpolation (Eq. 4), the FFT-diagonal
+ * Paganin-type preconditioner, and the single-thickness update (Eq. 7 and the
+ * "Iterative inversion" subsection).  The local O(L^2) closure (Eq. 1) is the
+ * same loop with the transport replaced by its finite-difference stencil.
+ *
+ * Conventions shared by every entry point:
+ *  - Maps are float32, row-major [ny][nx] (y = row), contiguous; a batch of B
+ *    projections is [B][ny][nx]; per-line maps are [B][n_lines][ny][nx].
+ *  - Thickness T is in metres; intensities are flat-field normalised (I_in = 1).
+ *  - Array arguments may be device pointers or host pointers (pageable or
+ *    pinned); the kind is detected with cudaPointerGetAttributes.  Host
+ *    buffers are staged through plan-owned device memory with copies on the
+ *    given stream; pinned host memory makes those copies asynchronous.
+ *    The caller owns every array; the library never frees them.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    asynchronous on it, except where an entry point says it synchronises.
+ *  - Sizes: nx and ny of the form 2^a 3^b with a >= 3, 16 <= n <= 4096.
+ *  - No exception, abort or device trap crosses the ABI.  Device-side
+ *    failures (a full overflow list, a non-finite input) are reported through
+ *    a status word read back by the solve calls.
+ *  - A plan is not thread safe: calls on one plan must not overlap in time
+ *    from several host threads.  Different plans are independent.
+ */
+#ifndef EPR_H
+#define EPR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct epr_plan_s* epr_plan_t;
+
+typedef enum {
+    EPR_OK = 0,
+    EPR_ERR_INVALID_ARG = 1,      /* a NULL pointer, bad count or option */
+    EPR_ERR_UNSUPPORTED_SIZE = 2, /* nx or ny not 2^a 3^b in [16, 4096]  */
+    EPR_ERR_OOM = 3,              /* device allocation failed           */
+    EPR_ERR_CUDA = 4,             /* a CUDA runtime or launch error     */
+    EPR_ERR_NONFINITE = 5,        /* NaN or Inf in an input map         */
+    EPR_ERR_TIMEOUT = 6,          /* reserved: a bounded device wait ran out */
+    EPR_ERR_NOT_CONVERGED = 7,    /* reserved                           */
+    EPR_ERR_SHIFT_OVERFLOW = 8    /* more large-shift sources than the overflow list holds */
+} epr_status;
+
+/* Forward models (Eq. 5: F_s is M_s for the non-local model, P_{m,s} for the
+ * local closure of order m). */
+typedef enum {
+    EPR_MODEL_NONLOCAL = 0,
+    EPR_MODEL_LOCAL1 = 1,
+    EPR_MODEL_LOCAL2 = 2
+} epr_model;
+
+/* Plan options (NULL = defaults). */
+typedef struct {
+    int max_shift_px;      /* fast-path reach of the splat, in pixels (default 12,
+                              range 1..32).  Sources whose shift exceeds it in
+                              either axis are not lost: they go through an
+                              overflow list and are added with global atomics. */
+    int deterministic;     /* 1 = accumulate the splat in int64 fixed point
+                              (value * 2^40, round to nearest even): results are
+                              bit-identical across runs.  0 = float32 shared
+                              memory atomics (default). */
+    int overflow_capacity; /* overflow entries per projection (default
+                              max(4096, nx*ny/16)); a fuller list sets
+                              EPR_ERR_SHIFT_OVERFLOW. */
+    int use_graphs;        /* 1 = capture solver iterations in a CUDA graph
+                              and replay it (default 1). */
+    int reserved[8];       /* must be zero */
+} epr_options;
+
+/* Solver options. */
+typedef struct {
+    int n_iter;       /* maximum iterations (>= 0) */
+    double omega;     /* relaxation of the update (the paper uses 0.4 in its
+                         multi-pixel stress test); > 0 */
+    double tol;       /* stop a projection once kappa <= tol; 0 = run n_iter */
+    double eps_I;     /* positivity floor of the updated line intensity,
+                         relative to its spectral weight (default 1e-8) */
+    int init;         /* 0 = start from the flat field (T := 0), 1 = start
+                         from the caller's T */
+} epr_solve_opts;
+
+/* Per-projection results of a solve, filled after the call synchronises
+ * its stream.  Each pointer is a HOST array of `batch` entries (or
+ * batch * n_iter for the histories), or NULL to skip it. */
+typedef struct {
+    int* iters;          /* iterations run per projection */
+    double* rho;         /* last |D - P| / |D| (residual before the last update) */
+    double* kappa;       /* last |T' - T| / |T'| */
+    double* rho_hist;    /* [batch][n_iter] */
+    double* kappa_hist;  /* [batch][n_iter] */
+    long long overflow_sources; /* out: sources that took the overflow path,
+                                   summed over projections and iterations */
+} epr_solve_info;
+
+/* Create a plan for nx x ny projections with pixel size pixel_m and
+ * propagation distance L_m, and n_lines spectral lines (1..16) with energies
+ * (keV), refractive index decrements delta_s, absorption indices beta_s and
+ * non-negative spectral weights (normalised to sum 1 by the library).
+ * Derived per line: lambda = hc/E, k = 2 pi/lambda, mu = 2 k beta, shift
+ * coefficient -L delta / p^2 (pixels per thickness step), Paganin symbol
+ * mu / (mu + L delta |q|^2).  Host arrays.  *out is NULL on failure. */
+epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, double L_m,
+                           int n_lines, const double* energy_keV, const double* delta,
+                           const double* beta, const double* weights, const epr_options* opt);
+
+/* Release the plan and its device workspace (synchronises the device). */
+void epr_plan_destroy(epr_plan_t plan);
+
+/* Forward model: P = sum_s F_s[f_s exp(-mu_s T)] for `batch` projections
+ * (Eq. 5).  Ps (may be NULL) receives the per-line predictions
+ * [batch][n_lines][ny][nx].  model is an epr_model.  Splat targets outside the
+ * grid are dropped. */
+epr_status epr_forward(epr_plan_t plan, const float* T, float* P, float* Ps, int batch,
+                       int model, void* stream);
+
+/* Adjoint of the non-local forward of line `line` at fixed T (Eq. 4):
+ * g = M_line^T r, the bilinear interpolation of the detector map r at the
+ * mapped coordinates; corners outside the grid read 0. */
+epr_status epr_adjoint(epr_plan_t plan, const float* T, const float* r, float* g, int line,
+                       int batch, void* stream);
+
+/* Paganin-type preconditioner of line `line`, in place: g <- Re F^-1[H_s F[g]],
+ * periodic, no padding. */
+epr_status epr_precondition(epr_plan_t plan, float* g, int line, int batch, void* stream);
+
+/* Non-local solve ("Iterative inversion"): per iteration, forward splat of all
+ * lines, residual D - P split across lines by P_s / P, adjoint gather,
+ * preconditioner, relaxed update floored at eps_I f_s and least-squares
+ * projection onto one thickness (Eq. 7).  T is the initial thickness when
+ * opts->init = 1 and receives the result.  info may be NULL; when it is not,
+ * the call synchronises the stream and fills it. */
+epr_status epr_solve_nonlocal(epr_plan_t plan, const float* D, float* T, int batch,
+                              const epr_solve_opts* opts, epr_solve_info* info, void* stream);
+
+/* Local solve: the same iteration with the local closure of order 1 or 2
+ * (Eq. 1) as forward model and the identity as back-transport. */
+epr_status epr_solve_local(epr_plan_t plan, const float* D, float* T, int batch, int order,
+                           const epr_solve_opts* opts, epr_solve_info* info, void* stream);
+
+/* Synchronise `stream`, read and clear the plan's device error word:
+ * EPR_ERR_SHIFT_OVERFLOW if a splat since the last check overfilled its
+ * overflow list (its prediction then lacks those sources), else EPR_OK. */
+epr_status epr_check_device_status(epr_plan_t plan, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* epr_status_string(epr_status s);
+
+/* Number of kernels this library has launched in the process so far (graph
+ * replays count every kernel node).  For launch accounting in benchmarks. */
+long long epr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPR_H */

@@ -1,0 +1,133 @@
+// Column pass of the 2-D preconditioner: forward FFT along y, the
+// FFT-diagonal Paganin-type filter H_s(q) = mu_s / (mu_s + L delta_s |q|^2)
+// (arXiv 2601.22793, "Linear term and relation to Paganin"; the approximate
+// inverse P_{1,s}^{-1} applied in "Iteration structure"), inverse FFT along y.
+// The 1 / (nx ny) normalisation of the two inverse transforms is folded into
+// the filter.
+//
+// One block transforms CW adjacent columns of the packed half spectrum of
+// one (projection, line); the tile [ny][CW] lives in shared memory.  Column 0
+// holds two real-input columns packed as one complex column (X[0] in the
+// real part, the Nyquist X[nx/2] in the imaginary part); after the forward
+// transform the two are separated with C[ky] and conj C[-ky], filtered with
+// their own symbols and packed again:
+//   C'[ky] = (H0 + HN)/2 C[ky] + (H0 - HN)/2 conj C[-ky].
+#include "epr_internal.cuh"
+#include "fft.cuh"
+
+namespace {
+
+struct ColArgs {
+    float2* S;            // [B][nl][ny][nx/2]
+    const EprProjState* st;
+    const float2* tw;     // exp(-2 pi i t / ny)
+    int CW, lgCW;
+    int line0, nl;
+    int check_done;
+};
+
+template <int EPT>
+__global__ void __launch_bounds__(1024) k_col(const EprConsts C, const ColArgs A)
+{
+    extern __shared__ __align__(16) float2 buf[];
+    const int b = blockIdx.z, sl = blockIdx.y;
+    if (A.check_done && A.st[b].done) return;
+    const int s = A.line0 + sl;
+    const int ny = C.ny, half = C.half, CW = A.CW, lgCW = A.lgCW;
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int kx0 = blockIdx.x * CW;
+    float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * half;
+
+    for (int e = tid; e < ny * CW; e += T) {
+        const int y = e >> lgCW, c = e & (CW - 1);
+        buf[e] = Sb[(size_t)y * half + kx0 + c];
+    }
+    __syncthreads();
+    eprfft::fft<-1, EPT>(buf, ny, lgCW, CW, 1, A.tw, T, tid);
+
+    // filter (two phases: column 0 reads the mirrored frequency)
+    const float ha = C.ha[s], hb = C.hb[s], inv_n = C.inv_n;
+    float2 nv[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int e = tid + k * T;
+        const int y = e >> lgCW, c = e & (CW - 1);
+        const int kx = kx0 + c;
+        const float ky = (float)(y <= ny / 2 ? y : y - ny);
+        const float qy = hb * ky * ky;
+        const float2 v = buf[e];
+        if (kx != 0) {
+            const float H = inv_n / (1.f + ha * (float)kx * (float)kx + qy);
+            nv[k] = cscale(v, H);
+        } else {
+            const float kn = (float)half;
+            const float H0 = inv_n / (1.f + qy);
+            const float HN = inv_n / (1.f + ha * kn * kn + qy);
+            const int yneg = (y == 0) ? 0 : ny - y;
+            const float2 w = cconj(buf[(yneg << lgCW) + c]);
+            const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
+            nv[k] = make_float2(hp * v.x + hm * w.x, hp * v.y + hm * w.y);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) buf[tid + k * T] = nv[k];
+    __syncthreads();
+    eprfft::fft<+1, EPT>(buf, ny, lgCW, CW, 1, A.tw, T, tid);
+    for (int e = tid; e < ny * CW; e += T) {
+        const int y = e >> lgCW, c = e & (CW - 1);
+        Sb[(size_t)y * half + kx0 + c] = buf[e];
+    }
+}
+
+}  // namespace
+
+struct EprColLaunch {
+    int CW, lgCW, EPT, threads;
+    size_t smem;
+};
+
+EprColLaunch epr_col_config(const EprConsts& C, int cw_hint)
+{
+    EprColLaunch L;
+    int cw = cw_hint > 0 ? cw_hint : 4;
+    while (cw > 1 && C.half % cw != 0) cw >>= 1;
+    // keep the block at 1024 threads or fewer
+    int ept = 8;
+    while (C.ny * cw / ept > 1024 && ept < 16) ept *= 2;
+    while (C.ny * cw / ept > 1024 && cw > 1) cw >>= 1;
+    L.CW = cw;
+    L.lgCW = 0;
+    while ((1 << L.lgCW) < cw) ++L.lgCW;
+    L.EPT = ept;
+    L.threads = C.ny * cw / ept;
+    L.smem = (size_t)C.ny * cw * sizeof(float2);
+    return L;
+}
+
+cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int nl, int batch,
+                           int check_done, int cw_hint, cudaStream_t stream)
+{
+    const EprColLaunch L = epr_col_config(C, cw_hint);
+    ColArgs A;
+    A.S = W.S;
+    A.st = W.st;
+    A.tw = W.tw_y;
+    A.CW = L.CW;
+    A.lgCW = L.lgCW;
+    A.line0 = line0;
+    A.nl = nl;
+    A.check_done = check_done;
+    dim3 grid(C.half / L.CW, nl, batch);
+    if (L.EPT == 8) k_col<8><<<grid, L.threads, L.smem, stream>>>(C, A);
+    else k_col<16><<<grid, L.threads, L.smem, stream>>>(C, A);
+    epr_count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t epr_col_init()
+{
+    cudaError_t e = epr_allow_max_smem(k_col<8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col<16>);
+    return e;
+}

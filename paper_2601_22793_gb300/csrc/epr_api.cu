@@ -1,0 +1,650 @@
+// Host runtime of libepr: plans, device workspace, the C ABI of include/epr.h,
+// launch sequences of the solvers and their capture in CUDA graphs.
+//
+// One solver iteration (arXiv 2601.22793, "Iterative inversion") is four
+// kernels over the whole batch:
+//   splat     forward transport of all lines, P and P_s        (splat.cu)
+//   row_fwd   split + adjoint gather + R2C row FFT, rho share  (rowfft.cu)
+//   col       column FFT, Paganin filter, inverse column FFT   (colfft.cu)
+//   row_inv   C2R row FFT + update + projection, kappa share   (rowfft.cu)
+// The local solver replaces splat by the stencil closure (local.cu) and the
+// gather by the identity.  The iteration loop is captured once per
+// (buffers, batch, options) into a CUDA graph and replayed.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "epr_internal.cuh"
+
+// --- launchers from the other translation units -----------------------------
+cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* T, int batch, int TH,
+                             int TW, int check_done, cudaStream_t stream);
+size_t epr_splat_smem(const EprConsts& C, int TH, int TW);
+cudaError_t epr_splat_init();
+struct EprRowLaunch {
+    int RP, lgRP, threads;
+    size_t smem;
+};
+EprRowLaunch epr_row_config(const EprConsts& C);
+cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
+                               const float* D, const float* G, int line0, int nl, int it, int batch,
+                               int check_done, cudaStream_t stream);
+cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, float* Out, int line0,
+                               int nl, int it, float omega, float eps, float tol, int batch,
+                               int check_done, cudaStream_t stream);
+cudaError_t epr_row_init();
+cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int nl, int batch,
+                           int check_done, int cw_hint, cudaStream_t stream);
+cudaError_t epr_col_init();
+cudaError_t epr_launch_gather(const EprConsts& C, const float* T, const float* r, float* g, int line,
+                              int batch, cudaStream_t stream);
+cudaError_t epr_launch_fx_to_float(const unsigned long long* q, float* out, size_t n, cudaStream_t stream);
+cudaError_t epr_launch_local(const EprConsts& C, const EprWork& W, const float* T, float* P, float* Ps,
+                             int order, int batch, int check_done, cudaStream_t stream);
+cudaError_t epr_local_init();
+
+// --- launch accounting -------------------------------------------------------
+static std::atomic<long long> g_launches(0);
+void epr_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern "C" long long epr_launch_count(void) { return g_launches.load(); }
+
+// --- plan --------------------------------------------------------------------
+namespace {
+
+constexpr double kHcEvM = 1.2398419843320026e-6;  // h c in eV m
+constexpr double kPi = 3.14159265358979323846;
+
+struct GraphKey {
+    const void* D;
+    const void* T;
+    int batch, n_iter, init, model;
+    double omega, tol, eps;
+    bool operator==(const GraphKey& o) const
+    {
+        return D == o.D && T == o.T && batch == o.batch && n_iter == o.n_iter && init == o.init &&
+               model == o.model && omega == o.omega && tol == o.tol && eps == o.eps;
+    }
+};
+
+}  // namespace
+
+struct epr_plan_s {
+    EprConsts C;
+    epr_options opt;
+    int device;
+    double pixel, L;
+    double E[EPR_MAX_LINES], delta[EPR_MAX_LINES], beta[EPR_MAX_LINES], w[EPR_MAX_LINES];
+    // workspace
+    EprWork W;
+    int cap_batch;       // batch the workspace is sized for
+    int cap_hist;        // history length it is sized for
+    std::vector<void*> allocs;
+    float2* tw_x;
+    float2* tw_y;
+    // staging of host arrays
+    float* stage[3];
+    size_t stage_elems[3];
+    // pinned host copies for solve info
+    EprProjState* h_st;
+    double* h_hist;
+    size_t h_hist_elems;
+    // tiles
+    int splat_TH, splat_TW;
+    // graph cache
+    cudaStream_t cap_stream;
+    cudaGraphExec_t gexec;
+    GraphKey gkey;
+    int gkernels;
+    bool has_graph;
+};
+
+namespace {
+
+bool size_ok(int n)
+{
+    if (n < 16 || n > 4096) return false;
+    int m = n, twos = 0;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++twos;
+    }
+    while (m % 3 == 0) m /= 3;
+    return m == 1 && twos >= 3;
+}
+
+epr_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return EPR_OK;
+    if (e == cudaErrorMemoryAllocation) return EPR_ERR_OOM;
+    return EPR_ERR_CUDA;
+}
+
+#define EPR_TRY(expr)                                       \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return cuda_status(_e);      \
+    } while (0)
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_workspace(epr_plan_s* p)
+{
+    for (void* a : p->allocs) cudaFree(a);
+    p->allocs.clear();
+    memset(&p->W, 0, sizeof(p->W));
+    p->W.tw_x = p->tw_x;
+    p->W.tw_y = p->tw_y;
+    p->cap_batch = 0;
+    p->cap_hist = 0;
+    if (p->has_graph) {
+        cudaGraphExecDestroy(p->gexec);
+        p->has_graph = false;
+    }
+}
+
+template <typename T>
+cudaError_t dalloc(epr_plan_s* p, T** out, size_t n)
+{
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+    if (e != cudaSuccess) return e;
+    p->allocs.push_back(ptr);
+    *out = reinterpret_cast<T*>(ptr);
+    return cudaSuccess;
+}
+
+epr_status ensure_workspace(epr_plan_s* p, int batch, int hist)
+{
+    if (batch <= p->cap_batch && hist <= p->cap_hist && p->cap_batch > 0) return EPR_OK;
+    const int nb = batch > p->cap_batch ? batch : p->cap_batch;
+    const int nh = hist > p->cap_hist ? hist : (p->cap_hist > 0 ? p->cap_hist : 1);
+    cudaDeviceSynchronize();
+    free_workspace(p);
+    const EprConsts& C = p->C;
+    const size_t npix = (size_t)C.nx * C.ny;
+    EprWork& W = p->W;
+    cudaError_t e = cudaSuccess;
+    W.max_blocks = C.ny / 2;
+    W.hist_len = nh;
+    e = dalloc(p, &W.P, (size_t)nb * npix);
+    if (e == cudaSuccess && C.ns > 1) e = dalloc(p, &W.Ps, (size_t)nb * C.ns * npix);
+    if (e == cudaSuccess && C.det) e = dalloc(p, &W.Pq, (size_t)nb * npix);
+    if (e == cudaSuccess && C.det && C.ns > 1) e = dalloc(p, &W.Psq, (size_t)nb * C.ns * npix);
+    if (e == cudaSuccess) e = dalloc(p, &W.S, (size_t)nb * C.ns * C.ny * C.half);
+    if (e == cudaSuccess) e = dalloc(p, &W.ovf_idx, (size_t)nb * C.ovf_cap);
+    if (e == cudaSuccess) e = dalloc(p, &W.ovf_mask, (size_t)nb * C.ovf_cap);
+    if (e == cudaSuccess) e = dalloc(p, &W.st, (size_t)nb);
+    if (e == cudaSuccess) e = dalloc(p, &W.part_a, (size_t)nb * W.max_blocks);
+    if (e == cudaSuccess) e = dalloc(p, &W.part_b, (size_t)nb * W.max_blocks);
+    if (e == cudaSuccess) e = dalloc(p, &W.rho_hist, (size_t)nb * nh);
+    if (e == cudaSuccess) e = dalloc(p, &W.kappa_hist, (size_t)nb * nh);
+    if (e == cudaSuccess) e = dalloc(p, &W.err, 1);
+    if (e == cudaSuccess) e = cudaMemset(W.st, 0, (size_t)nb * sizeof(EprProjState));
+    if (e == cudaSuccess) e = cudaMemset(W.err, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(W.rho_hist, 0, (size_t)nb * nh * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(W.kappa_hist, 0, (size_t)nb * nh * sizeof(double));
+    if (e != cudaSuccess) {
+        free_workspace(p);
+        return cuda_status(e);
+    }
+    W.tw_x = p->tw_x;
+    W.tw_y = p->tw_y;
+    p->cap_batch = nb;
+    p->cap_hist = nh;
+    // pinned host mirrors for solve info
+    if (p->h_st) cudaFreeHost(p->h_st);
+    if (p->h_hist) cudaFreeHost(p->h_hist);
+    p->h_st = nullptr;
+    p->h_hist = nullptr;
+    e = cudaMallocHost((void**)&p->h_st, (size_t)nb * sizeof(EprProjState));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_hist, (size_t)2 * nb * nh * sizeof(double));
+    if (e != cudaSuccess) return cuda_status(e);
+    p->h_hist_elems = (size_t)2 * nb * nh;
+    return EPR_OK;
+}
+
+// Device view of a caller array: the pointer itself, or a staging buffer
+// (filled from the host when `copy_in`).
+epr_status resolve(epr_plan_s* p, int slot, const float* ptr, size_t n, bool copy_in,
+                   cudaStream_t s, float** out, bool* staged)
+{
+    if (is_device_ptr(ptr)) {
+        *out = const_cast<float*>(ptr);
+        *staged = false;
+        return EPR_OK;
+    }
+    if (p->stage_elems[slot] < n) {
+        if (p->stage[slot]) {
+            cudaStreamSynchronize(s);
+            cudaFree(p->stage[slot]);
+            p->stage[slot] = nullptr;
+        }
+        EPR_TRY(cudaMalloc((void**)&p->stage[slot], n * sizeof(float)));
+        p->stage_elems[slot] = n;
+        if (p->has_graph) {  // staging address changed: the cached graph is stale
+            cudaGraphExecDestroy(p->gexec);
+            p->has_graph = false;
+        }
+    }
+    if (copy_in) EPR_TRY(cudaMemcpyAsync(p->stage[slot], ptr, n * sizeof(float), cudaMemcpyHostToDevice, s));
+    *out = p->stage[slot];
+    *staged = true;
+    return EPR_OK;
+}
+
+void choose_splat_tiles(epr_plan_s* p)
+{
+    const EprConsts& C = p->C;
+    const int cand[3][2] = {{64, 64}, {32, 64}, {32, 32}};
+    p->splat_TH = 32;
+    p->splat_TW = 32;
+    for (auto& c : cand) {
+        const size_t acc = (size_t)C.ns * c[0] * c[1] * (C.det ? 8 : 4);
+        if (acc <= 65536 && epr_splat_smem(C, c[0], c[1]) <= 200 * 1024) {
+            p->splat_TH = c[0];
+            p->splat_TW = c[1];
+            break;
+        }
+    }
+}
+
+// One pass of the chosen forward model writing W.P (and W.Ps / W.Pq / W.Psq).
+epr_status launch_forward(epr_plan_s* p, const float* T, int batch, int model, int check_done,
+                          cudaStream_t s)
+{
+    if (model == EPR_MODEL_NONLOCAL)
+        EPR_TRY(epr_launch_splat(p->C, p->W, T, batch, p->splat_TH, p->splat_TW, check_done, s));
+    else
+        EPR_TRY(epr_launch_local(p->C, p->W, T, p->W.P, p->W.Ps, model, batch, check_done, s));
+    return EPR_OK;
+}
+
+// The whole solve, launched on stream s (captured or not).
+epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, const epr_solve_opts* o,
+                        int model, cudaStream_t s)
+{
+    const EprConsts& C = p->C;
+    const size_t npix = (size_t)C.nx * C.ny;
+    EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)batch * sizeof(EprProjState), s));
+    EPR_TRY(cudaMemsetAsync(p->W.err, 0, sizeof(unsigned int), s));
+    if (o->init == 0) EPR_TRY(cudaMemsetAsync(T, 0, (size_t)batch * npix * sizeof(float), s));
+    const int fwd_mode = model == EPR_MODEL_NONLOCAL ? 0 : 1;
+    const float eps = (float)(o->eps_I > 0 ? o->eps_I : 1e-8);
+    for (int it = 0; it < o->n_iter; ++it) {
+        epr_status st = launch_forward(p, T, batch, model, 1, s);
+        if (st != EPR_OK) return st;
+        EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, T, D, nullptr, 0, C.ns, it, batch, 1, s));
+        EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 1, 0, s));
+        EPR_TRY(epr_launch_row_inv(C, p->W, 0, T, 0, C.ns, it, (float)o->omega, eps, (float)o->tol,
+                                   batch, 1, s));
+    }
+    return EPR_OK;
+}
+
+epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int model,
+                        const epr_solve_opts* o, epr_solve_info* info, cudaStream_t s)
+{
+    if (!p || !D || !T || !o || batch <= 0 || o->n_iter < 0 || !(o->omega > 0.0) || o->tol < 0.0)
+        return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    const size_t n = (size_t)batch * p->C.nx * p->C.ny;
+    epr_status st = ensure_workspace(p, batch, o->n_iter > 0 ? o->n_iter : 1);
+    if (st != EPR_OK) return st;
+    float *Dd, *Td;
+    bool sD, sT;
+    st = resolve(p, 0, D, n, true, s, &Dd, &sD);
+    if (st != EPR_OK) return st;
+    st = resolve(p, 1, T, n, o->init != 0, s, &Td, &sT);
+    if (st != EPR_OK) return st;
+
+    const int kernels_per_iter = 4;
+    if (p->opt.use_graphs && o->n_iter > 0) {
+        GraphKey key{Dd, Td, batch, o->n_iter, o->init, model, o->omega, o->tol, o->eps_I};
+        if (!(p->has_graph && p->gkey == key)) {
+            if (p->has_graph) {
+                cudaGraphExecDestroy(p->gexec);
+                p->has_graph = false;
+            }
+            cudaGraph_t g;
+            EPR_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+            const long long before = g_launches.load();
+            epr_status ls = launch_solve(p, Dd, Td, batch, o, model, p->cap_stream);
+            cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+            g_launches.store(before);  // captured launches did not run
+            if (ls != EPR_OK) {
+                if (ce == cudaSuccess) cudaGraphDestroy(g);
+                return ls;
+            }
+            EPR_TRY(ce);
+            cudaError_t ie = cudaGraphInstantiate(&p->gexec, g, 0);
+            cudaGraphDestroy(g);
+            EPR_TRY(ie);
+            p->gkey = key;
+            p->gkernels = kernels_per_iter * o->n_iter;
+            p->has_graph = true;
+        }
+        EPR_TRY(cudaGraphLaunch(p->gexec, s));
+        epr_count_launch(p->gkernels);
+    } else {
+        st = launch_solve(p, Dd, Td, batch, o, model, s);
+        if (st != EPR_OK) return st;
+    }
+    if (sT) EPR_TRY(cudaMemcpyAsync(T, Td, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+
+    if (info) {
+        const int nh = p->W.hist_len;
+        EPR_TRY(cudaMemcpyAsync(p->h_st, p->W.st, (size_t)batch * sizeof(EprProjState),
+                                cudaMemcpyDeviceToHost, s));
+        EPR_TRY(cudaMemcpyAsync(p->h_hist, p->W.rho_hist, (size_t)batch * nh * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+        EPR_TRY(cudaMemcpyAsync(p->h_hist + (size_t)batch * nh, p->W.kappa_hist,
+                                (size_t)batch * nh * sizeof(double), cudaMemcpyDeviceToHost, s));
+        unsigned int herr = 0;
+        EPR_TRY(cudaMemcpyAsync(&herr, p->W.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        EPR_TRY(cudaStreamSynchronize(s));
+        long long ovf = 0;
+        for (int b = 0; b < batch; ++b) {
+            const EprProjState& ps = p->h_st[b];
+            const int k = ps.iters;
+            if (info->iters) info->iters[b] = k;
+            if (info->rho) info->rho[b] = k > 0 ? p->h_hist[(size_t)b * nh + k - 1] : 0.0;
+            if (info->kappa) info->kappa[b] = k > 0 ? p->h_hist[(size_t)(batch + b) * nh + k - 1] : 0.0;
+            for (int i = 0; i < o->n_iter; ++i) {
+                const bool ran = i < k;
+                if (info->rho_hist)
+                    info->rho_hist[(size_t)b * o->n_iter + i] = ran ? p->h_hist[(size_t)b * nh + i] : 0.0;
+                if (info->kappa_hist)
+                    info->kappa_hist[(size_t)b * o->n_iter + i] =
+                        ran ? p->h_hist[(size_t)(batch + b) * nh + i] : 0.0;
+            }
+            ovf += ps.ovf_total;
+        }
+        info->overflow_sources = ovf;
+        if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
+    }
+    return EPR_OK;
+}
+
+std::mutex g_init_mu;
+int g_init_done[64];
+
+epr_status init_kernels(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (dev >= 0 && dev < 64 && g_init_done[dev]) return EPR_OK;
+    EPR_TRY(epr_splat_init());
+    EPR_TRY(epr_row_init());
+    EPR_TRY(epr_col_init());
+    EPR_TRY(epr_local_init());
+    if (dev >= 0 && dev < 64) g_init_done[dev] = 1;
+    return EPR_OK;
+}
+
+}  // namespace
+
+// --- C ABI -------------------------------------------------------------------
+extern "C" {
+
+const char* epr_status_string(epr_status s)
+{
+    switch (s) {
+    case EPR_OK: return "ok";
+    case EPR_ERR_INVALID_ARG: return "invalid argument";
+    case EPR_ERR_UNSUPPORTED_SIZE: return "unsupported size (need 2^a 3^b, a >= 3, 16..4096)";
+    case EPR_ERR_OOM: return "out of device memory";
+    case EPR_ERR_CUDA: return "CUDA error";
+    case EPR_ERR_NONFINITE: return "non-finite input";
+    case EPR_ERR_TIMEOUT: return "device wait timed out";
+    case EPR_ERR_NOT_CONVERGED: return "not converged";
+    case EPR_ERR_SHIFT_OVERFLOW: return "overflow list full (shifts beyond max_shift_px)";
+    }
+    return "unknown status";
+}
+
+epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, double L_m, int n_lines,
+                           const double* energy_keV, const double* delta, const double* beta,
+                           const double* weights, const epr_options* opt)
+{
+    if (!out) return EPR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!energy_keV || !delta || !beta || !weights) return EPR_ERR_INVALID_ARG;
+    if (n_lines < 1 || n_lines > EPR_MAX_LINES || !(pixel_m > 0.0) || !(L_m >= 0.0))
+        return EPR_ERR_INVALID_ARG;
+    if (!size_ok(nx) || !size_ok(ny)) return EPR_ERR_UNSUPPORTED_SIZE;
+    epr_options o = {12, 0, 0, 1, {0}};
+    if (opt) o = *opt;
+    if (o.max_shift_px < 1 || o.max_shift_px > EPR_MAX_SHIFT || o.overflow_capacity < 0)
+        return EPR_ERR_INVALID_ARG;
+    for (int i = 0; i < 8; ++i)
+        if (o.reserved[i] != 0) return EPR_ERR_INVALID_ARG;
+    double wsum = 0.0;
+    for (int s = 0; s < n_lines; ++s) {
+        if (!(energy_keV[s] > 0.0) || !(weights[s] >= 0.0) || !(beta[s] >= 0.0) || !isfinite(delta[s]))
+            return EPR_ERR_INVALID_ARG;
+        wsum += weights[s];
+    }
+    if (!(wsum > 0.0)) return EPR_ERR_INVALID_ARG;
+
+    epr_plan_s* p = new (std::nothrow) epr_plan_s();
+    if (!p) return EPR_ERR_OOM;
+    memset(&p->C, 0, sizeof(p->C));
+    p->opt = o;
+    p->pixel = pixel_m;
+    p->L = L_m;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return EPR_ERR_CUDA;
+    }
+    EprConsts& C = p->C;
+    C.nx = nx;
+    C.ny = ny;
+    C.ns = n_lines;
+    C.half = nx / 2;
+    C.smax = o.max_shift_px;
+    C.det = o.deterministic ? 1 : 0;
+    const size_t npix = (size_t)nx * ny;
+    C.ovf_cap = o.overflow_capacity > 0 ? o.overflow_capacity
+                                        : (int)(npix / 16 > 4096 ? npix / 16 : 4096);
+    C.inv_n = (float)(1.0 / ((double)nx * ny));
+    double den = 0.0;
+    double mu[EPR_MAX_LINES], f[EPR_MAX_LINES];
+    for (int s = 0; s < n_lines; ++s) {
+        const double lam = kHcEvM / (energy_keV[s] * 1e3);
+        const double k = 2.0 * kPi / lam;
+        mu[s] = 2.0 * k * beta[s];
+        f[s] = weights[s] / wsum;
+        den += f[s] * mu[s] * mu[s];
+        p->E[s] = energy_keV[s];
+        p->delta[s] = delta[s];
+        p->beta[s] = beta[s];
+        p->w[s] = weights[s];
+        const double Ld = L_m * delta[s];
+        C.f[s] = (float)f[s];
+        C.mu[s] = (float)mu[s];
+        C.c[s] = (float)(-Ld / (pixel_m * pixel_m));
+        const double fx1 = 1.0 / (nx * pixel_m), fy1 = 1.0 / (ny * pixel_m);
+        C.ha[s] = mu[s] > 0.0 ? (float)(Ld * 4.0 * kPi * kPi * fx1 * fx1 / mu[s]) : 0.f;
+        C.hb[s] = mu[s] > 0.0 ? (float)(Ld * 4.0 * kPi * kPi * fy1 * fy1 / mu[s]) : 0.f;
+        const double eps = L_m / k;
+        C.qc[s] = (float)(eps * eps / (4.0 * pixel_m * pixel_m * pixel_m * pixel_m));
+    }
+    if (!(den > 0.0)) {
+        delete p;
+        return EPR_ERR_INVALID_ARG;  // no line both weighted and absorbing
+    }
+    for (int s = 0; s < n_lines; ++s) C.wproj[s] = (float)(f[s] * mu[s] / den);
+
+    epr_status st = init_kernels(p->device);
+    if (st != EPR_OK) {
+        delete p;
+        return st;
+    }
+    // twiddle tables exp(-2 pi i t / n), built in double
+    std::vector<float2> tw(nx > ny ? nx : ny);
+    for (int t = 0; t < nx; ++t) {
+        const double a = -2.0 * kPi * (double)t / nx;
+        tw[t] = make_float2((float)cos(a), (float)sin(a));
+    }
+    e = cudaMalloc((void**)&p->tw_x, nx * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(p->tw_x, tw.data(), nx * sizeof(float2), cudaMemcpyHostToDevice);
+    for (int t = 0; t < ny; ++t) {
+        const double a = -2.0 * kPi * (double)t / ny;
+        tw[t] = make_float2((float)cos(a), (float)sin(a));
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->tw_y, ny * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemcpy(p->tw_y, tw.data(), ny * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        if (p->tw_x) cudaFree(p->tw_x);
+        if (p->tw_y) cudaFree(p->tw_y);
+        delete p;
+        return cuda_status(e);
+    }
+    p->W.tw_x = p->tw_x;
+    p->W.tw_y = p->tw_y;
+    choose_splat_tiles(p);
+    *out = p;
+    return EPR_OK;
+}
+
+void epr_plan_destroy(epr_plan_t p)
+{
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    free_workspace(p);
+    for (int i = 0; i < 3; ++i)
+        if (p->stage[i]) cudaFree(p->stage[i]);
+    if (p->tw_x) cudaFree(p->tw_x);
+    if (p->tw_y) cudaFree(p->tw_y);
+    if (p->h_st) cudaFreeHost(p->h_st);
+    if (p->h_hist) cudaFreeHost(p->h_hist);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    delete p;
+}
+
+epr_status epr_forward(epr_plan_t p, const float* T, float* P, float* Ps, int batch, int model,
+                       void* stream)
+{
+    if (!p || !T || !P || batch <= 0 || model < 0 || model > 2) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const EprConsts& C = p->C;
+    const size_t npix = (size_t)C.nx * C.ny, n = (size_t)batch * npix;
+    epr_status st = ensure_workspace(p, batch, 1);
+    if (st != EPR_OK) return st;
+    float *Td, *Pd, *Psd = nullptr;
+    bool sT, sP, sPs = false;
+    st = resolve(p, 0, T, n, true, s, &Td, &sT);
+    if (st == EPR_OK) st = resolve(p, 1, P, n, false, s, &Pd, &sP);
+    if (st == EPR_OK && Ps) st = resolve(p, 2, Ps, n * C.ns, false, s, &Psd, &sPs);
+    if (st != EPR_OK) return st;
+    st = launch_forward(p, Td, batch, model, 0, s);
+    if (st != EPR_OK) return st;
+    const bool fx = (model == EPR_MODEL_NONLOCAL) && C.det;
+    if (fx) {
+        EPR_TRY(epr_launch_fx_to_float(p->W.Pq, Pd, n, s));
+        if (Psd) {
+            if (C.ns > 1) EPR_TRY(epr_launch_fx_to_float(p->W.Psq, Psd, n * C.ns, s));
+            else EPR_TRY(epr_launch_fx_to_float(p->W.Pq, Psd, n, s));
+        }
+    } else {
+        EPR_TRY(cudaMemcpyAsync(Pd, p->W.P, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        if (Psd) {
+            const float* src = C.ns > 1 ? p->W.Ps : p->W.P;
+            EPR_TRY(cudaMemcpyAsync(Psd, src, n * C.ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    if (sP) EPR_TRY(cudaMemcpyAsync(P, Pd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (sPs) EPR_TRY(cudaMemcpyAsync(Ps, Psd, n * C.ns * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (sP || sPs) EPR_TRY(cudaStreamSynchronize(s));
+    return EPR_OK;
+}
+
+epr_status epr_adjoint(epr_plan_t p, const float* T, const float* r, float* g, int line, int batch,
+                       void* stream)
+{
+    if (!p || !T || !r || !g || batch <= 0 || line < 0 || line >= p->C.ns) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)batch * p->C.nx * p->C.ny;
+    float *Td, *rd, *gd;
+    bool sT, sr, sg;
+    epr_status st = resolve(p, 0, T, n, true, s, &Td, &sT);
+    if (st == EPR_OK) st = resolve(p, 1, r, n, true, s, &rd, &sr);
+    if (st == EPR_OK) st = resolve(p, 2, g, n, false, s, &gd, &sg);
+    if (st != EPR_OK) return st;
+    EPR_TRY(epr_launch_gather(p->C, Td, rd, gd, line, batch, s));
+    if (sg) {
+        EPR_TRY(cudaMemcpyAsync(g, gd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        EPR_TRY(cudaStreamSynchronize(s));
+    }
+    return EPR_OK;
+}
+
+epr_status epr_precondition(epr_plan_t p, float* g, int line, int batch, void* stream)
+{
+    if (!p || !g || batch <= 0 || line < 0 || line >= p->C.ns) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)batch * p->C.nx * p->C.ny;
+    epr_status st = ensure_workspace(p, batch, 1);
+    if (st != EPR_OK) return st;
+    float* gd;
+    bool sg;
+    st = resolve(p, 0, g, n, true, s, &gd, &sg);
+    if (st != EPR_OK) return st;
+    EPR_TRY(epr_launch_row_fwd(p->C, p->W, 2, nullptr, nullptr, gd, line, 1, 0, batch, 0, s));
+    EPR_TRY(epr_launch_col(p->C, p->W, line, 1, batch, 0, 0, s));
+    EPR_TRY(epr_launch_row_inv(p->C, p->W, 1, gd, line, 1, 0, 1.f, 0.f, 0.f, batch, 0, s));
+    if (sg) {
+        EPR_TRY(cudaMemcpyAsync(g, gd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        EPR_TRY(cudaStreamSynchronize(s));
+    }
+    return EPR_OK;
+}
+
+epr_status epr_solve_nonlocal(epr_plan_t p, const float* D, float* T, int batch,
+                              const epr_solve_opts* opts, epr_solve_info* info, void* stream)
+{
+    return solve_common(p, D, T, batch, EPR_MODEL_NONLOCAL, opts, info, (cudaStream_t)stream);
+}
+
+epr_status epr_solve_local(epr_plan_t p, const float* D, float* T, int batch, int order,
+                           const epr_solve_opts* opts, epr_solve_info* info, void* stream)
+{
+    if (order != 1 && order != 2) return EPR_ERR_INVALID_ARG;
+    return solve_common(p, D, T, batch, order, opts, info, (cudaStream_t)stream);
+}
+
+epr_status epr_check_device_status(epr_plan_t p, void* stream)
+{
+    if (!p) return EPR_ERR_INVALID_ARG;
+    if (!p->W.err) return EPR_OK;
+    EPR_TRY(cudaSetDevice(p->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int herr = 0;
+    EPR_TRY(cudaMemcpyAsync(&herr, p->W.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    EPR_TRY(cudaMemsetAsync(p->W.err, 0, sizeof(unsigned int), s));
+    EPR_TRY(cudaStreamSynchronize(s));
+    if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
+    return EPR_OK;
+}
+
+}  // extern "C"

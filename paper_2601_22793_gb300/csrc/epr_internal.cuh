@@ -1,0 +1,126 @@
+// Internal definitions shared by the CUDA translation units of libepr.
+// Nothing here is part of the C ABI (include/epr.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "epr.h"
+
+#define EPR_MAX_LINES 16
+#define EPR_MAX_SHIFT 32
+
+// Device-side error bits (OR-ed into the plan's error word).
+#define EPR_DEVERR_OVERFLOW 1u
+
+// Fixed-point scale of the deterministic splat: value * 2^40.
+#define EPR_FX_SCALE 1099511627776.0f
+#define EPR_FX_INV 9.094947017729282e-13f
+
+// Per-plan constants handed to every kernel by value.  All per-line values
+// are derived in double on the host and rounded once to float.
+struct EprConsts {
+    int nx, ny, ns;      // grid and number of spectral lines
+    int half;            // nx / 2 (complex columns of the packed half spectrum)
+    int smax;            // fast-path splat reach in pixels
+    int det;             // 1 = int64 fixed-point splat accumulation
+    int ovf_cap;         // overflow list entries per projection
+    float inv_n;         // 1 / (nx * ny), folded into the filter
+    float f[EPR_MAX_LINES];     // spectral weights, sum 1
+    float mu[EPR_MAX_LINES];    // attenuation 2 k beta (1/m)
+    float c[EPR_MAX_LINES];     // shift per thickness step: -L delta / p^2 (1/m)
+    float wproj[EPR_MAX_LINES]; // f mu / sum(f mu^2): weights of the projection
+    float ha[EPR_MAX_LINES];    // Paganin: L delta 4 pi^2 / (mu (nx p)^2)
+    float hb[EPR_MAX_LINES];    // Paganin: L delta 4 pi^2 / (mu (ny p)^2)
+    float qc[EPR_MAX_LINES];    // local closure: eps^2 / (4 p^4), eps = L / k
+};
+
+// Per-projection solver state in device memory.
+struct EprProjState {
+    int done;        // 1 = converged, later iterations skip the projection
+    int iters;       // iterations run
+    unsigned int cnt_splat;   // arrival counters of the last-block pattern
+    unsigned int cnt_fwd;
+    unsigned int cnt_inv;
+    int ovf_count;   // overflow list fill of the current splat
+    long long ovf_total;      // sources that took the overflow path, all iterations
+    float rho, kappa;         // last values
+};
+
+// Device workspace pointers (owned by the plan).
+struct EprWork {
+    float* P;            // [B][ny][nx]            (float mode)
+    float* Ps;           // [B][ns][ny][nx]        (float mode, ns > 1)
+    unsigned long long* Pq;   // [B][ny][nx]       (fixed-point mode)
+    unsigned long long* Psq;  // [B][ns][ny][nx]   (fixed-point mode, ns > 1)
+    float2* S;           // [B][ns][ny][nx/2] packed half spectrum
+    int* ovf_idx;        // [B][cap] source pixel index
+    unsigned int* ovf_mask;   // [B][cap] lines that took the overflow path
+    EprProjState* st;    // [B]
+    double* part_a;      // [B][max_blocks] block partial sums
+    double* part_b;      // [B][max_blocks]
+    double* rho_hist;    // [B][hist_len]
+    double* kappa_hist;  // [B][hist_len]
+    unsigned int* err;   // device error word
+    const float2* tw_x;  // twiddles exp(-2 pi i t / nx), t < nx
+    const float2* tw_y;  // twiddles exp(-2 pi i t / ny), t < ny
+    int hist_len;        // columns of rho_hist / kappa_hist
+    int max_blocks;      // columns of part_a / part_b
+};
+
+// --- small helpers ---------------------------------------------------------
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Block-wide sum of two floats; returns the totals in thread 0.
+// `red` must hold 2 * 32 floats of shared memory.
+__device__ __forceinline__ void block_sum2(float& a, float& b, float* red)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        red[wid] = a;
+        red[32 + wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        a = lane < nw ? red[lane] : 0.f;
+        b = lane < nw ? red[32 + lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+// Launch-accounting hook (defined in epr_api.cu).
+void epr_count_launch(int n);
+
+// Let a kernel use all opt-in shared memory of the device (called once per
+// device at plan creation, never while a stream is being captured).
+template <typename K>
+inline cudaError_t epr_allow_max_smem(K kernel)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}

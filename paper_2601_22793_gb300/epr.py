@@ -1,0 +1,268 @@
+"""Thin Python binding of libepr (the C ABI in include/epr.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libepr.so.  The functions carry the C names; arrays are torch
+tensors (CUDA or CPU, float32, contiguous) or numpy arrays, passed by data
+pointer.  The stream defaults to torch's current CUDA stream.
+
+If libepr.so is missing or cannot be loaded, every call raises RuntimeError:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libepr.so")
+_lock = threading.Lock()
+_lib = None
+
+EPR_OK = 0
+EPR_ERR_INVALID_ARG = 1
+EPR_ERR_UNSUPPORTED_SIZE = 2
+EPR_ERR_OOM = 3
+EPR_ERR_CUDA = 4
+EPR_ERR_NONFINITE = 5
+EPR_ERR_TIMEOUT = 6
+EPR_ERR_NOT_CONVERGED = 7
+EPR_ERR_SHIFT_OVERFLOW = 8
+
+EPR_MODEL_NONLOCAL = 0
+EPR_MODEL_LOCAL1 = 1
+EPR_MODEL_LOCAL2 = 2
+
+SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
+           "epr_precondition", "epr_solve_nonlocal", "epr_solve_local",
+           "epr_check_device_status", "epr_status_string", "epr_launch_count")
+
+
+class epr_options(ctypes.Structure):
+    _fields_ = [("max_shift_px", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("overflow_capacity", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class epr_solve_opts(ctypes.Structure):
+    _fields_ = [("n_iter", ctypes.c_int), ("omega", ctypes.c_double), ("tol", ctypes.c_double),
+                ("eps_I", ctypes.c_double), ("init", ctypes.c_int)]
+
+
+class epr_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.POINTER(ctypes.c_int)),
+                ("rho", ctypes.POINTER(ctypes.c_double)),
+                ("kappa", ctypes.POINTER(ctypes.c_double)),
+                ("rho_hist", ctypes.POINTER(ctypes.c_double)),
+                ("kappa_hist", ctypes.POINTER(ctypes.c_double)),
+                ("overflow_sources", ctypes.c_longlong)]
+
+
+class EprError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+def load(path: str | None = None):
+    """Load libepr.so (raises RuntimeError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libepr.so not found at {p}; build it with "
+                               "`python -m paper_2601_22793_gb300.build` (needs nvcc)")
+        lib = ctypes.CDLL(p)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.epr_plan_create.argtypes = [ctypes.POINTER(vp), i, i, d, d, i, dp, dp, dp, dp,
+                                        ctypes.POINTER(epr_options)]
+        lib.epr_plan_create.restype = i
+        lib.epr_plan_destroy.argtypes = [vp]
+        lib.epr_plan_destroy.restype = None
+        lib.epr_forward.argtypes = [vp, vp, vp, vp, i, i, vp]
+        lib.epr_forward.restype = i
+        lib.epr_adjoint.argtypes = [vp, vp, vp, vp, i, i, vp]
+        lib.epr_adjoint.restype = i
+        lib.epr_precondition.argtypes = [vp, vp, i, i, vp]
+        lib.epr_precondition.restype = i
+        lib.epr_solve_nonlocal.argtypes = [vp, vp, vp, i, ctypes.POINTER(epr_solve_opts),
+                                           ctypes.POINTER(epr_solve_info), vp]
+        lib.epr_solve_nonlocal.restype = i
+        lib.epr_solve_local.argtypes = [vp, vp, vp, i, i, ctypes.POINTER(epr_solve_opts),
+                                        ctypes.POINTER(epr_solve_info), vp]
+        lib.epr_solve_local.restype = i
+        lib.epr_check_device_status.argtypes = [vp, vp]
+        lib.epr_check_device_status.restype = i
+        lib.epr_status_string.argtypes = [i]
+        lib.epr_status_string.restype = ctypes.c_char_p
+        lib.epr_launch_count.argtypes = []
+        lib.epr_launch_count.restype = ctypes.c_longlong
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().epr_status_string(int(status)).decode()
+    except RuntimeError:
+        return "libepr not loaded"
+
+
+def epr_status_string(status: int) -> str:
+    return load().epr_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != EPR_OK:
+        raise EprError(status, what)
+
+
+def _ptr(a):
+    """Data pointer of a float32 contiguous torch tensor or numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be float32 and C-contiguous")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError("tensors must be float32 and contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    import torch
+    if torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def _darr(x):
+    a = np.ascontiguousarray(np.atleast_1d(np.asarray(x, dtype=np.float64)))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
+                    max_shift_px=12, deterministic=False, overflow_capacity=0, use_graphs=True):
+    """Returns an opaque plan handle (int)."""
+    lib = load()
+    E, Ep = _darr(energy_keV)
+    dl, dp_ = _darr(delta)
+    bt, bp = _darr(beta)
+    w, wp = _darr(np.ones(E.size) if weights is None else weights)
+    opt = epr_options(int(max_shift_px), int(bool(deterministic)), int(overflow_capacity),
+                      int(bool(use_graphs)), (ctypes.c_int * 8)())
+    h = ctypes.c_void_p()
+    _check(lib.epr_plan_create(ctypes.byref(h), int(nx), int(ny), float(pixel_m), float(L_m),
+                               int(E.size), Ep, dp_, bp, wp, ctypes.byref(opt)), "epr_plan_create")
+    return h.value
+
+
+def epr_plan_destroy(plan):
+    load().epr_plan_destroy(plan)
+
+
+def epr_forward(plan, T, P, Ps=None, batch=1, model=EPR_MODEL_NONLOCAL, stream=None):
+    _check(load().epr_forward(plan, _ptr(T), _ptr(P), _ptr(Ps), int(batch), int(model),
+                              _stream(stream)), "epr_forward")
+
+
+def epr_adjoint(plan, T, r, g, line=0, batch=1, stream=None):
+    _check(load().epr_adjoint(plan, _ptr(T), _ptr(r), _ptr(g), int(line), int(batch),
+                              _stream(stream)), "epr_adjoint")
+
+
+def epr_precondition(plan, g, line=0, batch=1, stream=None):
+    _check(load().epr_precondition(plan, _ptr(g), int(line), int(batch), _stream(stream)),
+           "epr_precondition")
+
+
+def _solve_opts(n_iter, omega, tol, eps_I, init):
+    return epr_solve_opts(int(n_iter), float(omega), float(tol), float(eps_I), int(init))
+
+
+def _info(batch, n_iter):
+    arrs = {"iters": np.zeros(batch, np.int32), "rho": np.zeros(batch), "kappa": np.zeros(batch),
+            "rho_hist": np.zeros((batch, max(n_iter, 1))),
+            "kappa_hist": np.zeros((batch, max(n_iter, 1)))}
+    info = epr_solve_info(
+        arrs["iters"].ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        arrs["rho"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        arrs["kappa"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        arrs["rho_hist"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        arrs["kappa_hist"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+    return info, arrs
+
+
+def epr_solve_nonlocal(plan, D, T, batch=1, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8,
+                       init=0, want_info=True, stream=None):
+    """Returns a dict of per-projection results (iters, rho, kappa, histories,
+    overflow_sources) when want_info, else None (asynchronous)."""
+    opts = _solve_opts(n_iter, omega, tol, eps_I, init)
+    info, arrs = _info(batch, n_iter) if want_info else (None, None)
+    st = load().epr_solve_nonlocal(plan, _ptr(D), _ptr(T), int(batch), ctypes.byref(opts),
+                                   ctypes.byref(info) if info is not None else None,
+                                   _stream(stream))
+    _check(st, "epr_solve_nonlocal")
+    if arrs is not None:
+        arrs["overflow_sources"] = int(info.overflow_sources)
+    return arrs
+
+
+def epr_solve_local(plan, D, T, batch=1, order=2, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8,
+                    init=0, want_info=True, stream=None):
+    opts = _solve_opts(n_iter, omega, tol, eps_I, init)
+    info, arrs = _info(batch, n_iter) if want_info else (None, None)
+    st = load().epr_solve_local(plan, _ptr(D), _ptr(T), int(batch), int(order),
+                                ctypes.byref(opts),
+                                ctypes.byref(info) if info is not None else None,
+                                _stream(stream))
+    _check(st, "epr_solve_local")
+    if arrs is not None:
+        arrs["overflow_sources"] = int(info.overflow_sources)
+    return arrs
+
+
+def epr_check_device_status(plan, stream=None):
+    _check(load().epr_check_device_status(plan, _stream(stream)), "epr_check_device_status")
+
+
+def epr_launch_count() -> int:
+    return int(load().epr_launch_count())
+
+
+class Plan:
+    """Owning wrapper of a plan handle (destroyed with the object)."""
+
+    def __init__(self, nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None, **opts):
+        self.nx, self.ny = int(nx), int(ny)
+        self.n_lines = int(np.atleast_1d(energy_keV).size)
+        self.handle = epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights,
+                                      **opts)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            epr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
