@@ -20,7 +20,9 @@
  *    pinned); the kind is detected with cudaPointerGetAttributes.  Host
  *    buffers are staged through plan-owned device memory with copies on the
  *    given stream; pinned host memory makes those copies asynchronous.
- *    The caller owns every array; the library never frees them.
+ *    The caller owns every array; the library never frees them.  Maps
+ *    start on a 16-byte boundary (cudaMalloc and torch allocations do);
+ *    an unaligned map is rejected with EPR_ERR_INVALID_ARG.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
  *    asynchronous on it, except where an entry point says it synchronises.
  *  - Sizes: nx and ny of the form 2^a 3^b with a >= 3, 16 <= n <= 4096.
@@ -61,7 +63,7 @@ typedef enum {
 
 /* Plan options (NULL = defaults). */
 typedef struct {
-    int max_shift_px;      /* fast-path reach of the splat, in pixels (default 12,
+    int max_shift_px;      /* fast-path reach of the splat, in pixels (default 4,
                               range 1..32).  Sources whose shift exceeds it in
                               either axis are not lost: they go through an
                               overflow list and are added with global atomics. */
@@ -151,6 +153,26 @@ epr_status epr_solve_local(epr_plan_t plan, const float* D, float* T, int batch,
  * EPR_ERR_SHIFT_OVERFLOW if a splat since the last check overfilled its
  * overflow list (its prediction then lacks those sources), else EPR_OK. */
 epr_status epr_check_device_status(epr_plan_t plan, void* stream);
+
+/* Kernel kinds reported by epr_profile_read. */
+typedef enum {
+    EPR_KERNEL_SPLAT = 0,    /* forward transport (bilinear redistribution)   */
+    EPR_KERNEL_ROW_FWD = 1,  /* split + adjoint gather + R2C row FFT          */
+    EPR_KERNEL_COL = 2,      /* column FFT + Paganin filter + inverse         */
+    EPR_KERNEL_ROW_INV = 3,  /* C2R row FFT + update + projection             */
+    EPR_KERNEL_LOCAL = 4,    /* local closure stencil                         */
+    EPR_KERNEL_OTHER = 5,    /* standalone gather, conversions                */
+    EPR_KERNEL_KINDS = 6
+} epr_kernel_kind;
+
+/* Kernel timing for benchmarks.  While enabled, the plan launches without
+ * CUDA graphs and brackets every kernel with CUDA events recorded on the
+ * kernel's own stream; epr_profile_read synchronises those events and
+ * returns, per kind, the number of launches and their summed duration in
+ * milliseconds since the last read (the counters are then cleared).
+ * Disabling drops pending records. */
+epr_status epr_profile_enable(epr_plan_t plan, int enable);
+epr_status epr_profile_read(epr_plan_t plan, int* launches, double* total_ms);
 
 /* Human-readable name of a status code (static string). */
 const char* epr_status_string(epr_status s);

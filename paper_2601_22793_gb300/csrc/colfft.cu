@@ -27,7 +27,7 @@ struct ColArgs {
 };
 
 template <int EPT>
-__global__ void __launch_bounds__(1024) k_col(const EprConsts C, const ColArgs A)
+__global__ void __launch_bounds__(512, 2) k_col(const EprConsts C, const ColArgs A)
 {
     extern __shared__ __align__(16) float2 buf[];
     const int b = blockIdx.z, sl = blockIdx.y;
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(1024) k_col(const EprConsts C, const ColArgs A
 
     for (int e = tid; e < ny * CW; e += T) {
         const int y = e >> lgCW, c = e & (CW - 1);
-        buf[e] = Sb[(size_t)y * half + kx0 + c];
+        buf[eprfft::pidx(e)] = Sb[(size_t)y * half + kx0 + c];
     }
     __syncthreads();
     eprfft::fft<-1, EPT>(buf, ny, lgCW, CW, 1, A.tw, T, tid);
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(1024) k_col(const EprConsts C, const ColArgs A
         const int kx = kx0 + c;
         const float ky = (float)(y <= ny / 2 ? y : y - ny);
         const float qy = hb * ky * ky;
-        const float2 v = buf[e];
+        const float2 v = buf[eprfft::pidx(e)];
         if (kx != 0) {
             const float H = inv_n / (1.f + ha * (float)kx * (float)kx + qy);
             nv[k] = cscale(v, H);
@@ -64,19 +64,19 @@ __global__ void __launch_bounds__(1024) k_col(const EprConsts C, const ColArgs A
             const float H0 = inv_n / (1.f + qy);
             const float HN = inv_n / (1.f + ha * kn * kn + qy);
             const int yneg = (y == 0) ? 0 : ny - y;
-            const float2 w = cconj(buf[(yneg << lgCW) + c]);
+            const float2 w = cconj(buf[eprfft::pidx((yneg << lgCW) + c)]);
             const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
             nv[k] = make_float2(hp * v.x + hm * w.x, hp * v.y + hm * w.y);
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) buf[tid + k * T] = nv[k];
+    for (int k = 0; k < EPT; ++k) buf[eprfft::pidx(tid + k * T)] = nv[k];
     __syncthreads();
     eprfft::fft<+1, EPT>(buf, ny, lgCW, CW, 1, A.tw, T, tid);
     for (int e = tid; e < ny * CW; e += T) {
         const int y = e >> lgCW, c = e & (CW - 1);
-        Sb[(size_t)y * half + kx0 + c] = buf[e];
+        Sb[(size_t)y * half + kx0 + c] = buf[eprfft::pidx(e)];
     }
 }
 
@@ -92,16 +92,16 @@ EprColLaunch epr_col_config(const EprConsts& C, int cw_hint)
     EprColLaunch L;
     int cw = cw_hint > 0 ? cw_hint : 4;
     while (cw > 1 && C.half % cw != 0) cw >>= 1;
-    // keep the block at 1024 threads or fewer
+    // keep the block at 512 threads or fewer
     int ept = 8;
-    while (C.ny * cw / ept > 1024 && ept < 16) ept *= 2;
-    while (C.ny * cw / ept > 1024 && cw > 1) cw >>= 1;
+    while (C.ny * cw / ept > 512 && ept < 16) ept *= 2;
+    while (C.ny * cw / ept > 512 && cw > 1) cw >>= 1;
     L.CW = cw;
     L.lgCW = 0;
     while ((1 << L.lgCW) < cw) ++L.lgCW;
     L.EPT = ept;
     L.threads = C.ny * cw / ept;
-    L.smem = (size_t)C.ny * cw * sizeof(float2);
+    L.smem = (size_t)eprfft::padded_len(C.ny * cw) * sizeof(float2);
     return L;
 }
 

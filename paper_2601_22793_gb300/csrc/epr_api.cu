@@ -12,6 +12,7 @@
 // (buffers, batch, options) into a CUDA graph and replayed.
 #include <math.h>
 #include <stdio.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -23,8 +24,9 @@
 #include "epr_internal.cuh"
 
 // --- launchers from the other translation units -----------------------------
-cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* T, int batch, int TH,
-                             int TW, int check_done, cudaStream_t stream);
+cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* T, const float* D,
+                             int resid, int parity, int batch, int TH, int TW, int check_done,
+                             cudaStream_t stream);
 size_t epr_splat_smem(const EprConsts& C, int TH, int TW);
 cudaError_t epr_splat_init();
 struct EprRowLaunch {
@@ -32,9 +34,11 @@ struct EprRowLaunch {
     size_t smem;
 };
 EprRowLaunch epr_row_config(const EprConsts& C);
-cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
-                               const float* D, const float* G, int line0, int nl, int it, int batch,
-                               int check_done, cudaStream_t stream);
+cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, int resid,
+                               const float* T, const float* D, const float* G, int line0, int nl,
+                               int it, int batch, int check_done, cudaStream_t stream);
+cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* D, int batch,
+                             cudaStream_t stream);
 cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, float* Out, int line0,
                                int nl, int it, float omega, float eps, float tol, int batch,
                                int check_done, cudaStream_t stream);
@@ -96,6 +100,14 @@ struct epr_plan_s {
     size_t h_hist_elems;
     // tiles
     int splat_TH, splat_TW;
+    // kernel timing (benchmarks)
+    bool profiling;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
     // graph cache
     cudaStream_t cap_stream;
     cudaGraphExec_t gexec;
@@ -130,6 +142,8 @@ epr_status cuda_status(cudaError_t e)
         cudaError_t _e = (expr);                            \
         if (_e != cudaSuccess) return cuda_status(_e);      \
     } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 bool is_device_ptr(const void* p)
 {
@@ -263,14 +277,57 @@ void choose_splat_tiles(epr_plan_s* p)
     }
 }
 
-// One pass of the chosen forward model writing W.P (and W.Ps / W.Pq / W.Psq).
-epr_status launch_forward(epr_plan_s* p, const float* T, int batch, int model, int check_done,
-                          cudaStream_t s)
+cudaEvent_t pool_get(epr_plan_s* p)
 {
-    if (model == EPR_MODEL_NONLOCAL)
-        EPR_TRY(epr_launch_splat(p->C, p->W, T, batch, p->splat_TH, p->splat_TW, check_done, s));
-    else
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets one kernel launch with events when the plan is profiling.
+struct ProfScope {
+    epr_plan_s* p;
+    cudaStream_t s;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(epr_plan_s* p_, int kind_, cudaStream_t s_) : p(p_), s(s_), kind(kind_)
+    {
+        if (p->profiling) {
+            a = pool_get(p);
+            if (a) cudaEventRecord(a, s);
+        }
+    }
+    ~ProfScope()
+    {
+        if (!a) return;
+        cudaEvent_t b = pool_get(p);
+        if (!b) {
+            p->pool.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, s);
+        p->recs.push_back({kind, a, b});
+    }
+};
+
+// One pass of the chosen forward model writing W.P (and W.Ps / W.Pq / W.Psq).
+// With D given (monochromatic float solve) W.P receives D - P instead of P.
+epr_status launch_forward(epr_plan_s* p, const float* T, const float* D, int parity, int batch,
+                          int model, int check_done, cudaStream_t s)
+{
+    if (model == EPR_MODEL_NONLOCAL) {
+        ProfScope ps(p, EPR_KERNEL_SPLAT, s);
+        EPR_TRY(epr_launch_splat(p->C, p->W, T, D, D != nullptr, parity, batch, p->splat_TH,
+                                 p->splat_TW, check_done, s));
+    } else {
+        ProfScope ps(p, EPR_KERNEL_LOCAL, s);
         EPR_TRY(epr_launch_local(p->C, p->W, T, p->W.P, p->W.Ps, model, batch, check_done, s));
+    }
     return EPR_OK;
 }
 
@@ -283,15 +340,31 @@ epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, cons
     EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)batch * sizeof(EprProjState), s));
     EPR_TRY(cudaMemsetAsync(p->W.err, 0, sizeof(unsigned int), s));
     if (o->init == 0) EPR_TRY(cudaMemsetAsync(T, 0, (size_t)batch * npix * sizeof(float), s));
+    {
+        ProfScope ps(p, EPR_KERNEL_OTHER, s);
+        EPR_TRY(epr_launch_dnorm(C, p->W, D, batch, s));
+    }
     const int fwd_mode = model == EPR_MODEL_NONLOCAL ? 0 : 1;
+    // monochromatic float transport: the splat stores the residual D - P
+    const bool resid = model == EPR_MODEL_NONLOCAL && C.ns == 1 && !C.det;
     const float eps = (float)(o->eps_I > 0 ? o->eps_I : 1e-8);
     for (int it = 0; it < o->n_iter; ++it) {
-        epr_status st = launch_forward(p, T, batch, model, 1, s);
+        epr_status st = launch_forward(p, T, resid ? D : nullptr, it & 1, batch, model, 1, s);
         if (st != EPR_OK) return st;
-        EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, T, D, nullptr, 0, C.ns, it, batch, 1, s));
-        EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 1, 0, s));
-        EPR_TRY(epr_launch_row_inv(C, p->W, 0, T, 0, C.ns, it, (float)o->omega, eps, (float)o->tol,
-                                   batch, 1, s));
+        {
+            ProfScope ps(p, EPR_KERNEL_ROW_FWD, s);
+            EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, resid, T, D, nullptr, 0, C.ns, it, batch,
+                                       1, s));
+        }
+        {
+            ProfScope ps(p, EPR_KERNEL_COL, s);
+            EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 1, 0, s));
+        }
+        {
+            ProfScope ps(p, EPR_KERNEL_ROW_INV, s);
+            EPR_TRY(epr_launch_row_inv(C, p->W, 0, T, 0, C.ns, it, (float)o->omega, eps,
+                                       (float)o->tol, batch, 1, s));
+        }
     }
     return EPR_OK;
 }
@@ -301,6 +374,7 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
 {
     if (!p || !D || !T || !o || batch <= 0 || o->n_iter < 0 || !(o->omega > 0.0) || o->tol < 0.0)
         return EPR_ERR_INVALID_ARG;
+    if (!aligned16(D) || !aligned16(T)) return EPR_ERR_INVALID_ARG;
     EPR_TRY(cudaSetDevice(p->device));
     const size_t n = (size_t)batch * p->C.nx * p->C.ny;
     epr_status st = ensure_workspace(p, batch, o->n_iter > 0 ? o->n_iter : 1);
@@ -312,8 +386,8 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
     st = resolve(p, 1, T, n, o->init != 0, s, &Td, &sT);
     if (st != EPR_OK) return st;
 
-    const int kernels_per_iter = 4;
-    if (p->opt.use_graphs && o->n_iter > 0) {
+    const int kernels_per_iter = model == EPR_MODEL_NONLOCAL ? 5 : 4;
+    if (p->opt.use_graphs && !p->profiling && o->n_iter > 0) {
         GraphKey key{Dd, Td, batch, o->n_iter, o->init, model, o->omega, o->tol, o->eps_I};
         if (!(p->has_graph && p->gkey == key)) {
             if (p->has_graph) {
@@ -335,7 +409,7 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
             cudaGraphDestroy(g);
             EPR_TRY(ie);
             p->gkey = key;
-            p->gkernels = kernels_per_iter * o->n_iter;
+            p->gkernels = kernels_per_iter * o->n_iter + 2;
             p->has_graph = true;
         }
         EPR_TRY(cudaGraphLaunch(p->gexec, s));
@@ -426,7 +500,7 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     if (n_lines < 1 || n_lines > EPR_MAX_LINES || !(pixel_m > 0.0) || !(L_m >= 0.0))
         return EPR_ERR_INVALID_ARG;
     if (!size_ok(nx) || !size_ok(ny)) return EPR_ERR_UNSUPPORTED_SIZE;
-    epr_options o = {12, 0, 0, 1, {0}};
+    epr_options o = {4, 0, 0, 1, {0}};
     if (opt) o = *opt;
     if (o.max_shift_px < 1 || o.max_shift_px > EPR_MAX_SHIFT || o.overflow_capacity < 0)
         return EPR_ERR_INVALID_ARG;
@@ -536,6 +610,11 @@ void epr_plan_destroy(epr_plan_t p)
     if (p->h_st) cudaFreeHost(p->h_st);
     if (p->h_hist) cudaFreeHost(p->h_hist);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (auto& r : p->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : p->pool) cudaEventDestroy(e);
     delete p;
 }
 
@@ -543,6 +622,7 @@ epr_status epr_forward(epr_plan_t p, const float* T, float* P, float* Ps, int ba
                        void* stream)
 {
     if (!p || !T || !P || batch <= 0 || model < 0 || model > 2) return EPR_ERR_INVALID_ARG;
+    if (!aligned16(T) || !aligned16(P) || (Ps && !aligned16(Ps))) return EPR_ERR_INVALID_ARG;
     EPR_TRY(cudaSetDevice(p->device));
     cudaStream_t s = (cudaStream_t)stream;
     const EprConsts& C = p->C;
@@ -555,7 +635,8 @@ epr_status epr_forward(epr_plan_t p, const float* T, float* P, float* Ps, int ba
     if (st == EPR_OK) st = resolve(p, 1, P, n, false, s, &Pd, &sP);
     if (st == EPR_OK && Ps) st = resolve(p, 2, Ps, n * C.ns, false, s, &Psd, &sPs);
     if (st != EPR_OK) return st;
-    st = launch_forward(p, Td, batch, model, 0, s);
+    EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)batch * sizeof(EprProjState), s));
+    st = launch_forward(p, Td, nullptr, 0, batch, model, 0, s);
     if (st != EPR_OK) return st;
     const bool fx = (model == EPR_MODEL_NONLOCAL) && C.det;
     if (fx) {
@@ -601,6 +682,7 @@ epr_status epr_adjoint(epr_plan_t p, const float* T, const float* r, float* g, i
 epr_status epr_precondition(epr_plan_t p, float* g, int line, int batch, void* stream)
 {
     if (!p || !g || batch <= 0 || line < 0 || line >= p->C.ns) return EPR_ERR_INVALID_ARG;
+    if (!aligned16(g)) return EPR_ERR_INVALID_ARG;
     EPR_TRY(cudaSetDevice(p->device));
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)batch * p->C.nx * p->C.ny;
@@ -610,7 +692,7 @@ epr_status epr_precondition(epr_plan_t p, float* g, int line, int batch, void* s
     bool sg;
     st = resolve(p, 0, g, n, true, s, &gd, &sg);
     if (st != EPR_OK) return st;
-    EPR_TRY(epr_launch_row_fwd(p->C, p->W, 2, nullptr, nullptr, gd, line, 1, 0, batch, 0, s));
+    EPR_TRY(epr_launch_row_fwd(p->C, p->W, 2, 0, nullptr, nullptr, gd, line, 1, 0, batch, 0, s));
     EPR_TRY(epr_launch_col(p->C, p->W, line, 1, batch, 0, 0, s));
     EPR_TRY(epr_launch_row_inv(p->C, p->W, 1, gd, line, 1, 0, 1.f, 0.f, 0.f, batch, 0, s));
     if (sg) {
@@ -644,6 +726,45 @@ epr_status epr_check_device_status(epr_plan_t p, void* stream)
     EPR_TRY(cudaMemsetAsync(p->W.err, 0, sizeof(unsigned int), s));
     EPR_TRY(cudaStreamSynchronize(s));
     if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
+    return EPR_OK;
+}
+
+epr_status epr_profile_enable(epr_plan_t p, int enable)
+{
+    if (!p) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    if (!enable) {
+        EPR_TRY(cudaDeviceSynchronize());
+        for (auto& r : p->recs) {
+            p->pool.push_back(r.a);
+            p->pool.push_back(r.b);
+        }
+        p->recs.clear();
+    }
+    p->profiling = enable != 0;
+    return EPR_OK;
+}
+
+epr_status epr_profile_read(epr_plan_t p, int* launches, double* total_ms)
+{
+    if (!p || !launches || !total_ms) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    for (int k = 0; k < EPR_KERNEL_KINDS; ++k) {
+        launches[k] = 0;
+        total_ms[k] = 0.0;
+    }
+    for (auto& r : p->recs) {
+        EPR_TRY(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        EPR_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+        if (r.kind >= 0 && r.kind < EPR_KERNEL_KINDS) {
+            launches[r.kind] += 1;
+            total_ms[r.kind] += ms;
+        }
+        p->pool.push_back(r.a);
+        p->pool.push_back(r.b);
+    }
+    p->recs.clear();
     return EPR_OK;
 }
 

@@ -39,17 +39,18 @@ struct EprConsts {
 struct EprProjState {
     int done;        // 1 = converged, later iterations skip the projection
     int iters;       // iterations run
-    unsigned int cnt_splat;   // arrival counters of the last-block pattern
-    unsigned int cnt_fwd;
+    unsigned int cnt_fwd;     // arrival counters of the last-block pattern
     unsigned int cnt_inv;
-    int ovf_count;   // overflow list fill of the current splat
+    int ovf_count[2];         // overflow list fill, by splat parity
     long long ovf_total;      // sources that took the overflow path, all iterations
+    double dnorm2;            // |D|^2 of the projection (set once per solve)
     float rho, kappa;         // last values
+    int pad_;
 };
 
 // Device workspace pointers (owned by the plan).
 struct EprWork {
-    float* P;            // [B][ny][nx]            (float mode)
+    float* P;            // [B][ny][nx]  P, or the residual D - P (mono float solve)
     float* Ps;           // [B][ns][ny][nx]        (float mode, ns > 1)
     unsigned long long* Pq;   // [B][ny][nx]       (fixed-point mode)
     unsigned long long* Psq;  // [B][ns][ny][nx]   (fixed-point mode, ns > 1)
@@ -103,6 +104,51 @@ __device__ __forceinline__ void block_sum2(float& a, float& b, float* red)
             b += __shfl_down_sync(0xffffffffu, b, o);
         }
     }
+}
+
+// Block-wide sum of one double in a fixed order (deterministic for a fixed
+// block size); the total is returned to every thread.  `red` holds 32 doubles.
+__device__ __forceinline__ double block_sum_d(double v, double* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+// Arrival counter of the last-block pattern: every block publishes (a, b)
+// in pa[blk], pb[blk]; the block that arrives last sums all of them in a
+// fixed order with all its threads and returns true (totals in A, B).
+__device__ __forceinline__ bool last_block_reduce(unsigned int* cnt, unsigned int nblk, double* pa,
+                                                  double* pb, int blk, float a, float b,
+                                                  double& A_out, double& B_out)
+{
+    __shared__ int s_last;
+    __shared__ double s_red[32];
+    if (threadIdx.x == 0) {
+        pa[blk] = (double)a;
+        pb[blk] = (double)b;
+        __threadfence();
+        const unsigned int prev = atomicAdd(cnt, 1u);
+        s_last = (prev == nblk - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double sa = 0.0, sb = 0.0;
+    for (unsigned int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        sa += __ldcg(&pa[i]);
+        sb += __ldcg(&pb[i]);
+    }
+    A_out = block_sum_d(sa, s_red);
+    B_out = block_sum_d(sb, s_red);
+    if (threadIdx.x == 0) *cnt = 0u;
+    return true;
 }
 
 // Launch-accounting hook (defined in epr_api.cu).

@@ -17,11 +17,20 @@
 // butterfly b of a stage maps to sequence b & (nseq-1) and index b >> lgseq.
 // Twiddles come from a table tw[t] = exp(-2 pi i t / N) (float, built in
 // double on the host); DIR = +1 uses its conjugate.  No normalisation.
+//
+// Shared-memory addresses pass through pidx(i) = i + i/8: one padding word
+// after every eight complex values.  The first stages write with strides of
+// 8 and 64 words, which otherwise fall into the same banks; with the padding
+// those stores are spread over all banks.  Callers index the buffers through
+// pidx too, and size them with padded_len().
 #pragma once
 
 #include "epr_internal.cuh"
 
 namespace eprfft {
+
+__host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 3) + 1; }
 
 // R-point DFTs in registers, sign DIR (-1 forward, +1 inverse).
 template <int DIR>
@@ -120,7 +129,7 @@ __device__ __forceinline__ void stage(float2* buf, int N, int Ns, int lgNs, int 
             const int jd = (lgNs >= 0) ? (j >> lgNs) : (j / Ns);
             const int base = m * sm;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][r] = buf[(j + r * NR) * sj + base];
+            for (int r = 0; r < R; ++r) v[k][r] = buf[pidx((j + r * NR) * sj + base)];
 #pragma unroll
             for (int r = 1; r < R; ++r) {
                 float2 w = __ldg(&tw[r * jm * twstep]);
@@ -136,7 +145,7 @@ __device__ __forceinline__ void stage(float2* buf, int N, int Ns, int lgNs, int 
         if (dst[k] >= 0) {
             dft<R, DIR>(v[k]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[dst[k] + r * Ns * sj] = v[k][r];
+            for (int r = 0; r < R; ++r) buf[pidx(dst[k] + r * Ns * sj)] = v[k][r];
         }
     }
     __syncthreads();

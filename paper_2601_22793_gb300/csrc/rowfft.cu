@@ -3,26 +3,28 @@
 // Forward row pass (R2C), one block per RP pairs of rows of one projection:
 //   prologue  back-transport of the split residual (arXiv 2601.22793, Eq. 4
 //             and "Iteration structure"): for every object pixel and line,
-//             g_s = sum of the four bilinear weights times
-//             r_s(corner) = (D - P) P_s / P at the shifted corners
-//             (mono: D - P); or the identity back-transport of the local
-//             solver; or a plain load of a real map (standalone filter);
+//             g_s = sum of the four bilinear weights times the residual
+//             r_s = (D - P) P_s / P at the shifted corners (mono: D - P,
+//             read directly when the splat stored it); or the identity
+//             back-transport of the local solver; or a plain load of a real
+//             map (standalone filter).  The thickness rows needed for the
+//             gradient are staged in shared memory first.
 //   transform two real rows packed as one complex row, z = g(y0) + i g(y1),
 //             shared-memory Stockham FFT of length nx;
 //   epilogue  unpack X0[k] = (Z[k] + conj Z[-k]) / 2, X1[k] = (Z[k] -
 //             conj Z[-k]) / 2i and store k < nx/2 with the real Nyquist
 //             value packed into the imaginary part of k = 0.
-// The block also adds its share of |D - P|^2 and |D|^2; the last block of a
-// projection reduces the shares in a fixed order (deterministic) into rho.
+// The block also adds its share of |D - P|^2; the last block of a projection
+// reduces the shares in a fixed order (deterministic) into rho.
 //
 // Inverse row pass (C2R), the mirror image, fused with the update
 // ("Iterative inversion"): per line, I'_s = max(I_s + omega h_s, eps f_s),
 // then the single-thickness projection of Eq. 7,
 //   T' = - sum_s f_s mu_s ln(I'_s / f_s) / sum_s f_s mu_s^2,
 // evaluated as T' = T - sum_s w_s ln(1 + omega h_s / I_s) (w_s = f_s mu_s /
-// sum f mu^2), which is the same quantity without forming exp then log of
-// values near one.  The last block of a projection reduces |T' - T|^2 and
-// |T'|^2 into kappa and retires the projection when kappa <= tol.
+// sum f mu^2), the same quantity without forming exp then log of values
+// near one.  The last block of a projection reduces |T' - T|^2 and |T'|^2
+// into kappa and retires the projection when kappa <= tol.
 #include "epr_internal.cuh"
 #include "fft.cuh"
 
@@ -37,7 +39,7 @@ constexpr int kPad = 4;   // float2 padding between packed rows in shared memory
 struct RowArgs {
     const float* T;          // [B][ny][nx]
     const float* D;          // [B][ny][nx]
-    const float* P;          // [B][ny][nx]          float mode
+    const float* P;          // [B][ny][nx]   P, or D - P when `resid`
     const float* Ps;         // [B][ns][ny][nx]
     const unsigned long long* Pq;   // fixed-point mode
     const unsigned long long* Psq;
@@ -56,6 +58,8 @@ struct RowArgs {
     float omega, eps, tol;
 };
 
+__device__ __forceinline__ int fdiv(int i, float inv_d) { return (int)(((float)i + 0.5f) * inv_d); }
+
 template <bool DET>
 __device__ __forceinline__ float ldP(const float* P, const unsigned long long* Pq, size_t i)
 {
@@ -63,24 +67,28 @@ __device__ __forceinline__ float ldP(const float* P, const unsigned long long* P
     else return __ldg(&P[i]);
 }
 
-// residual of line s at detector pixel q: (D - P) P_s / P (mono: D - P)
-template <bool DET>
+// residual of line s at detector pixel q of projection b (pb = b * npix)
+template <bool DET, bool RESID>
 __device__ __forceinline__ float resid(const EprConsts& C, const RowArgs& A, size_t pb, size_t q,
                                        int s)
 {
-    const float d = __ldg(&A.D[pb + q]);
-    const float p = ldP<DET>(A.P, A.Pq, pb + q);
-    const float r = d - p;
-    if (C.ns == 1) return r;
-    const size_t npix = (size_t)C.nx * C.ny;
-    const size_t ps = pb * C.ns + (size_t)s * npix + q;  // pb = b * npix
-    const float pl = ldP<DET>(A.Ps, A.Psq, ps);
-    return (p > 1e-30f) ? r * (pl / p) : r * C.f[s];
+    if constexpr (RESID) {
+        return __ldg(&A.P[pb + q]);
+    } else {
+        const float d = __ldg(&A.D[pb + q]);
+        const float p = ldP<DET>(A.P, A.Pq, pb + q);
+        const float r = d - p;
+        if (C.ns == 1) return r;
+        const size_t npix = (size_t)C.nx * C.ny;
+        const size_t ps = pb * C.ns + (size_t)s * npix + q;
+        const float pl = ldP<DET>(A.Ps, A.Psq, ps);
+        return (p > 1e-30f) ? r * (pl / p) : r * C.f[s];
+    }
 }
 
 // bilinear gather of line s's residual at (y + uy, x + ux); corners outside
 // the grid read 0 (Eq. 4)
-template <bool DET>
+template <bool DET, bool RESID>
 __device__ __forceinline__ float gather_px(const EprConsts& C, const RowArgs& A, size_t pb, int y,
                                            int x, float uy, float ux, int s)
 {
@@ -91,65 +99,25 @@ __device__ __forceinline__ float gather_px(const EprConsts& C, const RowArgs& A,
     const float dx = ux - fx, dy = uy - fy;
     const int cx = x + (int)fx, cy = y + (int)fy;
     const int nx = C.nx, ny = C.ny;
-    float acc = 0.f;
-    const bool x0 = cx >= 0 && cx < nx, x1 = cx + 1 >= 0 && cx + 1 < nx;
-    if (cy >= 0 && cy < ny) {
+    const bool x0 = (unsigned)cx < (unsigned)nx, x1 = (unsigned)(cx + 1) < (unsigned)nx;
+    float r00 = 0.f, r10 = 0.f, r01 = 0.f, r11 = 0.f;
+    if ((unsigned)cy < (unsigned)ny) {
         const size_t row = (size_t)cy * nx;
-        if (x0) acc += (1.f - dx) * (1.f - dy) * resid<DET>(C, A, pb, row + cx, s);
-        if (x1) acc += dx * (1.f - dy) * resid<DET>(C, A, pb, row + cx + 1, s);
+        if (x0) r00 = resid<DET, RESID>(C, A, pb, row + cx, s);
+        if (x1) r10 = resid<DET, RESID>(C, A, pb, row + cx + 1, s);
     }
-    if (cy + 1 >= 0 && cy + 1 < ny) {
+    if ((unsigned)(cy + 1) < (unsigned)ny) {
         const size_t row = (size_t)(cy + 1) * nx;
-        if (x0) acc += (1.f - dx) * dy * resid<DET>(C, A, pb, row + cx, s);
-        if (x1) acc += dx * dy * resid<DET>(C, A, pb, row + cx + 1, s);
+        if (x0) r01 = resid<DET, RESID>(C, A, pb, row + cx, s);
+        if (x1) r11 = resid<DET, RESID>(C, A, pb, row + cx + 1, s);
     }
-    return acc;
+    const float top = r00 + dx * (r10 - r00);
+    const float bot = r01 + dx * (r11 - r01);
+    return (1.f - dy) * top + dy * bot;
 }
 
-__device__ __forceinline__ float grad_at(const float* Tb, int y, int x, int ny, int nx, bool along_x)
-{
-    const size_t o = (size_t)y * nx + x;
-    if (along_x) {
-        if (x == 0) return __ldg(&Tb[o + 1]) - __ldg(&Tb[o]);
-        if (x == nx - 1) return __ldg(&Tb[o]) - __ldg(&Tb[o - 1]);
-        return 0.5f * (__ldg(&Tb[o + 1]) - __ldg(&Tb[o - 1]));
-    }
-    if (y == 0) return __ldg(&Tb[o + nx]) - __ldg(&Tb[o]);
-    if (y == ny - 1) return __ldg(&Tb[o]) - __ldg(&Tb[o - nx]);
-    return 0.5f * (__ldg(&Tb[o + nx]) - __ldg(&Tb[o - nx]));
-}
-
-// deterministic last-block reduction of per-block (a, b) partial sums
-__device__ __forceinline__ bool last_block_reduce(unsigned int* cnt, unsigned int nblk, double* pa,
-                                                  double* pb, int blk, float a, float b,
-                                                  double& A_out, double& B_out)
-{
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-        pa[blk] = (double)a;
-        pb[blk] = (double)b;
-        __threadfence();
-        const unsigned int prev = atomicAdd(cnt, 1u);
-        s_last = (prev == nblk - 1u);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0;
-        for (unsigned int i = 0; i < nblk; ++i) {
-            sa += ((volatile double*)pa)[i];
-            sb += ((volatile double*)pb)[i];
-        }
-        A_out = sa;
-        B_out = sb;
-        *cnt = 0u;
-    }
-    return true;
-}
-
-template <int MODE, bool DET>
-__global__ void __launch_bounds__(512) k_row_fwd(const EprConsts C, const RowArgs A)
+template <int MODE, bool DET, bool RESID, int NS>
+__global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const RowArgs A)
 {
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
@@ -161,71 +129,85 @@ __global__ void __launch_bounds__(512) k_row_fwd(const EprConsts C, const RowArg
     const size_t npix = (size_t)nx * ny;
     const size_t pb = (size_t)b * npix;
     const int yb = blockIdx.x * RP * 2;   // first row of the block
-    const float* Tb = A.T ? A.T + pb : nullptr;
+    const int nl = NS ? NS : A.nl;
+    // thickness rows yb-1 .. yb+2RP (clamped), after the FFT buffer
+    float* Ts = reinterpret_cast<float*>(zs + ((eprfft::padded_len(RP * sm) + 1) & ~1));
+    const int nrows = 2 * RP + 2;
 
-    // per-thread pixels: element e = tid + k T of the RP x nx packed rows
-    int px[kEPT], pm[kEPT];
-    float gxa[kEPT], gya[kEPT], gxb[kEPT], gyb[kEPT];
-    float ra = 0.f, rb = 0.f;   // |D - P|^2, |D|^2 shares
-#pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        const int e = tid + k * T;
-        pm[k] = e / nx;
-        px[k] = e - pm[k] * nx;
-        if constexpr (MODE == FWD_SOLVE_NL) {
-            const int y0 = yb + 2 * pm[k];
-            gxa[k] = grad_at(Tb, y0, px[k], ny, nx, true);
-            gya[k] = grad_at(Tb, y0, px[k], ny, nx, false);
-            gxb[k] = grad_at(Tb, y0 + 1, px[k], ny, nx, true);
-            gyb[k] = grad_at(Tb, y0 + 1, px[k], ny, nx, false);
+    if constexpr (MODE == FWD_SOLVE_NL) {
+        const float* Tb = A.T + pb;
+        const int q4 = nx >> 2;
+        const float inv_q4 = 1.f / (float)q4;
+        for (int i = tid; i < nrows * q4; i += T) {
+            const int r = fdiv(i, inv_q4), c4 = i - r * q4;
+            const int gy = min(max(yb - 1 + r, 0), ny - 1);
+            reinterpret_cast<float4*>(Ts)[i] =
+                __ldg(reinterpret_cast<const float4*>(Tb + (size_t)gy * nx) + c4);
         }
-        if constexpr (MODE != FWD_LOAD) {
-            const int y0 = yb + 2 * pm[k];
-            const size_t q0 = (size_t)y0 * nx + px[k], q1 = q0 + nx;
-            const float d0 = __ldg(&A.D[pb + q0]), d1 = __ldg(&A.D[pb + q1]);
-            const float r0 = d0 - ldP<DET>(A.P, A.Pq, pb + q0);
-            const float r1 = d1 - ldP<DET>(A.P, A.Pq, pb + q1);
-            ra += r0 * r0 + r1 * r1;
-            rb += d0 * d0 + d1 * d1;
-        }
+        __syncthreads();
     }
 
-    for (int sl = 0; sl < A.nl; ++sl) {
+    float ra = 0.f;   // |D - P|^2 share
+    const float inv_nx = 1.f / (float)nx;
+    for (int sl = 0; sl < nl; ++sl) {
         const int s = A.line0 + sl;
         // prologue: packed complex input rows in shared memory
-#pragma unroll
+#pragma unroll 2
         for (int k = 0; k < kEPT; ++k) {
-            const int y0 = yb + 2 * pm[k], x = px[k];
-            float v0, v1;
-            if constexpr (MODE == FWD_SOLVE_NL) {
-                const float cs = C.c[s];
-                v0 = gather_px<DET>(C, A, pb, y0, x, cs * gya[k], cs * gxa[k], s);
-                v1 = gather_px<DET>(C, A, pb, y0 + 1, x, cs * gyb[k], cs * gxb[k], s);
-            } else if constexpr (MODE == FWD_SOLVE_LOCAL) {
-                v0 = resid<DET>(C, A, pb, (size_t)y0 * nx + x, s);
-                v1 = resid<DET>(C, A, pb, (size_t)(y0 + 1) * nx + x, s);
-            } else {
-                const float* Gb = A.G + pb;
-                v0 = __ldg(&Gb[(size_t)y0 * nx + x]);
-                v1 = __ldg(&Gb[(size_t)(y0 + 1) * nx + x]);
+            const int e = tid + k * T;
+            const int m = RP == 1 ? 0 : fdiv(e, inv_nx);
+            const int x = e - m * nx;
+            const int y0 = yb + 2 * m;
+            float v[2];
+#pragma unroll
+            for (int r0 = 0; r0 < 2; ++r0) {
+                const int y = y0 + r0;
+                if constexpr (MODE == FWD_SOLVE_NL) {
+                    const float* tr = Ts + (2 * m + r0 + 1) * nx;   // row y
+                    const float t = tr[x];
+                    float gx, gy;
+                    if (x == 0) gx = tr[1] - t;
+                    else if (x == nx - 1) gx = t - tr[x - 1];
+                    else gx = 0.5f * (tr[x + 1] - tr[x - 1]);
+                    if (y == 0) gy = tr[nx + x] - t;
+                    else if (y == ny - 1) gy = t - tr[x - nx];
+                    else gy = 0.5f * (tr[nx + x] - tr[x - nx]);
+                    const float cs = C.c[s];
+                    v[r0] = gather_px<DET, RESID>(C, A, pb, y, x, cs * gy, cs * gx, s);
+                } else if constexpr (MODE == FWD_SOLVE_LOCAL) {
+                    v[r0] = resid<DET, false>(C, A, pb, (size_t)y * nx + x, s);
+                } else {
+                    v[r0] = __ldg(&A.G[pb + (size_t)y * nx + x]);
+                }
+                if constexpr (MODE != FWD_LOAD) {
+                    if (sl == 0) {
+                        const size_t q = (size_t)y * nx + x;
+                        float r;
+                        if constexpr (RESID) r = __ldg(&A.P[pb + q]);
+                        else r = __ldg(&A.D[pb + q]) - ldP<DET>(A.P, A.Pq, pb + q);
+                        ra += r * r;
+                    }
+                }
             }
-            zs[pm[k] * sm + x] = make_float2(v0, v1);
+            zs[eprfft::pidx(m * sm + x)] = make_float2(v[0], v[1]);
         }
         __syncthreads();
         eprfft::fft<-1, kEPT>(zs, nx, A.lgRP, 1, sm, A.tw, T, tid);
         // epilogue: unpack the two real spectra and store k < nx/2
         float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * half;
+        const float inv_half = 1.f / (float)half;
         for (int e = tid; e < RP * half; e += T) {
-            const int m = e / half, k = e - m * half;
+            const int m = RP == 1 ? 0 : fdiv(e, inv_half);
+            const int k = e - m * half;
             const int y0 = yb + 2 * m;
-            const float2* z = zs + m * sm;
+            const int zb = m * sm;
             float2 X0, X1;
             if (k == 0) {
-                const float2 z0 = z[0], zn = z[half];
+                const float2 z0 = zs[eprfft::pidx(zb)], zn = zs[eprfft::pidx(zb + half)];
                 X0 = make_float2(z0.x, zn.x);
                 X1 = make_float2(z0.y, zn.y);
             } else {
-                const float2 a = z[k], bb = cconj(z[nx - k]);
+                const float2 a = zs[eprfft::pidx(zb + k)], bb = cconj(zs[eprfft::pidx(zb + nx - k)]);
                 const float2 sp = cadd(a, bb), df = csub(a, bb);
                 X0 = make_float2(0.5f * sp.x, 0.5f * sp.y);
                 X1 = make_float2(0.5f * df.y, -0.5f * df.x);
@@ -237,12 +219,14 @@ __global__ void __launch_bounds__(512) k_row_fwd(const EprConsts C, const RowArg
     }
 
     if constexpr (MODE != FWD_LOAD) {
+        float rb = 0.f;
         block_sum2(ra, rb, red);
         double sa, sb;
         if (last_block_reduce(&A.st[b].cnt_fwd, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
                               A.part_b + (size_t)b * A.max_blocks, blockIdx.x, ra, rb, sa, sb)) {
             if (threadIdx.x == 0) {
-                const double rho = sb > 0.0 ? sqrt(sa / sb) : sqrt(sa);
+                const double dn = A.st[b].dnorm2;
+                const double rho = dn > 0.0 ? sqrt(sa / dn) : sqrt(sa);
                 A.st[b].rho = (float)rho;
                 if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = rho;
             }
@@ -250,8 +234,22 @@ __global__ void __launch_bounds__(512) k_row_fwd(const EprConsts C, const RowArg
     }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(512) k_row_inv(const EprConsts C, const RowArgs A)
+// ln(I'_s / (f_s exp(-mu_s t))) for the update of one pixel and line
+__device__ __forceinline__ float log_ratio(float t, float h, float fs, float mus, float omega,
+                                           float eps)
+{
+    const float E = __expf(-mus * t);          // I_s / f_s
+    const float add = omega * h / fs;          // omega h_s / f_s
+    const float v = E + add;                   // I'_s / f_s before the floor
+    if (v >= eps) {
+        const float q = add / E;
+        return (fabsf(q) < 0.5f) ? log1pf(q) : (logf(v) + mus * t);
+    }
+    return logf(eps) + mus * t;
+}
+
+template <int MODE, int NS>
+__global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const RowArgs A)
 {
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
@@ -263,89 +261,83 @@ __global__ void __launch_bounds__(512) k_row_inv(const EprConsts C, const RowArg
     const size_t npix = (size_t)nx * ny;
     const size_t pb = (size_t)b * npix;
     const int yb = blockIdx.x * RP * 2;
+    const int nl = NS ? NS : A.nl;
+    float* acc = reinterpret_cast<float*>(zs + ((eprfft::padded_len(RP * sm) + 1) & ~1));  // [2 RP][nx]
+    const float inv_nx = 1.f / (float)nx, inv_half = 1.f / (float)half;
+    float da = 0.f, db = 0.f;
 
-    int px[kEPT], pm[kEPT];
-    float t0[kEPT], t1[kEPT], a0[kEPT], a1[kEPT];
-#pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        const int e = tid + k * T;
-        pm[k] = e / nx;
-        px[k] = e - pm[k] * nx;
-        a0[k] = 0.f;
-        a1[k] = 0.f;
-        if constexpr (MODE == INV_UPDATE) {
-            const size_t q0 = (size_t)(yb + 2 * pm[k]) * nx + px[k];
-            t0[k] = A.Out[pb + q0];
-            t1[k] = A.Out[pb + q0 + nx];
-        }
-    }
-
-    for (int sl = 0; sl < A.nl; ++sl) {
+    for (int sl = 0; sl < nl; ++sl) {
         const int s = A.line0 + sl;
         const float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * half;
         // unpack Z[k] = X0[k] + i X1[k] over the full row
         for (int e = tid; e < RP * half; e += T) {
-            const int m = e / half, k = e - m * half;
+            const int m = RP == 1 ? 0 : fdiv(e, inv_half);
+            const int k = e - m * half;
             const int y0 = yb + 2 * m;
             const float2 s0 = Sb[(size_t)y0 * half + k];
             const float2 s1 = Sb[(size_t)(y0 + 1) * half + k];
-            float2* z = zs + m * sm;
+            const int zb = m * sm;
             if (k == 0) {
-                z[0] = make_float2(s0.x, s1.x);
-                z[half] = make_float2(s0.y, s1.y);
+                zs[eprfft::pidx(zb)] = make_float2(s0.x, s1.x);
+                zs[eprfft::pidx(zb + half)] = make_float2(s0.y, s1.y);
             } else {
-                z[k] = make_float2(s0.x - s1.y, s0.y + s1.x);
-                z[nx - k] = make_float2(s0.x + s1.y, s1.x - s0.y);
+                zs[eprfft::pidx(zb + k)] = make_float2(s0.x - s1.y, s0.y + s1.x);
+                zs[eprfft::pidx(zb + nx - k)] = make_float2(s0.x + s1.y, s1.x - s0.y);
             }
         }
         __syncthreads();
         eprfft::fft<+1, kEPT>(zs, nx, A.lgRP, 1, sm, A.tw, T, tid);
-#pragma unroll
+#pragma unroll 2
         for (int k = 0; k < kEPT; ++k) {
-            const float2 h = zs[pm[k] * sm + px[k]];
+            const int e = tid + k * T;
+            const int m = RP == 1 ? 0 : fdiv(e, inv_nx);
+            const int x = e - m * nx;
+            const float2 h = zs[eprfft::pidx(m * sm + x)];
+            const size_t q0 = pb + (size_t)(yb + 2 * m) * nx + x;
             if constexpr (MODE == INV_UPDATE) {
-                // ln of the updated line intensity relative to f_s exp(-mu_s T)
-                const float fs = C.f[s], mus = C.mu[s];
-                float lr[2];
-                const float hv[2] = {h.x, h.y}, tv[2] = {t0[k], t1[k]};
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const float E = __expf(-mus * tv[r]);          // I_s / f_s
-                    const float add = A.omega * hv[r] / fs;         // omega h_s / f_s
-                    const float v = E + add;                        // I'_s / f_s before the floor
-                    if (v >= A.eps) {
-                        const float q = add / E;
-                        lr[r] = (fabsf(q) < 0.5f) ? log1pf(q) : (logf(v) + mus * tv[r]);
+                const float fs = C.f[s], mus = C.mu[s], w = C.wproj[s];
+                const float t0 = A.Out[q0], t1 = A.Out[q0 + nx];
+                const float l0 = w * log_ratio(t0, h.x, fs, mus, A.omega, A.eps);
+                const float l1 = w * log_ratio(t1, h.y, fs, mus, A.omega, A.eps);
+                if (nl == 1) {
+                    const float n0 = t0 - l0, n1 = t1 - l1;
+                    A.Out[q0] = n0;
+                    A.Out[q0 + nx] = n1;
+                    da += l0 * l0 + l1 * l1;
+                    db += n0 * n0 + n1 * n1;
+                } else {
+                    float* a0 = acc + (2 * m) * nx + x;
+                    if (sl == 0) {
+                        a0[0] = l0;
+                        a0[nx] = l1;
                     } else {
-                        lr[r] = logf(A.eps) + mus * tv[r];
+                        a0[0] += l0;
+                        a0[nx] += l1;
                     }
                 }
-                a0[k] += C.wproj[s] * lr[0];
-                a1[k] += C.wproj[s] * lr[1];
             } else {
-                a0[k] = h.x;
-                a1[k] = h.y;
+                A.Out[q0] = h.x;
+                A.Out[q0 + nx] = h.y;
             }
         }
         __syncthreads();
     }
 
-    float da = 0.f, db = 0.f;
-#pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        const size_t q0 = (size_t)(yb + 2 * pm[k]) * nx + px[k];
-        if constexpr (MODE == INV_UPDATE) {
-            const float n0 = t0[k] - a0[k], n1 = t1[k] - a1[k];
-            A.Out[pb + q0] = n0;
-            A.Out[pb + q0 + nx] = n1;
-            da += a0[k] * a0[k] + a1[k] * a1[k];
-            db += n0 * n0 + n1 * n1;
-        } else {
-            A.Out[pb + q0] = a0[k];
-            A.Out[pb + q0 + nx] = a1[k];
-        }
-    }
     if constexpr (MODE == INV_UPDATE) {
+        if (nl > 1) {
+            for (int k = 0; k < kEPT; ++k) {
+                const int e = tid + k * T;
+                const int m = RP == 1 ? 0 : fdiv(e, inv_nx);
+                const int x = e - m * nx;
+                const size_t q0 = pb + (size_t)(yb + 2 * m) * nx + x;
+                const float l0 = acc[(2 * m) * nx + x], l1 = acc[(2 * m + 1) * nx + x];
+                const float n0 = A.Out[q0] - l0, n1 = A.Out[q0 + nx] - l1;
+                A.Out[q0] = n0;
+                A.Out[q0 + nx] = n1;
+                da += l0 * l0 + l1 * l1;
+                db += n0 * n0 + n1 * n1;
+            }
+        }
         block_sum2(da, db, red);
         double sa, sb;
         if (last_block_reduce(&A.st[b].cnt_inv, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
@@ -359,6 +351,33 @@ __global__ void __launch_bounds__(512) k_row_inv(const EprConsts C, const RowArg
             }
         }
     }
+}
+
+// |D|^2 per projection, deterministic: block partials, then a fixed-order sum
+__global__ void __launch_bounds__(256) k_sumsq_part(const float* __restrict__ D, size_t npix,
+                                                    double* part, int max_blocks)
+{
+    __shared__ float red[64];
+    const int b = blockIdx.y;
+    const float4* Db = reinterpret_cast<const float4*>(D + (size_t)b * npix);
+    const size_t n4 = npix / 4;
+    float a = 0.f, z = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(&Db[i]);
+        a += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+    }
+    block_sum2(a, z, red);
+    if (threadIdx.x == 0) part[(size_t)b * max_blocks + blockIdx.x] = (double)a;
+}
+
+__global__ void k_sumsq_final(const double* part, int nparts, int max_blocks, EprProjState* st)
+{
+    const int b = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += part[(size_t)b * max_blocks + i];
+    st[b].dnorm2 = s;
 }
 
 }  // namespace
@@ -377,14 +396,18 @@ EprRowLaunch epr_row_config(const EprConsts& C)
     L.lgRP = 0;
     while ((1 << L.lgRP) < rp) ++L.lgRP;
     L.threads = C.nx * rp / kEPT;
-    L.smem = (size_t)rp * (C.nx + kPad) * sizeof(float2);
+    // FFT rows, then the staged thickness rows (forward) or line accumulators
+    // (inverse); the larger of the two
+    const size_t extra = (size_t)(2 * rp + 2) * C.nx * sizeof(float);
+    L.smem = (size_t)((eprfft::padded_len(rp * (C.nx + kPad)) + 1) & ~1) * sizeof(float2) + extra;
     return L;
 }
 
-// mode: 0 = non-local solve, 1 = local solve, 2 = load real map G
-cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
-                               const float* D, const float* G, int line0, int nl, int it,
-                               int batch, int check_done, cudaStream_t stream)
+// mode: 0 = non-local solve, 1 = local solve, 2 = load real map G.
+// resid = 1: P holds D - P (mono float solve).
+cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, int resid,
+                               const float* T, const float* D, const float* G, int line0, int nl,
+                               int it, int batch, int check_done, cudaStream_t stream)
 {
     const EprRowLaunch L = epr_row_config(C);
     RowArgs A = {};
@@ -395,14 +418,22 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, c
     A.tw = W.tw_x; A.RP = L.RP; A.lgRP = L.lgRP; A.line0 = line0; A.nl = nl; A.it = it;
     A.check_done = check_done;
     dim3 grid(C.ny / (2 * L.RP), batch);
-    // the local closure writes float maps in both accumulation modes
+    const bool mono = nl == 1;
     if (mode == FWD_SOLVE_NL) {
-        if (C.det) k_row_fwd<FWD_SOLVE_NL, true><<<grid, L.threads, L.smem, stream>>>(C, A);
-        else k_row_fwd<FWD_SOLVE_NL, false><<<grid, L.threads, L.smem, stream>>>(C, A);
+        if (C.det) {
+            if (mono) k_row_fwd<FWD_SOLVE_NL, true, false, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+            else k_row_fwd<FWD_SOLVE_NL, true, false, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
+        } else if (resid && mono) {
+            k_row_fwd<FWD_SOLVE_NL, false, true, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+        } else {
+            if (mono) k_row_fwd<FWD_SOLVE_NL, false, false, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+            else k_row_fwd<FWD_SOLVE_NL, false, false, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
+        }
     } else if (mode == FWD_SOLVE_LOCAL) {
-        k_row_fwd<FWD_SOLVE_LOCAL, false><<<grid, L.threads, L.smem, stream>>>(C, A);
+        // the local closure writes float maps in both accumulation modes
+        k_row_fwd<FWD_SOLVE_LOCAL, false, false, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
     } else {
-        k_row_fwd<FWD_LOAD, false><<<grid, L.threads, L.smem, stream>>>(C, A);
+        k_row_fwd<FWD_LOAD, false, false, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
     }
     epr_count_launch(1);
     return cudaGetLastError();
@@ -420,19 +451,39 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
     A.tw = W.tw_x; A.RP = L.RP; A.lgRP = L.lgRP; A.line0 = line0; A.nl = nl; A.it = it;
     A.omega = omega; A.eps = eps; A.tol = tol; A.check_done = check_done;
     dim3 grid(C.ny / (2 * L.RP), batch);
-    if (mode == INV_UPDATE) k_row_inv<INV_UPDATE><<<grid, L.threads, L.smem, stream>>>(C, A);
-    else k_row_inv<INV_STORE><<<grid, L.threads, L.smem, stream>>>(C, A);
+    if (mode == INV_UPDATE) {
+        if (nl == 1) k_row_inv<INV_UPDATE, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+        else k_row_inv<INV_UPDATE, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
+    } else {
+        k_row_inv<INV_STORE, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+    }
     epr_count_launch(1);
+    return cudaGetLastError();
+}
+
+// |D|^2 of each projection into the solver state (two small launches).
+cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* D, int batch,
+                             cudaStream_t stream)
+{
+    const int parts = W.max_blocks < 64 ? W.max_blocks : 64;
+    const size_t npix = (size_t)C.nx * C.ny;
+    k_sumsq_part<<<dim3(parts, batch), 256, 0, stream>>>(D, npix, W.part_a, W.max_blocks);
+    k_sumsq_final<<<batch, 32, 0, stream>>>(W.part_a, parts, W.max_blocks, W.st);
+    epr_count_launch(2);
     return cudaGetLastError();
 }
 
 cudaError_t epr_row_init()
 {
-    cudaError_t e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, true>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, false>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_LOCAL, false>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_LOAD, false>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_STORE>);
+    cudaError_t e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, true, false, 1>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, true, false, 0>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, false, true, 1>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, false, false, 1>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, false, false, 0>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_LOCAL, false, false, 0>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_LOAD, false, false, 1>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 1>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 0>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_STORE, 1>);
     return e;
 }

@@ -7,9 +7,10 @@
 //  * A block owns one TH x TW destination tile of one projection and holds
 //    its accumulators (one per line) in shared memory.
 //  * It scans every source pixel whose shifted corners can land in the tile:
-//    the tile grown by R = smax + 1 pixels on each side.  The thickness of
+//    the tile grown by R = reach + 1 pixels on each side.  The thickness of
 //    that region plus a one-pixel ring (for the gradient) is staged in shared
-//    memory with coalesced loads.
+//    memory with coalesced loads.  Blocks whose staged region lies inside the
+//    grid take a path without edge tests.
 //  * Per source and line it forms the shift u = c_s G[T] (central
 //    differences, one-sided at the grid edges), splits u into floor and
 //    fraction (the integer pixel index never passes through float), and adds
@@ -17,16 +18,18 @@
 //    the tile with shared-memory atomics.  exp is evaluated only when the
 //    source reaches the tile.
 //  * Every destination pixel is written exactly once, with plain coalesced
-//    stores: no zero fill and no global atomics on the fast path.
-//  * A source-line with |u| > smax in either axis is never splatted by the
+//    stores: no zero fill and no global atomics on the fast path.  In the
+//    monochromatic float solve the flush stores the residual D - P instead
+//    of P (the adjoint gather then reads one value per corner).
+//  * A source-line with |u| > reach in either axis is never splatted by the
 //    scan; the block that owns the source pixel appends it (with a bit mask
-//    of its long lines) to a per-projection overflow list.  The last block of
-//    the projection to finish (arrival counter after a memory fence) adds
-//    those contributions with global atomics, so no mass is lost whatever
-//    the shift.
-//  * Fixed-point mode accumulates round(v * 2^40) in uint64 (all
-//    contributions are non-negative) in shared and global memory: integer
-//    addition is associative, so the result is bit-identical across runs.
+//    of its long lines) to a per-projection overflow list, and a second
+//    kernel adds those contributions with global atomics.  No mass is lost,
+//    whatever the shift.  The list fill counter alternates between two slots
+//    by iteration parity, so the overflow kernel can clear the next slot.
+//  * Fixed-point mode accumulates round(v * 2^40) in uint64 (contributions
+//    are non-negative) in shared and global memory: integer addition is
+//    associative, so the result is bit-identical across runs.
 #include "epr_internal.cuh"
 
 namespace {
@@ -35,7 +38,8 @@ constexpr int kSplatThreads = 256;
 
 struct SplatArgs {
     const float* T;          // [B][ny][nx]
-    float* P;                // [B][ny][nx]          (float mode)
+    const float* D;          // [B][ny][nx] (residual output)
+    float* P;                // [B][ny][nx]   P, or D - P (residual output)
     float* Ps;               // [B][ns][ny][nx] or NULL (float mode, ns > 1)
     unsigned long long* Pq;  // fixed-point mode
     unsigned long long* Psq;
@@ -43,7 +47,7 @@ struct SplatArgs {
     unsigned int* ovf_mask;
     EprProjState* st;
     unsigned int* err;
-    int TH, TW, tiles_x, tiles_y;
+    int TH, TW, lgTW, parity;
     int check_done;
 };
 
@@ -54,6 +58,9 @@ __device__ __forceinline__ float grad1(float lo, float mid, float hi, int i, int
     if (i == n - 1) return mid - lo;
     return 0.5f * (hi - lo);
 }
+
+// i / d for 0 <= i < 2^20 and d < 2^12 without an integer division
+__device__ __forceinline__ int fdiv(int i, float inv_d) { return (int)(((float)i + 0.5f) * inv_d); }
 
 template <bool DET>
 __device__ __forceinline__ void acc_add(void* acc, int idx, float v)
@@ -66,14 +73,16 @@ __device__ __forceinline__ void acc_add(void* acc, int idx, float v)
     }
 }
 
-template <bool DET>
+// NS = 1: single line known at compile time; NS = 0: C.ns lines.
+template <int NS, bool DET, bool RESID>
 __global__ void __launch_bounds__(kSplatThreads)
 k_splat(const EprConsts C, const SplatArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int b = blockIdx.z;
     if (A.check_done && A.st[b].done) return;
-    const int nx = C.nx, ny = C.ny, ns = C.ns;
+    const int nx = C.nx, ny = C.ny;
+    const int ns = NS ? NS : C.ns;
     const int TH = A.TH, TW = A.TW;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     const int R = C.smax + 1;
@@ -81,121 +90,138 @@ k_splat(const EprConsts C, const SplatArgs A)
     const int SH = RH + 2, SW = RW + 2;              // staged thickness
     const int tile = TH * TW;
     const size_t npix = (size_t)nx * ny;
+    const int tid = threadIdx.x;
 
-    // shared layout: accumulators [ns][TH][TW], then thickness [SH][SW]
     void* acc = smem;
     const size_t acc_bytes = (size_t)ns * tile * (DET ? 8 : 4);
     float* Ts = reinterpret_cast<float*>(smem + ((acc_bytes + 15) & ~size_t(15)));
     const float* Tb = A.T + (size_t)b * npix;
 
-    // stage thickness rows ty0-R-1 .. ty0+TH+R and cols tx0-R-1 .. tx0+TW+R
     const int sy0 = ty0 - R - 1, sx0 = tx0 - R - 1;
-    for (int i = threadIdx.x; i < SH * SW; i += kSplatThreads) {
-        const int ly = i / SW, lx = i - ly * SW;
-        const int gy = sy0 + ly, gx = sx0 + lx;
-        float v = 0.f;
-        if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) v = __ldg(&Tb[(size_t)gy * nx + gx]);
-        Ts[i] = v;
+    const bool interior = sy0 >= 0 && sx0 >= 0 && sy0 + SH <= ny && sx0 + SW <= nx;
+    const float inv_SW = 1.f / (float)SW, inv_RW = 1.f / (float)RW;
+    if (interior) {
+        for (int i = tid; i < SH * SW; i += kSplatThreads) {
+            const int ly = fdiv(i, inv_SW), lx = i - ly * SW;
+            Ts[i] = __ldg(&Tb[(size_t)(sy0 + ly) * nx + sx0 + lx]);
+        }
+    } else {
+        for (int i = tid; i < SH * SW; i += kSplatThreads) {
+            const int ly = fdiv(i, inv_SW), lx = i - ly * SW;
+            const int gy = sy0 + ly, gx = sx0 + lx;
+            float v = 0.f;
+            if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) v = __ldg(&Tb[(size_t)gy * nx + gx]);
+            Ts[i] = v;
+        }
     }
     if constexpr (DET) {
         unsigned long long* a = reinterpret_cast<unsigned long long*>(acc);
-        for (int i = threadIdx.x; i < ns * tile; i += kSplatThreads) a[i] = 0ull;
+        for (int i = tid; i < ns * tile; i += kSplatThreads) a[i] = 0ull;
     } else {
-        float* a = reinterpret_cast<float*>(acc);
-        for (int i = threadIdx.x; i < ns * tile; i += kSplatThreads) a[i] = 0.f;
+        float4* a = reinterpret_cast<float4*>(acc);
+        for (int i = tid; i < ns * tile / 4; i += kSplatThreads) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 
     const float fsmax = (float)C.smax;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int ly = warp; ly < RH; ly += kSplatThreads / 32) {
-        const int sy = ty0 - R + ly;
-        if (sy < 0 || sy >= ny) continue;
-        for (int lx = lane; lx < RW; lx += 32) {
-            const int sx = tx0 - R + lx;
-            if (sx < 0 || sx >= nx) continue;
-            const float* tp = Ts + (ly + 1) * SW + (lx + 1);
-            const float t = tp[0];
-            const float gx = grad1(tp[-1], t, tp[1], sx, nx);
-            const float gy = grad1(tp[-SW], t, tp[SW], sy, ny);
-            const bool own = (ly >= R) && (ly < R + TH) && (lx >= R) && (lx < R + TW);
-            unsigned int far = 0u;
-            for (int s = 0; s < ns; ++s) {
-                const float ux = C.c[s] * gx, uy = C.c[s] * gy;
-                if (!(fabsf(ux) <= fsmax && fabsf(uy) <= fsmax)) {
-                    far |= 1u << s;
-                    continue;
-                }
-                const float fx = floorf(ux), fy = floorf(uy);
-                const float dx = ux - fx, dy = uy - fy;
-                const int cx = sx + (int)fx - tx0, cy = sy + (int)fy - ty0;  // corner 00, tile-local
-                if (cx < -1 || cx >= TW || cy < -1 || cy >= TH) continue;
-                const float m = C.f[s] * __expf(-C.mu[s] * t);
-                const float w00 = (1.f - dx) * (1.f - dy), w10 = dx * (1.f - dy);
-                const float w01 = (1.f - dx) * dy, w11 = dx * dy;
-                const int base = s * tile;
-                const bool x0in = cx >= 0, x1in = cx + 1 < TW;
-                const bool y0in = cy >= 0, y1in = cy + 1 < TH;
-                if (y0in && x0in) acc_add<DET>(acc, base + cy * TW + cx, m * w00);
-                if (y0in && x1in) acc_add<DET>(acc, base + cy * TW + cx + 1, m * w10);
-                if (y1in && x0in) acc_add<DET>(acc, base + (cy + 1) * TW + cx, m * w01);
-                if (y1in && x1in) acc_add<DET>(acc, base + (cy + 1) * TW + cx + 1, m * w11);
+    const int nsrc = RH * RW;
+    for (int i = tid; i < nsrc; i += kSplatThreads) {
+        const int ly = fdiv(i, inv_RW), lx = i - ly * RW;
+        const int sy = ty0 - R + ly, sx = tx0 - R + lx;
+        const float* tp = Ts + (ly + 1) * SW + (lx + 1);
+        const float t = tp[0];
+        float gx, gy;
+        if (interior) {
+            gx = 0.5f * (tp[1] - tp[-1]);
+            gy = 0.5f * (tp[SW] - tp[-SW]);
+        } else {
+            if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) continue;
+            gx = grad1(tp[-1], t, tp[1], sx, nx);
+            gy = grad1(tp[-SW], t, tp[SW], sy, ny);
+        }
+        unsigned int far = 0u;
+#pragma unroll(NS ? NS : 1)
+        for (int s = 0; s < ns; ++s) {
+            const float cs = C.c[s];
+            const float ux = cs * gx, uy = cs * gy;
+            if (!(fabsf(ux) <= fsmax && fabsf(uy) <= fsmax)) {
+                far |= 1u << s;
+                continue;
             }
-            if (far && own) {
-                const int pos = atomicAdd(&A.st[b].ovf_count, 1);
-                if (pos < C.ovf_cap) {
-                    A.ovf_idx[(size_t)b * C.ovf_cap + pos] = sy * nx + sx;
-                    A.ovf_mask[(size_t)b * C.ovf_cap + pos] = far;
-                } else {
-                    atomicOr(A.err, EPR_DEVERR_OVERFLOW);
-                }
+            const float fx = floorf(ux), fy = floorf(uy);
+            const float dx = ux - fx, dy = uy - fy;
+            const int cx = lx - R + (int)fx, cy = ly - R + (int)fy;  // corner 00, tile-local
+            if ((unsigned)(cx + 1) > (unsigned)TW || (unsigned)(cy + 1) > (unsigned)TH) continue;
+            const float m = C.f[s] * __expf(-C.mu[s] * t);
+            const float mx1 = m * dx, mx0 = m - mx1;          // m (1 - dx), m dx
+            const int idx = s * tile + cy * TW + cx;
+            if (cy >= 0) {
+                const float w = 1.f - dy;
+                if (cx >= 0) acc_add<DET>(acc, idx, mx0 * w);
+                if (cx + 1 < TW) acc_add<DET>(acc, idx + 1, mx1 * w);
+            }
+            if (cy + 1 < TH) {
+                if (cx >= 0) acc_add<DET>(acc, idx + TW, mx0 * dy);
+                if (cx + 1 < TW) acc_add<DET>(acc, idx + TW + 1, mx1 * dy);
+            }
+        }
+        if (far && (unsigned)(ly - R) < (unsigned)TH && (unsigned)(lx - R) < (unsigned)TW) {
+            const int pos = atomicAdd(&A.st[b].ovf_count[A.parity], 1);
+            if (pos < C.ovf_cap) {
+                A.ovf_idx[(size_t)b * C.ovf_cap + pos] = sy * nx + sx;
+                A.ovf_mask[(size_t)b * C.ovf_cap + pos] = far;
+            } else {
+                atomicOr(A.err, EPR_DEVERR_OVERFLOW);
             }
         }
     }
     __syncthreads();
 
     // flush: every pixel of the tile inside the grid, once, coalesced
-    for (int i = threadIdx.x; i < tile; i += kSplatThreads) {
-        const int ly = i / TW, lx = i - ly * TW;
+    for (int i = tid; i < tile; i += kSplatThreads) {
+        const int ly = i >> A.lgTW, lx = i & (TW - 1);
         const int gy = ty0 + ly, gx = tx0 + lx;
         if (gy >= ny || gx >= nx) continue;
-        const size_t o = (size_t)gy * nx + gx;
+        const size_t o = (size_t)b * npix + (size_t)gy * nx + gx;
         if constexpr (DET) {
             const unsigned long long* a = reinterpret_cast<const unsigned long long*>(acc);
             unsigned long long sum = 0ull;
             for (int s = 0; s < ns; ++s) {
                 const unsigned long long q = a[s * tile + i];
                 sum += q;
-                if (ns > 1) A.Psq[((size_t)b * ns + s) * npix + o] = q;
+                if (ns > 1) A.Psq[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = q;
             }
-            A.Pq[(size_t)b * npix + o] = sum;
+            A.Pq[o] = sum;
         } else {
             const float* a = reinterpret_cast<const float*>(acc);
             float sum = 0.f;
             for (int s = 0; s < ns; ++s) {
                 const float q = a[s * tile + i];
                 sum += q;
-                if (ns > 1) A.Ps[((size_t)b * ns + s) * npix + o] = q;
+                if (ns > 1) A.Ps[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = q;
             }
-            A.P[(size_t)b * npix + o] = sum;
+            if constexpr (RESID) A.P[o] = __ldg(&A.D[o]) - sum;
+            else A.P[o] = sum;
         }
     }
+}
 
-    // last block of this projection adds the overflow list
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int nblk = (unsigned int)(A.tiles_x * A.tiles_y);
-        const unsigned int prev = atomicAdd(&A.st[b].cnt_splat, 1u);
-        s_last = (prev == nblk - 1u);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const int cnt_raw = *((volatile int*)&A.st[b].ovf_count);
+// The long-shift sources of the overflow list, added with global atomics.
+template <bool DET, bool RESID>
+__global__ void __launch_bounds__(256) k_splat_overflow(const EprConsts C, const SplatArgs A)
+{
+    const int b = blockIdx.y;
+    if (A.check_done && A.st[b].done) return;
+    const int nx = C.nx, ny = C.ny, ns = C.ns;
+    const size_t npix = (size_t)nx * ny;
+    const int cnt_raw = A.st[b].ovf_count[A.parity];
     const int cnt = cnt_raw < C.ovf_cap ? cnt_raw : C.ovf_cap;
-    for (int e = threadIdx.x; e < cnt; e += kSplatThreads) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.st[b].ovf_count[A.parity ^ 1] = 0;   // the next splat's slot
+        if (cnt > 0) A.st[b].ovf_total += cnt;
+    }
+    const float* Tb = A.T + (size_t)b * npix;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
         const int pix = A.ovf_idx[(size_t)b * C.ovf_cap + e];
         const unsigned int mask = A.ovf_mask[(size_t)b * C.ovf_cap + e];
         const int sy = pix / nx, sx = pix - sy * nx;
@@ -221,6 +247,8 @@ k_splat(const EprConsts C, const SplatArgs A)
                     const unsigned long long q = (unsigned long long)__float2ll_rn(v * EPR_FX_SCALE);
                     atomicAdd(&A.Pq[(size_t)b * npix + o], q);
                     if (ns > 1) atomicAdd(&A.Psq[((size_t)b * ns + s) * npix + o], q);
+                } else if constexpr (RESID) {
+                    atomicAdd(&A.P[(size_t)b * npix + o], -v);
                 } else {
                     atomicAdd(&A.P[(size_t)b * npix + o], v);
                     if (ns > 1) atomicAdd(&A.Ps[((size_t)b * ns + s) * npix + o], v);
@@ -228,24 +256,35 @@ k_splat(const EprConsts C, const SplatArgs A)
             }
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (cnt > 0) A.st[b].ovf_total += cnt;
-        A.st[b].ovf_count = 0;
-        A.st[b].cnt_splat = 0u;
-        __threadfence();
-    }
+}
+
+template <int NS, bool DET, bool RESID>
+void launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
+              cudaStream_t stream)
+{
+    k_splat<NS, DET, RESID><<<grid, kSplatThreads, smem, stream>>>(C, A);
+    k_splat_overflow<DET, RESID><<<dim3(32, batch), 256, 0, stream>>>(C, A);
 }
 
 }  // namespace
 
-// Host launcher.  TH x TW is the destination tile; shared memory =
-// ns * TH * TW accumulators + (TH + 2R + 2)(TW + 2R + 2) floats.
-cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* T, int batch,
-                             int TH, int TW, int check_done, cudaStream_t stream)
+size_t epr_splat_smem(const EprConsts& C, int TH, int TW)
+{
+    const int R = C.smax + 1;
+    const size_t acc_bytes = (size_t)C.ns * TH * TW * (C.det ? 8 : 4);
+    return ((acc_bytes + 15) & ~size_t(15)) + (size_t)(TH + 2 * R + 2) * (TW + 2 * R + 2) * sizeof(float);
+}
+
+// Host launcher: the tile kernel, then the overflow kernel (2 launches).
+// resid = 1 (mono float only): P receives D - P.  `parity` alternates the
+// overflow counter slot between consecutive splats of a solve.
+cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* T, const float* D,
+                             int resid, int parity, int batch, int TH, int TW, int check_done,
+                             cudaStream_t stream)
 {
     SplatArgs A;
     A.T = T;
+    A.D = D;
     A.P = W.P;
     A.Ps = W.Ps;
     A.Pq = W.Pq;
@@ -256,30 +295,32 @@ cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* 
     A.err = W.err;
     A.TH = TH;
     A.TW = TW;
-    A.tiles_x = (C.nx + TW - 1) / TW;
-    A.tiles_y = (C.ny + TH - 1) / TH;
+    A.lgTW = 0;
+    while ((1 << A.lgTW) < TW) ++A.lgTW;
+    A.parity = parity & 1;
     A.check_done = check_done;
-    const int R = C.smax + 1;
-    const size_t acc_bytes = (size_t)C.ns * TH * TW * (C.det ? 8 : 4);
-    const size_t smem = ((acc_bytes + 15) & ~size_t(15)) +
-                        (size_t)(TH + 2 * R + 2) * (TW + 2 * R + 2) * sizeof(float);
-    dim3 grid(A.tiles_x, A.tiles_y, batch);
-    if (C.det) k_splat<true><<<grid, kSplatThreads, smem, stream>>>(C, A);
-    else k_splat<false><<<grid, kSplatThreads, smem, stream>>>(C, A);
-    epr_count_launch(1);
+    const size_t smem = epr_splat_smem(C, TH, TW);
+    dim3 grid((C.nx + TW - 1) / TW, (C.ny + TH - 1) / TH, batch);
+    const bool mono = C.ns == 1;
+    if (C.det) {
+        if (mono) launch_t<1, true, false>(C, A, grid, smem, batch, stream);
+        else launch_t<0, true, false>(C, A, grid, smem, batch, stream);
+    } else if (resid && mono) {
+        launch_t<1, false, true>(C, A, grid, smem, batch, stream);
+    } else {
+        if (mono) launch_t<1, false, false>(C, A, grid, smem, batch, stream);
+        else launch_t<0, false, false>(C, A, grid, smem, batch, stream);
+    }
+    epr_count_launch(2);
     return cudaGetLastError();
-}
-
-size_t epr_splat_smem(const EprConsts& C, int TH, int TW)
-{
-    const int R = C.smax + 1;
-    const size_t acc_bytes = (size_t)C.ns * TH * TW * (C.det ? 8 : 4);
-    return ((acc_bytes + 15) & ~size_t(15)) + (size_t)(TH + 2 * R + 2) * (TW + 2 * R + 2) * sizeof(float);
 }
 
 cudaError_t epr_splat_init()
 {
-    cudaError_t e = epr_allow_max_smem(k_splat<true>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<false>);
+    cudaError_t e = epr_allow_max_smem(k_splat<1, true, false>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, true, false>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, false>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false>);
     return e;
 }

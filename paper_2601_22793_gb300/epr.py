@@ -37,7 +37,10 @@ EPR_MODEL_LOCAL2 = 2
 
 SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
            "epr_precondition", "epr_solve_nonlocal", "epr_solve_local",
-           "epr_check_device_status", "epr_status_string", "epr_launch_count")
+           "epr_check_device_status", "epr_status_string", "epr_launch_count",
+           "epr_profile_enable", "epr_profile_read")
+
+KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 
 
 class epr_options(ctypes.Structure):
@@ -100,6 +103,10 @@ def load(path: str | None = None):
         lib.epr_check_device_status.restype = i
         lib.epr_status_string.argtypes = [i]
         lib.epr_status_string.restype = ctypes.c_char_p
+        lib.epr_profile_enable.argtypes = [vp, i]
+        lib.epr_profile_enable.restype = i
+        lib.epr_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
+        lib.epr_profile_read.restype = i
         lib.epr_launch_count.argtypes = []
         lib.epr_launch_count.restype = ctypes.c_longlong
         _lib = lib
@@ -153,7 +160,7 @@ def _darr(x):
 
 
 def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
-                    max_shift_px=12, deterministic=False, overflow_capacity=0, use_graphs=True):
+                    max_shift_px=4, deterministic=False, overflow_capacity=0, use_graphs=True):
     """Returns an opaque plan handle (int)."""
     lib = load()
     E, Ep = _darr(energy_keV)
@@ -235,6 +242,19 @@ def epr_solve_local(plan, D, T, batch=1, order=2, n_iter=20, omega=1.0, tol=0.0,
 
 def epr_check_device_status(plan, stream=None):
     _check(load().epr_check_device_status(plan, _stream(stream)), "epr_check_device_status")
+
+
+def epr_profile_enable(plan, enable=True):
+    _check(load().epr_profile_enable(plan, int(bool(enable))), "epr_profile_enable")
+
+
+def epr_profile_read(plan):
+    """{kind: (launches, total_ms)} since the last read (synchronises)."""
+    n = len(KERNEL_KINDS)
+    cnt = (ctypes.c_int * n)()
+    ms = (ctypes.c_double * n)()
+    _check(load().epr_profile_read(plan, cnt, ms), "epr_profile_read")
+    return {k: (int(cnt[i]), float(ms[i])) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def epr_launch_count() -> int:
