@@ -154,6 +154,25 @@ epr_status epr_solve_local(epr_plan_t plan, const float* D, float* T, int batch,
  * overflow list (its prediction then lacks those sources), else EPR_OK. */
 epr_status epr_check_device_status(epr_plan_t plan, void* stream);
 
+/* Paganin-type preconditioner of one line without a plan and without any
+ * device allocation: g <- Re F^-1[H F[g]] in place for `batch` maps of
+ * nx x ny (the operation of epr_precondition, for a single line with the
+ * given energy, delta and beta; L_m and pixel_m as for a plan).  The paper
+ * has no counterpart: this serves callers that cannot let a library call
+ * cudaMalloc (their device memory is owned by their own pool allocator or
+ * fixed at start-up, or an allocation's possible device synchronisation is
+ * not acceptable).  Scratch lives in a static device array of 16 MiB + 64 KiB
+ * that every GPU loading the library holds until the process exits; it
+ * bounds batch * nx * ny to 4 Mi pixels (e.g. one 2048 x 2048 map), and a
+ * larger request returns EPR_ERR_UNSUPPORTED_SIZE.  The first call on each
+ * device performs a one-time set-up (the array's device address and kernel
+ * attributes); make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU race.  g is device
+ * memory, 16-byte aligned. */
+epr_status epr_precondition_noalloc(float* g, int nx, int ny, double pixel_m, double L_m,
+                                    double energy_keV, double delta, double beta, int batch,
+                                    void* stream);
+
 /* Kernel kinds reported by epr_profile_read. */
 typedef enum {
     EPR_KERNEL_SPLAT = 0,    /* forward transport (bilinear redistribution)   */

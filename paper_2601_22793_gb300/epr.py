@@ -38,7 +38,7 @@ EPR_MODEL_LOCAL2 = 2
 SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
            "epr_precondition", "epr_solve_nonlocal", "epr_solve_local",
            "epr_check_device_status", "epr_status_string", "epr_launch_count",
-           "epr_profile_enable", "epr_profile_read")
+           "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc")
 
 KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 
@@ -107,6 +107,8 @@ def load(path: str | None = None):
         lib.epr_profile_enable.restype = i
         lib.epr_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
         lib.epr_profile_read.restype = i
+        lib.epr_precondition_noalloc.argtypes = [vp, i, i, d, d, d, d, d, i, vp]
+        lib.epr_precondition_noalloc.restype = i
         lib.epr_launch_count.argtypes = []
         lib.epr_launch_count.restype = ctypes.c_longlong
         _lib = lib
@@ -192,6 +194,16 @@ def epr_adjoint(plan, T, r, g, line=0, batch=1, stream=None):
 def epr_precondition(plan, g, line=0, batch=1, stream=None):
     _check(load().epr_precondition(plan, _ptr(g), int(line), int(batch), _stream(stream)),
            "epr_precondition")
+
+
+def epr_precondition_noalloc(g, nx, ny, pixel_m, L_m, energy_keV, delta, beta, batch=1,
+                             stream=None):
+    """Plan-free preconditioner of one line that allocates no device memory
+    (scratch in a static device array; batch * nx * ny <= 4 Mi pixels)."""
+    _check(load().epr_precondition_noalloc(_ptr(g), int(nx), int(ny), float(pixel_m), float(L_m),
+                                           float(energy_keV), float(delta), float(beta),
+                                           int(batch), _stream(stream)),
+           "epr_precondition_noalloc")
 
 
 def _solve_opts(n_iter, omega, tol, eps_I, init):
