@@ -17,6 +17,8 @@
 
 namespace {
 
+using PC = eprfft::PadCol;  // shared layout of the column tile
+
 struct ColArgs {
     float2* S;            // [B][nl][ny][nx/2]
     const EprProjState* st;
@@ -40,10 +42,10 @@ __global__ void __launch_bounds__(512, 2) k_col(const EprConsts C, const ColArgs
 
     for (int e = tid; e < ny * CW; e += T) {
         const int y = e >> lgCW, c = e & (CW - 1);
-        buf[eprfft::pidx(e)] = Sb[(size_t)y * half + kx0 + c];
+        buf[PC::idx(e)] = Sb[(size_t)y * half + kx0 + c];
     }
     __syncthreads();
-    eprfft::fft<-1, EPT>(buf, ny, lgCW, CW, 1, A.tw, T, tid);
+    eprfft::fft<PC, -1, EPT>(buf, ny, lgCW, CW, 1, A.tw, T, tid);
 
     // filter (two phases: column 0 reads the mirrored frequency)
     const float ha = C.ha[s], hb = C.hb[s], inv_n = C.inv_n;
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(512, 2) k_col(const EprConsts C, const ColArgs
         const int kx = kx0 + c;
         const float ky = (float)(y <= ny / 2 ? y : y - ny);
         const float qy = hb * ky * ky;
-        const float2 v = buf[eprfft::pidx(e)];
+        const float2 v = buf[PC::idx(e)];
         if (kx != 0) {
             const float H = inv_n / (1.f + ha * (float)kx * (float)kx + qy);
             nv[k] = cscale(v, H);
@@ -64,19 +66,77 @@ __global__ void __launch_bounds__(512, 2) k_col(const EprConsts C, const ColArgs
             const float H0 = inv_n / (1.f + qy);
             const float HN = inv_n / (1.f + ha * kn * kn + qy);
             const int yneg = (y == 0) ? 0 : ny - y;
-            const float2 w = cconj(buf[eprfft::pidx((yneg << lgCW) + c)]);
+            const float2 w = cconj(buf[PC::idx((yneg << lgCW) + c)]);
             const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
             nv[k] = make_float2(hp * v.x + hm * w.x, hp * v.y + hm * w.y);
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) buf[eprfft::pidx(tid + k * T)] = nv[k];
+    for (int k = 0; k < EPT; ++k) buf[PC::idx(tid + k * T)] = nv[k];
     __syncthreads();
-    eprfft::fft<+1, EPT>(buf, ny, lgCW, CW, 1, A.tw, T, tid);
+    eprfft::fft<PC, +1, EPT>(buf, ny, lgCW, CW, 1, A.tw, T, tid);
     for (int e = tid; e < ny * CW; e += T) {
         const int y = e >> lgCW, c = e & (CW - 1);
-        Sb[(size_t)y * half + kx0 + c] = buf[eprfft::pidx(e)];
+        Sb[(size_t)y * half + kx0 + c] = buf[PC::idx(e)];
+    }
+}
+
+// Compile-time column length NY and width CW, on the compile-time FFT engine.
+template <int NY, int CW, int EPT>
+__global__ void __launch_bounds__(NY * CW / EPT, (65536 / 64) / (NY * CW / EPT))
+k_col_ct(const EprConsts C, const ColArgs A)
+{
+    constexpr int T = NY * CW / EPT;
+    constexpr int LGCW = CW == 1 ? 0 : CW == 2 ? 1 : CW == 4 ? 2 : CW == 8 ? 3 : 4;
+    extern __shared__ __align__(16) float2 buf[];
+    const int b = blockIdx.z, sl = blockIdx.y;
+    if (A.check_done && A.st[b].done) return;
+    const int s = A.line0 + sl;
+    const int half = C.half, tid = threadIdx.x;
+    const int kx0 = blockIdx.x * CW;
+    float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)NY * half;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int e = tid + k * T;
+        const int y = e >> LGCW, c = e & (CW - 1);
+        buf[PC::idx(e)] = Sb[(size_t)y * half + kx0 + c];
+    }
+    __syncthreads();
+    eprfft::fft_ct<PC, -1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
+    const float ha = C.ha[s], hb = C.hb[s], inv_n = C.inv_n;
+    float2 nv[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int e = tid + k * T;
+        const int y = e >> LGCW, c = e & (CW - 1);
+        const int kx = kx0 + c;
+        const float ky = (float)(y <= NY / 2 ? y : y - NY);
+        const float qy = hb * ky * ky;
+        const float2 v = buf[PC::idx(e)];
+        if (kx != 0) {
+            const float H = inv_n / (1.f + ha * (float)kx * (float)kx + qy);
+            nv[k] = cscale(v, H);
+        } else {
+            const float kn = (float)half;
+            const float H0 = inv_n / (1.f + qy);
+            const float HN = inv_n / (1.f + ha * kn * kn + qy);
+            const int yneg = (NY - y) & (NY - 1);
+            const float2 w = cconj(buf[PC::idx((yneg << LGCW) + c)]);
+            const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
+            nv[k] = make_float2(hp * v.x + hm * w.x, hp * v.y + hm * w.y);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) buf[PC::idx(tid + k * T)] = nv[k];
+    __syncthreads();
+    eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int e = tid + k * T;
+        const int y = e >> LGCW, c = e & (CW - 1);
+        Sb[(size_t)y * half + kx0 + c] = buf[PC::idx(e)];
     }
 }
 
@@ -92,16 +152,16 @@ EprColLaunch epr_col_config(const EprConsts& C, int cw_hint)
     EprColLaunch L;
     int cw = cw_hint > 0 ? cw_hint : 4;
     while (cw > 1 && C.half % cw != 0) cw >>= 1;
-    // keep the block at 512 threads or fewer
+    // keep the block at 512 threads or fewer, 8 elements per thread if possible
     int ept = 8;
-    while (C.ny * cw / ept > 512 && ept < 16) ept *= 2;
     while (C.ny * cw / ept > 512 && cw > 1) cw >>= 1;
+    while (C.ny * cw / ept > 512 && ept < 16) ept *= 2;
     L.CW = cw;
     L.lgCW = 0;
     while ((1 << L.lgCW) < cw) ++L.lgCW;
     L.EPT = ept;
     L.threads = C.ny * cw / ept;
-    L.smem = (size_t)eprfft::padded_len(C.ny * cw) * sizeof(float2);
+    L.smem = (size_t)PC::len(C.ny * cw) * sizeof(float2);
     return L;
 }
 
@@ -119,8 +179,22 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     A.nl = nl;
     A.check_done = check_done;
     dim3 grid(C.half / L.CW, nl, batch);
-    if (L.EPT == 8) k_col<8><<<grid, L.threads, L.smem, stream>>>(C, A);
-    else k_col<16><<<grid, L.threads, L.smem, stream>>>(C, A);
+    bool done = false;
+#define EPR_COL_CASE(NYV, CWV, EPTV)                                                           \
+    if (!done && C.ny == NYV && L.CW == CWV && L.EPT == EPTV) {                               \
+        k_col_ct<NYV, CWV, EPTV><<<grid, NYV * CWV / EPTV, L.smem, stream>>>(C, A);           \
+        done = true;                                                                          \
+    }
+    EPR_COL_CASE(256, 4, 8)
+    EPR_COL_CASE(512, 4, 8)
+    EPR_COL_CASE(1024, 4, 8)
+    EPR_COL_CASE(2048, 2, 8)
+    EPR_COL_CASE(4096, 1, 8)
+#undef EPR_COL_CASE
+    if (!done) {
+        if (L.EPT == 8) k_col<8><<<grid, L.threads, L.smem, stream>>>(C, A);
+        else k_col<16><<<grid, L.threads, L.smem, stream>>>(C, A);
+    }
     epr_count_launch(1);
     return cudaGetLastError();
 }
@@ -129,5 +203,10 @@ cudaError_t epr_col_init()
 {
     cudaError_t e = epr_allow_max_smem(k_col<8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col<16>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<256, 4, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<512, 4, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1024, 4, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<2048, 2, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<4096, 1, 8>);
     return e;
 }

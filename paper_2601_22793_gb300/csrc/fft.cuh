@@ -18,19 +18,35 @@
 // Twiddles come from a table tw[t] = exp(-2 pi i t / N) (float, built in
 // double on the host); DIR = +1 uses its conjugate.  No normalisation.
 //
-// Shared-memory addresses pass through pidx(i) = i + i/8: one padding word
-// after every eight complex values.  The first stages write with strides of
-// 8 and 64 words, which otherwise fall into the same banks; with the padding
-// those stores are spread over all banks.  Callers index the buffers through
-// pidx too, and size them with padded_len().
+// Shared-memory addresses pass through a layout policy PAD (PAD::idx(i)),
+// and callers size and index their buffers with the same policy.  A 64-bit
+// shared access is served per half-warp, 16 complex values (128 bytes) per
+// wavefront, so the policies keep 16 consecutive values in distinct banks
+// and spread the strided Stockham stores:
+//  * PadRow (one sequence laid out contiguously, the row passes): an XOR
+//    swizzle of the low four bits by the 128-byte row index (and, every
+//    four rows, its bit 3) makes the stride-8 and stride-64 stores of the
+//    first two radix-8 stages conflict-free; no extra space.
+//  * PadCol (CW interleaved columns, the column pass): two padding values
+//    after every sixteen, i + 2 (i / 16).
 #pragma once
 
 #include "epr_internal.cuh"
 
 namespace eprfft {
 
-__host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
-__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 3) + 1; }
+struct PadRow {
+    __host__ __device__ static __forceinline__ int idx(int i)
+    {
+        return (i & ~15) | ((i & 15) ^ (((i >> 4) & 7) ^ (((i >> 6) & 1) << 3)));
+    }
+    __host__ __device__ static __forceinline__ int len(int n) { return (n + 15) & ~15; }
+};
+
+struct PadCol {
+    __host__ __device__ static __forceinline__ int idx(int i) { return i + 2 * (i >> 4); }
+    __host__ __device__ static __forceinline__ int len(int n) { return n + 2 * (n >> 4) + 2; }
+};
 
 // R-point DFTs in registers, sign DIR (-1 forward, +1 inverse).
 template <int DIR>
@@ -107,7 +123,7 @@ __device__ __forceinline__ void dft(float2* v)
     else dft8<DIR>(v);
 }
 
-template <int R, int DIR, int EPT>
+template <class PAD, int R, int DIR, int EPT>
 __device__ __forceinline__ void stage(float2* buf, int N, int Ns, int lgNs, int lgseq, int sj,
                                       int sm, const float2* __restrict__ tw, int T, int tid)
 {
@@ -129,7 +145,7 @@ __device__ __forceinline__ void stage(float2* buf, int N, int Ns, int lgNs, int 
             const int jd = (lgNs >= 0) ? (j >> lgNs) : (j / Ns);
             const int base = m * sm;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][r] = buf[pidx((j + r * NR) * sj + base)];
+            for (int r = 0; r < R; ++r) v[k][r] = buf[PAD::idx((j + r * NR) * sj + base)];
 #pragma unroll
             for (int r = 1; r < R; ++r) {
                 float2 w = __ldg(&tw[r * jm * twstep]);
@@ -145,7 +161,7 @@ __device__ __forceinline__ void stage(float2* buf, int N, int Ns, int lgNs, int 
         if (dst[k] >= 0) {
             dft<R, DIR>(v[k]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[pidx(dst[k] + r * Ns * sj)] = v[k][r];
+            for (int r = 0; r < R; ++r) buf[PAD::idx(dst[k] + r * Ns * sj)] = v[k][r];
         }
     }
     __syncthreads();
@@ -153,7 +169,7 @@ __device__ __forceinline__ void stage(float2* buf, int N, int Ns, int lgNs, int 
 
 // Full transform.  The caller synchronises before (data in buf) and may read
 // buf right after return (the last stage ends with a barrier).
-template <int DIR, int EPT>
+template <class PAD, int DIR, int EPT>
 __device__ void fft(float2* buf, int N, int lgseq, int sj, int sm, const float2* __restrict__ tw,
                     int T, int tid)
 {
@@ -164,19 +180,123 @@ __device__ void fft(float2* buf, int N, int lgseq, int sj, int sm, const float2*
     }
     int Ns = 1, lgNs = 0;
     while (rem2 >= 8) {
-        stage<8, DIR, EPT>(buf, N, Ns, lgNs, lgseq, sj, sm, tw, T, tid);
+        stage<PAD, 8, DIR, EPT>(buf, N, Ns, lgNs, lgseq, sj, sm, tw, T, tid);
         Ns *= 8; lgNs += 3; rem2 /= 8;
     }
     if (rem2 == 4) {
-        stage<4, DIR, EPT>(buf, N, Ns, lgNs, lgseq, sj, sm, tw, T, tid);
+        stage<PAD, 4, DIR, EPT>(buf, N, Ns, lgNs, lgseq, sj, sm, tw, T, tid);
         Ns *= 4; lgNs += 2;
     } else if (rem2 == 2) {
-        stage<2, DIR, EPT>(buf, N, Ns, lgNs, lgseq, sj, sm, tw, T, tid);
+        stage<PAD, 2, DIR, EPT>(buf, N, Ns, lgNs, lgseq, sj, sm, tw, T, tid);
         Ns *= 2; lgNs += 1;
     }
     while (rem3 > 1) {
-        stage<3, DIR, EPT>(buf, N, Ns, -1, lgseq, sj, sm, tw, T, tid);
+        stage<PAD, 3, DIR, EPT>(buf, N, Ns, -1, lgseq, sj, sm, tw, T, tid);
         Ns *= 3; rem3 /= 3;
+    }
+}
+
+}  // namespace eprfft
+
+// ---------------------------------------------------------------------------
+// Compile-time-sized variant of the same Stockham schedule.  N, the number of
+// sequences (1 << LGSEQ), the strides SJ / SM and the elements per thread are
+// template parameters, so every stage is unrolled, strides fold into address
+// offsets, the first stage (Ns = 1) needs no twiddle, and a radix-R stage
+// loads one twiddle w = exp(DIR 2 pi i jm / (Ns R)) and forms w^2 .. w^(R-1)
+// by complex multiplication (a few ulp, well inside the transform's error).
+// ---------------------------------------------------------------------------
+namespace eprfft {
+
+__host__ __device__ constexpr int ct_pow2_part(int n)
+{
+    while (n % 3 == 0) n /= 3;
+    return n;
+}
+__host__ __device__ constexpr int ct_n_stages(int n)
+{
+    int p = ct_pow2_part(n), c = 0;
+    while (p >= 8) { p /= 8; ++c; }
+    if (p > 1) ++c;
+    int t = n / ct_pow2_part(n);
+    while (t > 1) { t /= 3; ++c; }
+    return c;
+}
+__host__ __device__ constexpr int ct_radix(int n, int s)
+{
+    int p = ct_pow2_part(n), k = 0;
+    while (p >= 8) {
+        if (k == s) return 8;
+        p /= 8;
+        ++k;
+    }
+    if (p > 1) {
+        if (k == s) return p;
+        ++k;
+    }
+    return 3;
+}
+__host__ __device__ constexpr int ct_ns(int n, int s)
+{
+    int v = 1;
+    for (int i = 0; i < s; ++i) v *= ct_radix(n, i);
+    return v;
+}
+
+template <class PAD, int R, int DIR, int EPT, int N, int NS, int LGSEQ, int SJ, int SM>
+__device__ __forceinline__ void stage_ct(float2* buf, const float2* __restrict__ tw, int tid)
+{
+    constexpr int NSEQ = 1 << LGSEQ;
+    constexpr int T = (N * NSEQ) / EPT;
+    constexpr int PER = (EPT + R - 1) / R;
+    constexpr int NR = N / R;
+    constexpr int NB = NR * NSEQ;
+    constexpr int TWSTEP = N / (NS * R);
+    float2 v[PER][R];
+    int dst[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int b = tid + k * T;
+        dst[k] = -1;
+        if (NB % T == 0 || b < NB) {
+            const int m = b & (NSEQ - 1);
+            const int j = b >> LGSEQ;
+            const int jm = j % NS;
+            const int jd = j / NS;
+            const int base = m * SM;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[k][r] = buf[PAD::idx((j + r * NR) * SJ + base)];
+            if constexpr (NS > 1) {
+                float2 w = __ldg(&tw[jm * TWSTEP]);
+                if (DIR > 0) w.y = -w.y;
+                float2 wr = w;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    v[k][r] = cmul(v[k][r], wr);
+                    if (r + 1 < R) wr = cmul(wr, w);
+                }
+            }
+            dst[k] = (jd * NS * R + jm) * SJ + base;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (NB % T == 0 || dst[k] >= 0) {
+            dft<R, DIR>(v[k]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[PAD::idx(dst[k] + r * NS * SJ)] = v[k][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int S = 0>
+__device__ __forceinline__ void fft_ct(float2* buf, const float2* __restrict__ tw, int tid)
+{
+    if constexpr (S < ct_n_stages(N)) {
+        stage_ct<PAD, ct_radix(N, S), DIR, EPT, N, ct_ns(N, S), LGSEQ, SJ, SM>(buf, tw, tid);
+        fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, S + 1>(buf, tw, tid);
     }
 }
 

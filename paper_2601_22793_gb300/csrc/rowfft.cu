@@ -34,6 +34,7 @@ enum { FWD_SOLVE_NL = 0, FWD_SOLVE_LOCAL = 1, FWD_LOAD = 2 };
 enum { INV_UPDATE = 0, INV_STORE = 1 };
 
 constexpr int kEPT = 8;   // complex elements per thread in the row FFT
+using PR = eprfft::PadRow;  // shared layout of the packed rows
 constexpr int kPad = 4;   // float2 padding between packed rows in shared memory
 
 struct RowArgs {
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
     const int yb = blockIdx.x * RP * 2;   // first row of the block
     const int nl = NS ? NS : A.nl;
     // thickness rows yb-1 .. yb+2RP (clamped), after the FFT buffer
-    float* Ts = reinterpret_cast<float*>(zs + ((eprfft::padded_len(RP * sm) + 1) & ~1));
+    float* Ts = reinterpret_cast<float*>(zs + ((PR::len(RP * sm) + 1) & ~1));
     const int nrows = 2 * RP + 2;
 
     if constexpr (MODE == FWD_SOLVE_NL) {
@@ -189,10 +190,10 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
                     }
                 }
             }
-            zs[eprfft::pidx(m * sm + x)] = make_float2(v[0], v[1]);
+            zs[PR::idx(m * sm + x)] = make_float2(v[0], v[1]);
         }
         __syncthreads();
-        eprfft::fft<-1, kEPT>(zs, nx, A.lgRP, 1, sm, A.tw, T, tid);
+        eprfft::fft<PR, -1, kEPT>(zs, nx, A.lgRP, 1, sm, A.tw, T, tid);
         // epilogue: unpack the two real spectra and store k < nx/2
         float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * half;
         const float inv_half = 1.f / (float)half;
@@ -203,11 +204,11 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
             const int zb = m * sm;
             float2 X0, X1;
             if (k == 0) {
-                const float2 z0 = zs[eprfft::pidx(zb)], zn = zs[eprfft::pidx(zb + half)];
+                const float2 z0 = zs[PR::idx(zb)], zn = zs[PR::idx(zb + half)];
                 X0 = make_float2(z0.x, zn.x);
                 X1 = make_float2(z0.y, zn.y);
             } else {
-                const float2 a = zs[eprfft::pidx(zb + k)], bb = cconj(zs[eprfft::pidx(zb + nx - k)]);
+                const float2 a = zs[PR::idx(zb + k)], bb = cconj(zs[PR::idx(zb + nx - k)]);
                 const float2 sp = cadd(a, bb), df = csub(a, bb);
                 X0 = make_float2(0.5f * sp.x, 0.5f * sp.y);
                 X1 = make_float2(0.5f * df.y, -0.5f * df.x);
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const Row
     const size_t pb = (size_t)b * npix;
     const int yb = blockIdx.x * RP * 2;
     const int nl = NS ? NS : A.nl;
-    float* acc = reinterpret_cast<float*>(zs + ((eprfft::padded_len(RP * sm) + 1) & ~1));  // [2 RP][nx]
+    float* acc = reinterpret_cast<float*>(zs + ((PR::len(RP * sm) + 1) & ~1));  // [2 RP][nx]
     const float inv_nx = 1.f / (float)nx, inv_half = 1.f / (float)half;
     float da = 0.f, db = 0.f;
 
@@ -278,21 +279,21 @@ __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const Row
             const float2 s1 = Sb[(size_t)(y0 + 1) * half + k];
             const int zb = m * sm;
             if (k == 0) {
-                zs[eprfft::pidx(zb)] = make_float2(s0.x, s1.x);
-                zs[eprfft::pidx(zb + half)] = make_float2(s0.y, s1.y);
+                zs[PR::idx(zb)] = make_float2(s0.x, s1.x);
+                zs[PR::idx(zb + half)] = make_float2(s0.y, s1.y);
             } else {
-                zs[eprfft::pidx(zb + k)] = make_float2(s0.x - s1.y, s0.y + s1.x);
-                zs[eprfft::pidx(zb + nx - k)] = make_float2(s0.x + s1.y, s1.x - s0.y);
+                zs[PR::idx(zb + k)] = make_float2(s0.x - s1.y, s0.y + s1.x);
+                zs[PR::idx(zb + nx - k)] = make_float2(s0.x + s1.y, s1.x - s0.y);
             }
         }
         __syncthreads();
-        eprfft::fft<+1, kEPT>(zs, nx, A.lgRP, 1, sm, A.tw, T, tid);
+        eprfft::fft<PR, +1, kEPT>(zs, nx, A.lgRP, 1, sm, A.tw, T, tid);
 #pragma unroll 2
         for (int k = 0; k < kEPT; ++k) {
             const int e = tid + k * T;
             const int m = RP == 1 ? 0 : fdiv(e, inv_nx);
             const int x = e - m * nx;
-            const float2 h = zs[eprfft::pidx(m * sm + x)];
+            const float2 h = zs[PR::idx(m * sm + x)];
             const size_t q0 = pb + (size_t)(yb + 2 * m) * nx + x;
             if constexpr (MODE == INV_UPDATE) {
                 const float fs = C.f[s], mus = C.mu[s], w = C.wproj[s];
@@ -380,6 +381,237 @@ __global__ void k_sumsq_final(const double* part, int nparts, int max_blocks, Ep
     st[b].dnorm2 = s;
 }
 
+// ---------------------------------------------------------------------------
+// Monochromatic float solve, compile-time row length NX and RP row pairs per
+// block: the same passes as k_row_fwd / k_row_inv (modes FWD_SOLVE_NL with
+// the residual stored by the splat, INV_UPDATE with one line) on the
+// compile-time FFT engine.
+// ---------------------------------------------------------------------------
+template <int NX>
+__host__ __device__ constexpr int ct_lg(int v) { return v <= 1 ? 0 : 1 + ct_lg<NX>(v / 2); }
+
+template <int NX, int RP>
+__global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
+k_row_fwd_mono(const EprConsts C, const RowArgs A)
+{
+    constexpr int T = NX * RP / kEPT;
+    constexpr int SM = NX + kPad;
+    constexpr int HALF = NX / 2;
+    constexpr int LGRP = ct_lg<NX>(RP);
+    constexpr int LGNX = ct_lg<NX>(NX);
+    extern __shared__ __align__(16) float2 zs[];
+    __shared__ float red[64];
+    const int b = blockIdx.y;
+    if (A.check_done && A.st[b].done) return;
+    const int ny = C.ny, tid = threadIdx.x;
+    const size_t npix = (size_t)NX * ny;
+    const size_t pb = (size_t)b * npix;
+    const int yb = blockIdx.x * RP * 2;
+    float* Ts = reinterpret_cast<float*>(zs + ((PR::len(RP * SM) + 1) & ~1));
+    {
+        const float* Tb = A.T + pb;
+        constexpr int Q4 = NX / 4;
+        constexpr int NROWS = 2 * RP + 2;
+#pragma unroll
+        for (int i0 = 0; i0 < NROWS * Q4; i0 += T) {
+            const int i = i0 + tid;
+            if (NROWS * Q4 % T == 0 || i < NROWS * Q4) {
+                const int r = i / Q4, c4 = i % Q4;
+                const int gy = min(max(yb - 1 + r, 0), ny - 1);
+                reinterpret_cast<float4*>(Ts)[i] =
+                    __ldg(reinterpret_cast<const float4*>(Tb + (size_t)gy * NX) + c4);
+            }
+        }
+    }
+    __syncthreads();
+    const float cs = C.c[0];
+    const float* Rb = A.P + pb;   // residual D - P
+    float ra = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < kEPT; ++k) {
+        const int e = tid + k * T;
+        const int m = e >> LGNX, x = e & (NX - 1);
+        const int y0 = yb + 2 * m;
+        float v[2];
+#pragma unroll
+        for (int r0 = 0; r0 < 2; ++r0) {
+            const int y = y0 + r0;
+            const float* tr = Ts + (2 * m + r0 + 1) * NX;
+            const float t = tr[x];
+            float gx, gy;
+            if (x == 0) gx = tr[1] - t;
+            else if (x == NX - 1) gx = t - tr[x - 1];
+            else gx = 0.5f * (tr[x + 1] - tr[x - 1]);
+            if (y == 0) gy = tr[NX + x] - t;
+            else if (y == ny - 1) gy = t - tr[x - NX];
+            else gy = 0.5f * (tr[NX + x] - tr[x - NX]);
+            const float lim = 2.f * (float)(NX > ny ? NX : ny);
+            const float ux = fminf(fmaxf(cs * gx, -lim), lim);
+            const float uy = fminf(fmaxf(cs * gy, -lim), lim);
+            const float fx = floorf(ux), fy = floorf(uy);
+            const float dx = ux - fx, dy = uy - fy;
+            const int cx = x + (int)fx, cy = y + (int)fy;
+            const bool x0 = (unsigned)cx < (unsigned)NX, x1 = (unsigned)(cx + 1) < (unsigned)NX;
+            float r00 = 0.f, r10 = 0.f, r01 = 0.f, r11 = 0.f;
+            if ((unsigned)cy < (unsigned)ny) {
+                const float* rr = Rb + (size_t)cy * NX + cx;
+                if (x0) r00 = __ldg(rr);
+                if (x1) r10 = __ldg(rr + 1);
+            }
+            if ((unsigned)(cy + 1) < (unsigned)ny) {
+                const float* rr = Rb + (size_t)(cy + 1) * NX + cx;
+                if (x0) r01 = __ldg(rr);
+                if (x1) r11 = __ldg(rr + 1);
+            }
+            const float top = r00 + dx * (r10 - r00);
+            const float bot = r01 + dx * (r11 - r01);
+            v[r0] = (1.f - dy) * top + dy * bot;
+            const float own = __ldg(Rb + (size_t)y * NX + x);
+            ra += own * own;
+        }
+        zs[PR::idx(m * SM + x)] = make_float2(v[0], v[1]);
+    }
+    __syncthreads();
+    eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
+    float2* Sb = A.S + (size_t)b * (size_t)ny * HALF;
+#pragma unroll 2
+    for (int i0 = 0; i0 < RP * HALF; i0 += T) {
+        const int e = i0 + tid;
+        const int m = e / HALF, k = e % HALF;
+        const int y0 = yb + 2 * m;
+        const int zb = m * SM;
+        float2 X0, X1;
+        if (k == 0) {
+            const float2 z0 = zs[PR::idx(zb)], zn = zs[PR::idx(zb + HALF)];
+            X0 = make_float2(z0.x, zn.x);
+            X1 = make_float2(z0.y, zn.y);
+        } else {
+            const float2 a = zs[PR::idx(zb + k)], bb = cconj(zs[PR::idx(zb + NX - k)]);
+            const float2 sp = cadd(a, bb), df = csub(a, bb);
+            X0 = make_float2(0.5f * sp.x, 0.5f * sp.y);
+            X1 = make_float2(0.5f * df.y, -0.5f * df.x);
+        }
+        Sb[(size_t)y0 * HALF + k] = X0;
+        Sb[(size_t)(y0 + 1) * HALF + k] = X1;
+    }
+    float rb = 0.f;
+    block_sum2(ra, rb, red);
+    double sa, sb;
+    if (last_block_reduce(&A.st[b].cnt_fwd, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
+                          A.part_b + (size_t)b * A.max_blocks, blockIdx.x, ra, rb, sa, sb)) {
+        if (threadIdx.x == 0) {
+            const double dn = A.st[b].dnorm2;
+            const double rho = dn > 0.0 ? sqrt(sa / dn) : sqrt(sa);
+            A.st[b].rho = (float)rho;
+            if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = rho;
+        }
+    }
+}
+
+template <int NX, int RP>
+__global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
+k_row_inv_mono(const EprConsts C, const RowArgs A)
+{
+    constexpr int T = NX * RP / kEPT;
+    constexpr int SM = NX + kPad;
+    constexpr int HALF = NX / 2;
+    constexpr int LGRP = ct_lg<NX>(RP);
+    constexpr int LGNX = ct_lg<NX>(NX);
+    extern __shared__ __align__(16) float2 zs[];
+    __shared__ float red[64];
+    const int b = blockIdx.y;
+    if (A.check_done && A.st[b].done) return;
+    const int ny = C.ny, tid = threadIdx.x;
+    const size_t pb = (size_t)b * NX * ny;
+    const int yb = blockIdx.x * RP * 2;
+    const float2* Sb = A.S + (size_t)b * (size_t)ny * HALF;
+#pragma unroll 2
+    for (int i0 = 0; i0 < RP * HALF; i0 += T) {
+        const int e = i0 + tid;
+        const int m = e / HALF, k = e % HALF;
+        const int y0 = yb + 2 * m;
+        const float2 s0 = Sb[(size_t)y0 * HALF + k];
+        const float2 s1 = Sb[(size_t)(y0 + 1) * HALF + k];
+        const int zb = m * SM;
+        if (k == 0) {
+            zs[PR::idx(zb)] = make_float2(s0.x, s1.x);
+            zs[PR::idx(zb + HALF)] = make_float2(s0.y, s1.y);
+        } else {
+            zs[PR::idx(zb + k)] = make_float2(s0.x - s1.y, s0.y + s1.x);
+            zs[PR::idx(zb + NX - k)] = make_float2(s0.x + s1.y, s1.x - s0.y);
+        }
+    }
+    __syncthreads();
+    eprfft::fft_ct<PR, +1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
+    const float fs = C.f[0], mus = C.mu[0], w = C.wproj[0];
+    float da = 0.f, db = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < kEPT; ++k) {
+        const int e = tid + k * T;
+        const int m = e >> LGNX, x = e & (NX - 1);
+        const float2 h = zs[PR::idx(m * SM + x)];
+        const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
+        const float t0 = A.Out[q0], t1 = A.Out[q0 + NX];
+        const float l0 = w * log_ratio(t0, h.x, fs, mus, A.omega, A.eps);
+        const float l1 = w * log_ratio(t1, h.y, fs, mus, A.omega, A.eps);
+        const float n0 = t0 - l0, n1 = t1 - l1;
+        A.Out[q0] = n0;
+        A.Out[q0 + NX] = n1;
+        da += l0 * l0 + l1 * l1;
+        db += n0 * n0 + n1 * n1;
+    }
+    block_sum2(da, db, red);
+    double sa, sb;
+    if (last_block_reduce(&A.st[b].cnt_inv, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
+                          A.part_b + (size_t)b * A.max_blocks, blockIdx.x, da, db, sa, sb)) {
+        if (threadIdx.x == 0) {
+            const double kap = sb > 0.0 ? sqrt(sa / sb) : sqrt(sa);
+            A.st[b].kappa = (float)kap;
+            A.st[b].iters = A.it + 1;
+            if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = kap;
+            if (A.tol > 0.f && kap <= (double)A.tol) A.st[b].done = 1;
+        }
+    }
+}
+
+// launch a specialised mono kernel when nx has one; returns false otherwise
+template <bool FWD>
+bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream, const EprConsts& C,
+                    const RowArgs& A)
+{
+#define EPR_MONO_CASE(NXV, RPV)                                                              \
+    if (nx == NXV && rp == RPV) {                                                            \
+        if (FWD) k_row_fwd_mono<NXV, RPV><<<grid, NXV * RPV / kEPT, smem, stream>>>(C, A);   \
+        else k_row_inv_mono<NXV, RPV><<<grid, NXV * RPV / kEPT, smem, stream>>>(C, A);       \
+        return true;                                                                         \
+    }
+    EPR_MONO_CASE(256, 8)
+    EPR_MONO_CASE(512, 4)
+    EPR_MONO_CASE(1024, 2)
+    EPR_MONO_CASE(2048, 1)
+    EPR_MONO_CASE(4096, 1)
+#undef EPR_MONO_CASE
+    return false;
+}
+
+template <typename K>
+cudaError_t allow(K k) { return epr_allow_max_smem(k); }
+
+cudaError_t init_mono_ct()
+{
+    cudaError_t e = cudaSuccess;
+#define EPR_MONO_INIT(NXV, RPV)                                                  \
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV>);                    \
+    if (e == cudaSuccess) e = allow(k_row_inv_mono<NXV, RPV>);
+    EPR_MONO_INIT(256, 8)
+    EPR_MONO_INIT(512, 4)
+    EPR_MONO_INIT(1024, 2)
+    EPR_MONO_INIT(2048, 1)
+    EPR_MONO_INIT(4096, 1)
+#undef EPR_MONO_INIT
+    return e;
+}
+
 }  // namespace
 
 struct EprRowLaunch {
@@ -399,7 +631,7 @@ EprRowLaunch epr_row_config(const EprConsts& C)
     // FFT rows, then the staged thickness rows (forward) or line accumulators
     // (inverse); the larger of the two
     const size_t extra = (size_t)(2 * rp + 2) * C.nx * sizeof(float);
-    L.smem = (size_t)((eprfft::padded_len(rp * (C.nx + kPad)) + 1) & ~1) * sizeof(float2) + extra;
+    L.smem = (size_t)((PR::len(rp * (C.nx + kPad)) + 1) & ~1) * sizeof(float2) + extra;  // EPR_ROW_SMEM
     return L;
 }
 
@@ -424,7 +656,8 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, i
             if (mono) k_row_fwd<FWD_SOLVE_NL, true, false, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
             else k_row_fwd<FWD_SOLVE_NL, true, false, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
         } else if (resid && mono) {
-            k_row_fwd<FWD_SOLVE_NL, false, true, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+            if (!launch_mono_ct<true>(C.nx, L.RP, grid, L.smem, stream, C, A))
+                k_row_fwd<FWD_SOLVE_NL, false, true, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
         } else {
             if (mono) k_row_fwd<FWD_SOLVE_NL, false, false, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
             else k_row_fwd<FWD_SOLVE_NL, false, false, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
@@ -452,7 +685,8 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
     A.omega = omega; A.eps = eps; A.tol = tol; A.check_done = check_done;
     dim3 grid(C.ny / (2 * L.RP), batch);
     if (mode == INV_UPDATE) {
-        if (nl == 1) k_row_inv<INV_UPDATE, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+        if (nl == 1 && !C.det && launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A)) {
+        } else if (nl == 1) k_row_inv<INV_UPDATE, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
         else k_row_inv<INV_UPDATE, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
     } else {
         k_row_inv<INV_STORE, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
@@ -485,5 +719,6 @@ cudaError_t epr_row_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 1>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 0>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_STORE, 1>);
+    if (e == cudaSuccess) e = init_mono_ct();
     return e;
 }
