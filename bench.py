@@ -249,7 +249,7 @@ def run_ours(a):
 
     # kernel roofline: the same solves with per-kernel CUDA events
     epr.epr_profile_enable(plan.handle, True)
-    n_prof = max(3, min(10, a.steps))
+    n_prof = max(3, min(8, a.steps))
     for _ in range(n_prof):
         flush.zero_()
         solve()

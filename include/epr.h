@@ -184,12 +184,14 @@ typedef enum {
     EPR_KERNEL_KINDS = 6
 } epr_kernel_kind;
 
-/* Kernel timing for benchmarks.  While enabled, the plan launches without
- * CUDA graphs and brackets every kernel with CUDA events recorded on the
- * kernel's own stream; epr_profile_read synchronises those events and
- * returns, per kind, the number of launches and their summed duration in
- * milliseconds since the last read (the counters are then cleared).
- * Disabling drops pending records. */
+/* Kernel timing for benchmarks.  While enabled, every kernel the plan
+ * launches is bracketed by CUDA events recorded on the kernel's own stream;
+ * a solve is then captured afresh into a CUDA graph that contains those
+ * event records, so its kernels run back to back exactly as in an untimed
+ * solve.  epr_profile_read synchronises the events and returns, per kind,
+ * the number of launches and their summed duration in milliseconds since
+ * the last read (the counters are then cleared).  Disabling drops pending
+ * records. */
 epr_status epr_profile_enable(epr_plan_t plan, int enable);
 epr_status epr_profile_read(epr_plan_t plan, int* launches, double* total_ms);
 

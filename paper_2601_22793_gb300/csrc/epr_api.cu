@@ -114,6 +114,7 @@ struct epr_plan_s {
     GraphKey gkey;
     int gkernels;
     bool has_graph;
+    cudaGraphExec_t prof_exec;   // last profiled solve
 };
 
 namespace {
@@ -277,15 +278,15 @@ void choose_splat_tiles(epr_plan_s* p)
     }
 }
 
+// Events come from a pool filled when profiling is enabled (none is created
+// while a stream is being captured); an empty pool skips the timing.
+constexpr int kProfEvents = 8192;
+
 cudaEvent_t pool_get(epr_plan_s* p)
 {
-    if (!p->pool.empty()) {
-        cudaEvent_t e = p->pool.back();
-        p->pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    if (p->pool.empty()) return nullptr;
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
     return e;
 }
 
@@ -299,7 +300,7 @@ struct ProfScope {
     {
         if (p->profiling) {
             a = pool_get(p);
-            if (a) cudaEventRecord(a, s);
+            if (a) cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
         }
     }
     ~ProfScope()
@@ -310,7 +311,7 @@ struct ProfScope {
             p->pool.push_back(a);
             return;
         }
-        cudaEventRecord(b, s);
+        cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
         p->recs.push_back({kind, a, b});
     }
 };
@@ -387,7 +388,31 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
     if (st != EPR_OK) return st;
 
     const int kernels_per_iter = model == EPR_MODEL_NONLOCAL ? 5 : 4;
-    if (p->opt.use_graphs && !p->profiling && o->n_iter > 0) {
+    if (p->profiling && o->n_iter > 0) {
+        // profiled solve: capture a fresh graph whose kernels are bracketed by
+        // event-record nodes, so the kernels run back to back as in the timed
+        // solve and the events time the kernels, not the host's launches
+        if (p->prof_exec) {
+            cudaGraphExecDestroy(p->prof_exec);
+            p->prof_exec = nullptr;
+        }
+        cudaGraph_t g;
+        EPR_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const long long before = g_launches.load();
+        epr_status ls = launch_solve(p, Dd, Td, batch, o, model, p->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+        g_launches.store(before);
+        if (ls != EPR_OK) {
+            if (ce == cudaSuccess) cudaGraphDestroy(g);
+            return ls;
+        }
+        EPR_TRY(ce);
+        cudaError_t ie = cudaGraphInstantiate(&p->prof_exec, g, 0);
+        cudaGraphDestroy(g);
+        EPR_TRY(ie);
+        EPR_TRY(cudaGraphLaunch(p->prof_exec, s));
+        epr_count_launch(kernels_per_iter * o->n_iter + 2);
+    } else if (p->opt.use_graphs && o->n_iter > 0) {
         GraphKey key{Dd, Td, batch, o->n_iter, o->init, model, o->omega, o->tol, o->eps_I};
         if (!(p->has_graph && p->gkey == key)) {
             if (p->has_graph) {
@@ -609,6 +634,7 @@ void epr_plan_destroy(epr_plan_t p)
     if (p->tw_y) cudaFree(p->tw_y);
     if (p->h_st) cudaFreeHost(p->h_st);
     if (p->h_hist) cudaFreeHost(p->h_hist);
+    if (p->prof_exec) cudaGraphExecDestroy(p->prof_exec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto& r : p->recs) {
         cudaEventDestroy(r.a);
@@ -740,6 +766,13 @@ epr_status epr_profile_enable(epr_plan_t p, int enable)
             p->pool.push_back(r.b);
         }
         p->recs.clear();
+    }
+    if (enable) {
+        while (p->pool.size() + 2 * p->recs.size() < (size_t)kProfEvents) {
+            cudaEvent_t e = nullptr;
+            EPR_TRY(cudaEventCreate(&e));
+            p->pool.push_back(e);
+        }
     }
     p->profiling = enable != 0;
     return EPR_OK;

@@ -74,11 +74,19 @@ __device__ __forceinline__ void acc_add(void* acc, int idx, float v)
 }
 
 // NS = 1: single line known at compile time; NS = 0: C.ns lines.
+// Shared layout: accumulators [ns][TH][TW]; the staged thickness window
+// [SH][SWa] whose first column ax0 = tx0 - HX is 16-byte aligned (HX = R + 1
+// rounded up to 4) so rows load as float4; a list of far sources.
+constexpr int kFarList = 256;
+
 template <int NS, bool DET, bool RESID>
 __global__ void __launch_bounds__(kSplatThreads)
 k_splat(const EprConsts C, const SplatArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_far_idx[kFarList];
+    __shared__ unsigned int s_far_mask[kFarList];
+    __shared__ int s_far_n, s_far_base;
     const int b = blockIdx.z;
     if (A.check_done && A.st[b].done) return;
     const int nx = C.nx, ny = C.ny;
@@ -87,7 +95,9 @@ k_splat(const EprConsts C, const SplatArgs A)
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     const int R = C.smax + 1;
     const int RH = TH + 2 * R, RW = TW + 2 * R;     // source region
-    const int SH = RH + 2, SW = RW + 2;              // staged thickness
+    const int HX = (R + 1 + 3) & ~3;
+    const int SH = RH + 2, SWa = TW + 2 * HX;        // staged thickness
+    const int coff = HX - R - 1;                     // staged column of source column tx0 - R - 1
     const int tile = TH * TW;
     const size_t npix = (size_t)nx * ny;
     const int tid = threadIdx.x;
@@ -96,22 +106,39 @@ k_splat(const EprConsts C, const SplatArgs A)
     const size_t acc_bytes = (size_t)ns * tile * (DET ? 8 : 4);
     float* Ts = reinterpret_cast<float*>(smem + ((acc_bytes + 15) & ~size_t(15)));
     const float* Tb = A.T + (size_t)b * npix;
+    if (tid == 0) s_far_n = 0;
 
-    const int sy0 = ty0 - R - 1, sx0 = tx0 - R - 1;
-    const bool interior = sy0 >= 0 && sx0 >= 0 && sy0 + SH <= ny && sx0 + SW <= nx;
-    const float inv_SW = 1.f / (float)SW, inv_RW = 1.f / (float)RW;
-    if (interior) {
-        for (int i = tid; i < SH * SW; i += kSplatThreads) {
-            const int ly = fdiv(i, inv_SW), lx = i - ly * SW;
-            Ts[i] = __ldg(&Tb[(size_t)(sy0 + ly) * nx + sx0 + lx]);
+    // the detector data of the tile, fetched before the scan (residual output)
+    constexpr int kDq = 4;   // float4 per thread: tiles up to 64 x 64
+    float4 dreg[kDq];
+    const int nq = tile >> 2;
+    const int tw4 = TW >> 2;
+    if constexpr (RESID) {
+#pragma unroll
+        for (int k = 0; k < kDq; ++k) {
+            const int i4 = tid + k * kSplatThreads;
+            dreg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i4 < nq) {
+                const int ly = i4 / tw4, lx = (i4 - ly * tw4) << 2;
+                const int gy = ty0 + ly, gx = tx0 + lx;
+                if (gy < ny && gx < nx)
+                    dreg[k] = __ldg(reinterpret_cast<const float4*>(A.D + (size_t)b * npix + (size_t)gy * nx + gx));
+            }
         }
-    } else {
-        for (int i = tid; i < SH * SW; i += kSplatThreads) {
-            const int ly = fdiv(i, inv_SW), lx = i - ly * SW;
-            const int gy = sy0 + ly, gx = sx0 + lx;
-            float v = 0.f;
-            if (gy >= 0 && gy < ny && gx >= 0 && gx < nx) v = __ldg(&Tb[(size_t)gy * nx + gx]);
-            Ts[i] = v;
+    }
+
+    const int sy0 = ty0 - R - 1, sx0 = tx0 - R - 1, ax0 = tx0 - HX;
+    const bool interior = sy0 >= 0 && sx0 >= 0 && sy0 + SH <= ny && sx0 + RW + 2 <= nx;
+    {
+        const int q = SWa >> 2;
+        const float inv_q = 1.f / (float)q;
+        for (int i = tid; i < SH * q; i += kSplatThreads) {
+            const int ly = fdiv(i, inv_q), c4 = i - ly * q;
+            const int gy = sy0 + ly, gx = ax0 + 4 * c4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gy >= 0 && gy < ny && gx >= 0 && gx < nx)   // nx % 4 == 0: all four or none
+                v = __ldg(reinterpret_cast<const float4*>(Tb + (size_t)gy * nx + gx));
+            reinterpret_cast<float4*>(Ts)[i] = v;
         }
     }
     if constexpr (DET) {
@@ -125,19 +152,20 @@ k_splat(const EprConsts C, const SplatArgs A)
 
     const float fsmax = (float)C.smax;
     const int nsrc = RH * RW;
+    const float inv_RW = 1.f / (float)RW;
     for (int i = tid; i < nsrc; i += kSplatThreads) {
         const int ly = fdiv(i, inv_RW), lx = i - ly * RW;
         const int sy = ty0 - R + ly, sx = tx0 - R + lx;
-        const float* tp = Ts + (ly + 1) * SW + (lx + 1);
+        const float* tp = Ts + (ly + 1) * SWa + (lx + 1 + coff);
         const float t = tp[0];
         float gx, gy;
         if (interior) {
             gx = 0.5f * (tp[1] - tp[-1]);
-            gy = 0.5f * (tp[SW] - tp[-SW]);
+            gy = 0.5f * (tp[SWa] - tp[-SWa]);
         } else {
             if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) continue;
             gx = grad1(tp[-1], t, tp[1], sx, nx);
-            gy = grad1(tp[-SW], t, tp[SW], sy, ny);
+            gy = grad1(tp[-SWa], t, tp[SWa], sy, ny);
         }
         unsigned int far = 0u;
 #pragma unroll(NS ? NS : 1)
@@ -166,49 +194,85 @@ k_splat(const EprConsts C, const SplatArgs A)
             }
         }
         if (far && (unsigned)(ly - R) < (unsigned)TH && (unsigned)(lx - R) < (unsigned)TW) {
-            const int pos = atomicAdd(&A.st[b].ovf_count[A.parity], 1);
-            if (pos < C.ovf_cap) {
-                A.ovf_idx[(size_t)b * C.ovf_cap + pos] = sy * nx + sx;
-                A.ovf_mask[(size_t)b * C.ovf_cap + pos] = far;
-            } else {
-                atomicOr(A.err, EPR_DEVERR_OVERFLOW);
+            const int pos = atomicAdd(&s_far_n, 1);
+            if (pos < kFarList) {
+                s_far_idx[pos] = sy * nx + sx;
+                s_far_mask[pos] = far;
+            } else {   // list full: append to the global list directly
+                const int gpos = atomicAdd(&A.st[b].ovf_count[A.parity], 1);
+                if (gpos < C.ovf_cap) {
+                    A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = sy * nx + sx;
+                    A.ovf_mask[(size_t)b * C.ovf_cap + gpos] = far;
+                } else {
+                    atomicOr(A.err, EPR_DEVERR_OVERFLOW);
+                }
             }
         }
     }
     __syncthreads();
 
+    // far sources of this block: one reservation in the global list
+    const int nfar = s_far_n < kFarList ? s_far_n : kFarList;
+    if (nfar > 0) {
+        if (tid == 0) s_far_base = atomicAdd(&A.st[b].ovf_count[A.parity], nfar);
+        __syncthreads();
+        for (int e = tid; e < nfar; e += kSplatThreads) {
+            const int gpos = s_far_base + e;
+            if (gpos < C.ovf_cap) {
+                A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = s_far_idx[e];
+                A.ovf_mask[(size_t)b * C.ovf_cap + gpos] = s_far_mask[e];
+            } else {
+                atomicOr(A.err, EPR_DEVERR_OVERFLOW);
+            }
+        }
+    }
+
     // flush: every pixel of the tile inside the grid, once, coalesced
-    for (int i = tid; i < tile; i += kSplatThreads) {
-        const int ly = i >> A.lgTW, lx = i & (TW - 1);
-        const int gy = ty0 + ly, gx = tx0 + lx;
-        if (gy >= ny || gx >= nx) continue;
-        const size_t o = (size_t)b * npix + (size_t)gy * nx + gx;
-        if constexpr (DET) {
-            const unsigned long long* a = reinterpret_cast<const unsigned long long*>(acc);
-            unsigned long long sum = 0ull;
-            for (int s = 0; s < ns; ++s) {
-                const unsigned long long q = a[s * tile + i];
-                sum += q;
-                if (ns > 1) A.Psq[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = q;
+    if constexpr (RESID) {
+        const float4* a4 = reinterpret_cast<const float4*>(acc);
+#pragma unroll
+        for (int k = 0; k < kDq; ++k) {
+            const int i4 = tid + k * kSplatThreads;
+            if (i4 >= nq) continue;
+            const int ly = i4 / tw4, lx = (i4 - ly * tw4) << 2;
+            const int gy = ty0 + ly, gx = tx0 + lx;
+            if (gy >= ny || gx >= nx) continue;
+            const float4 v = a4[i4], d = dreg[k];
+            *reinterpret_cast<float4*>(A.P + (size_t)b * npix + (size_t)gy * nx + gx) =
+                make_float4(d.x - v.x, d.y - v.y, d.z - v.z, d.w - v.w);
+        }
+    } else {
+        for (int i = tid; i < tile; i += kSplatThreads) {
+            const int ly = i >> A.lgTW, lx = i & (TW - 1);
+            const int gy = ty0 + ly, gx = tx0 + lx;
+            if (gy >= ny || gx >= nx) continue;
+            const size_t o = (size_t)b * npix + (size_t)gy * nx + gx;
+            if constexpr (DET) {
+                const unsigned long long* a = reinterpret_cast<const unsigned long long*>(acc);
+                unsigned long long sum = 0ull;
+                for (int s = 0; s < ns; ++s) {
+                    const unsigned long long q = a[s * tile + i];
+                    sum += q;
+                    if (ns > 1) A.Psq[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = q;
+                }
+                A.Pq[o] = sum;
+            } else {
+                const float* a = reinterpret_cast<const float*>(acc);
+                float sum = 0.f;
+                for (int s = 0; s < ns; ++s) {
+                    const float q = a[s * tile + i];
+                    sum += q;
+                    if (ns > 1) A.Ps[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = q;
+                }
+                A.P[o] = sum;
             }
-            A.Pq[o] = sum;
-        } else {
-            const float* a = reinterpret_cast<const float*>(acc);
-            float sum = 0.f;
-            for (int s = 0; s < ns; ++s) {
-                const float q = a[s * tile + i];
-                sum += q;
-                if (ns > 1) A.Ps[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = q;
-            }
-            if constexpr (RESID) A.P[o] = __ldg(&A.D[o]) - sum;
-            else A.P[o] = sum;
         }
     }
 }
 
 // The long-shift sources of the overflow list, added with global atomics.
 template <bool DET, bool RESID>
-__global__ void __launch_bounds__(256) k_splat_overflow(const EprConsts C, const SplatArgs A)
+__global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const SplatArgs A)
 {
     const int b = blockIdx.y;
     if (A.check_done && A.st[b].done) return;
@@ -263,7 +327,7 @@ void launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, in
               cudaStream_t stream)
 {
     k_splat<NS, DET, RESID><<<grid, kSplatThreads, smem, stream>>>(C, A);
-    k_splat_overflow<DET, RESID><<<dim3(32, batch), 256, 0, stream>>>(C, A);
+    k_splat_overflow<DET, RESID><<<dim3(128, batch), 128, 0, stream>>>(C, A);
 }
 
 }  // namespace
@@ -271,8 +335,9 @@ void launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, in
 size_t epr_splat_smem(const EprConsts& C, int TH, int TW)
 {
     const int R = C.smax + 1;
+    const int HX = (R + 1 + 3) & ~3;
     const size_t acc_bytes = (size_t)C.ns * TH * TW * (C.det ? 8 : 4);
-    return ((acc_bytes + 15) & ~size_t(15)) + (size_t)(TH + 2 * R + 2) * (TW + 2 * R + 2) * sizeof(float);
+    return ((acc_bytes + 15) & ~size_t(15)) + (size_t)(TH + 2 * R + 2) * (TW + 2 * HX) * sizeof(float);
 }
 
 // Host launcher: the tile kernel, then the overflow kernel (2 launches).
