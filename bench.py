@@ -155,12 +155,15 @@ def _traffic(kernel: str):
 
 def kernel_bytes_per_px(ns: int) -> dict:
     """Unavoidable reads + writes of each kernel of one iteration.
-    splat:   read T, write P (and P_s when ns > 1)
-    row_fwd: read T, D, P (and P_s), write the packed half spectrum (4 B/px/line)
-    col:     read + write the half spectrum
-    row_inv: read the spectrum, read T, write T'"""
+    mono (float): splat reads T and D and writes the residual D - P;
+                  row_fwd reads T and the residual, writes the packed half
+                  spectrum (4 B/px); col reads + writes the spectrum;
+                  row_inv reads the spectrum and T, writes T'.
+    n_s lines:    splat reads T, writes P and P_s; row_fwd reads T, D, P, P_s,
+                  writes n_s spectra; col 8 B/px/line; row_inv reads n_s
+                  spectra and T, writes T'."""
     if ns == 1:
-        return {"splat": 8, "row_fwd": 16, "col": 8, "row_inv": 12}
+        return {"splat": 12, "row_fwd": 12, "col": 8, "row_inv": 12}
     return {"splat": 8 + 4 * ns, "row_fwd": 12 + 8 * ns, "col": 8 * ns, "row_inv": 8 + 4 * ns}
 
 
