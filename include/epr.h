@@ -131,6 +131,18 @@ epr_status epr_forward(epr_plan_t plan, const float* T, float* P, float* Ps, int
 epr_status epr_adjoint(epr_plan_t plan, const float* T, const float* r, float* g, int line,
                        int batch, void* stream);
 
+/* Vector-Jacobian product of the non-local forward model (not in the paper:
+ * the analytic transpose of Eq. 3 with the shift of Eq. 2 and the intensity
+ * of Eq. 7, for calibration by gradient descent).  With gbar = dF/dP for
+ * `batch` projections, writes Tbar = dF/dT and, when the host arrays are not
+ * NULL, delta_bar[batch][n_lines] = dF/ddelta_s, beta_bar[batch][n_lines] =
+ * dF/dbeta_s and L_bar[batch] = dF/dL.  Where a mapped point sits exactly on
+ * a pixel boundary the transport is not differentiable; the right
+ * derivative is returned.  Synchronises the stream when scalars or host
+ * buffers are requested. */
+epr_status epr_vjp(epr_plan_t plan, const float* T, const float* gbar, float* Tbar,
+                   double* delta_bar, double* beta_bar, double* L_bar, int batch, void* stream);
+
 /* Paganin-type preconditioner of line `line`, in place: g <- Re F^-1[H_s F[g]],
  * periodic, no padding. */
 epr_status epr_precondition(epr_plan_t plan, float* g, int line, int batch, void* stream);

@@ -550,6 +550,106 @@ int orc_precondition(int ny, int nx, double p, double L, int n_lines,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Vector-Jacobian product of the non-local forward (not in the paper; the  */
+/* analytic transpose of Eq. 3 with Eq. 2, 6, 7 as read in R1, R2, R9).      */
+/* ------------------------------------------------------------------------ */
+
+/* Transpose of the unit-spacing numpy-gradient stencil along one axis of
+ * length n (>= 3), applied to v with stride `st` over n entries starting at
+ * v0: out[x] = sum_j dG[j]/da[x] v[j]. */
+static double gT(const double* v0, size_t st, int n, int x)
+{
+    double acc = 0.0;
+    /* interior rows j = x-1 (coefficient +1/2) and j = x+1 (-1/2) */
+    if (x - 1 >= 1 && x - 1 <= n - 2) acc += 0.5 * v0[(size_t)(x - 1) * st];
+    if (x + 1 >= 1 && x + 1 <= n - 2) acc -= 0.5 * v0[(size_t)(x + 1) * st];
+    /* one-sided edges: G[0] = a[1] - a[0], G[n-1] = a[n-1] - a[n-2] */
+    if (x == 1) acc += v0[0];
+    if (x == 0) acc -= v0[0];
+    if (x == n - 1) acc += v0[(size_t)(n - 1) * st];
+    if (x == n - 2) acc -= v0[(size_t)(n - 1) * st];
+    return acc;
+}
+
+/* Given gbar = dF/dP, returns Tbar = dF/dtau, and per line dF/ddelta_s,
+ * dF/dbeta_s and dF/dL.  Per line s and source pixel with mapped point
+ * (x + u_x, y + u_y) and corner values g00, g10, g01, g11 of gbar (0 outside
+ * the grid):
+ *   through I_s = f_s exp(-mu_s tau):  -mu_s I_s (M_s^* gbar)
+ *   through u_s = c_s G[tau]:          c_s G^T[ubar_s], with the derivative of
+ *     the bilinear weights in the target coordinates,
+ *     ubar_x = I_s [(1-d_y)(g10 - g00) + d_y (g11 - g01)],
+ *     ubar_y = I_s [(1-d_x)(g01 - g00) + d_x (g11 - g10)]
+ *   (the right derivative where a target crosses an integer);
+ *   scalars: c_s = -L delta_s / p^2 gives cbar_s = <ubar_s, G[tau]>,
+ *   deltabar_s = -L / p^2 cbar_s, Lbar = sum_s -delta_s / p^2 cbar_s;
+ *   mu_s = 2 k_s beta_s gives mubar_s = -<tau I_s, M_s^* gbar>, betabar_s =
+ *   2 k_s mubar_s. */
+int orc_vjp(int ny, int nx, double p, double L, int n_lines, const double* E_keV,
+            const double* delta, const double* beta, const double* weights,
+            const double* T, const double* gbar, double* Tbar, double* delta_bar,
+            double* beta_bar, double* L_bar)
+{
+    if (ny < 3 || nx < 3) return ORC_EINVAL;
+    orc_lines ln;
+    int st = lines_init(&ln, n_lines, E_keV, delta, beta, weights, L, p);
+    size_t n = (size_t)nx * (size_t)ny;
+    double *gy = alloc_n(n), *gx = alloc_n(n), *vy = alloc_n(n), *vx = alloc_n(n);
+    if (st == ORC_OK && (!gy || !gx || !vy || !vx)) st = ORC_ENOMEM;
+    if (st == ORC_OK) {
+        orc_gradient(ny, nx, T, gy, gx);
+        for (size_t i = 0; i < n; ++i) {
+            Tbar[i] = 0.0;
+            vy[i] = 0.0;
+            vx[i] = 0.0;
+        }
+        double lbar = 0.0;
+        for (int s = 0; s < ln.n_lines; ++s) {
+            double cbar = 0.0, mubar = 0.0;
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t i = IDX(y, x);
+                    double ux = ln.c[s] * gx[i], uy = ln.c[s] * gy[i];
+                    double xt = (double)x + ux, yt = (double)y + uy;
+                    double fx0 = floor(xt), fy0 = floor(yt);
+                    double dx = xt - fx0, dy = yt - fy0;
+                    double g[4];
+                    int ox[4] = {0, 1, 0, 1}, oy[4] = {0, 0, 1, 1};
+                    for (int c = 0; c < 4; ++c) {
+                        double cx = fx0 + ox[c], cy = fy0 + oy[c];
+                        g[c] = (cx >= 0.0 && cx < (double)nx && cy >= 0.0 && cy < (double)ny)
+                                   ? gbar[IDX((int)cy, (int)cx)]
+                                   : 0.0;
+                    }
+                    double a = (1.0 - dx) * (1.0 - dy) * g[0] + dx * (1.0 - dy) * g[1] +
+                               (1.0 - dx) * dy * g[2] + dx * dy * g[3];
+                    double Is = ln.f[s] * exp(-ln.mu[s] * T[i]);
+                    Tbar[i] += -ln.mu[s] * Is * a;
+                    double ubx = Is * ((1.0 - dy) * (g[1] - g[0]) + dy * (g[3] - g[2]));
+                    double uby = Is * ((1.0 - dx) * (g[2] - g[0]) + dx * (g[3] - g[1]));
+                    vx[i] += ln.c[s] * ubx;
+                    vy[i] += ln.c[s] * uby;
+                    cbar += ubx * gx[i] + uby * gy[i];
+                    mubar += -T[i] * Is * a;
+                }
+            if (delta_bar) delta_bar[s] = -L / (p * p) * cbar;
+            if (beta_bar) beta_bar[s] = 2.0 * ln.k[s] * mubar;
+            lbar += -ln.delta[s] / (p * p) * cbar;
+        }
+        if (L_bar) *L_bar = lbar;
+        /* G^T of the accumulated shift adjoints */
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                Tbar[IDX(y, x)] += gT(vx + IDX(y, 0), 1, nx, x);
+                Tbar[IDX(y, x)] += gT(vy + x, (size_t)nx, ny, y);
+            }
+    }
+    free(gy); free(gx); free(vy); free(vx);
+    lines_free(&ln);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Iterative inversion ("Iterative inversion (local and non-local)").       */
 /* ------------------------------------------------------------------------ */
 

@@ -66,6 +66,7 @@ def _load():
             lib.orc_forward.argtypes = [i, i, f, f, i, d, d, d, d, i, d, d, d, d]
             lib.orc_adjoint.argtypes = [i, i, f, f, i, d, d, d, d, i, d, d, d]
             lib.orc_precondition.argtypes = [i, i, f, f, i, d, d, d, d, i, d]
+            lib.orc_vjp.argtypes = [i, i, f, f, i, d, d, d, d, d, d, d, d, d, d]
             lib.orc_solve.argtypes = [i, i, f, f, i, d, d, d, d, i, d, d, i, f, f, f,
                                       d, d, ip]
             _lib = lib
@@ -198,6 +199,20 @@ def precondition(lines: Lines, g, line=0):
     st = _load().orc_precondition(g.shape[0], g.shape[1], *lines._args(), line, _p(g))
     _check(st, "precondition")
     return g
+
+
+def vjp(lines: Lines, T, gbar):
+    """(Tbar, delta_bar[n], beta_bar[n], L_bar) of F = <gbar, P(T)> for the
+    non-local forward."""
+    T, gbar = _c(T), _c(gbar)
+    Tbar = np.empty_like(T)
+    db = np.zeros(lines.n)
+    bb = np.zeros(lines.n)
+    lb = np.zeros(1)
+    st = _load().orc_vjp(T.shape[0], T.shape[1], *lines._args(), _p(T), _p(gbar), _p(Tbar),
+                         _p(db), _p(bb), _p(lb))
+    _check(st, "vjp")
+    return Tbar, db, bb, float(lb[0])
 
 
 def solve(lines: Lines, D, T0=None, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8,

@@ -52,6 +52,9 @@ cudaError_t epr_launch_fx_to_float(const unsigned long long* q, float* out, size
 cudaError_t epr_launch_local(const EprConsts& C, const EprWork& W, const float* T, float* P, float* Ps,
                              int order, int batch, int check_done, cudaStream_t stream);
 cudaError_t epr_local_init();
+cudaError_t epr_launch_vjp(const EprConsts& C, const float* T, const float* gbar, float* Tbar,
+                           float* vx, float* vy, double* part, int nblk, int batch,
+                           cudaStream_t stream);
 
 // --- launch accounting -------------------------------------------------------
 static std::atomic<long long> g_launches(0);
@@ -115,6 +118,12 @@ struct epr_plan_s {
     int gkernels;
     bool has_graph;
     cudaGraphExec_t prof_exec;   // last profiled solve
+    // vector-Jacobian product workspace (allocated on first use)
+    float* vjp_vx;
+    float* vjp_vy;
+    double* vjp_part;
+    double* h_vjp_part;
+    int vjp_cap;
 };
 
 namespace {
@@ -635,6 +644,10 @@ void epr_plan_destroy(epr_plan_t p)
     if (p->h_st) cudaFreeHost(p->h_st);
     if (p->h_hist) cudaFreeHost(p->h_hist);
     if (p->prof_exec) cudaGraphExecDestroy(p->prof_exec);
+    if (p->vjp_vx) cudaFree(p->vjp_vx);
+    if (p->vjp_vy) cudaFree(p->vjp_vy);
+    if (p->vjp_part) cudaFree(p->vjp_part);
+    if (p->h_vjp_part) cudaFreeHost(p->h_vjp_part);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto& r : p->recs) {
         cudaEventDestroy(r.a);
@@ -739,6 +752,72 @@ epr_status epr_solve_local(epr_plan_t p, const float* D, float* T, int batch, in
 {
     if (order != 1 && order != 2) return EPR_ERR_INVALID_ARG;
     return solve_common(p, D, T, batch, order, opts, info, (cudaStream_t)stream);
+}
+
+epr_status epr_vjp(epr_plan_t p, const float* T, const float* gbar, float* Tbar,
+                   double* delta_bar, double* beta_bar, double* L_bar, int batch, void* stream)
+{
+    if (!p || !T || !gbar || !Tbar || batch <= 0) return EPR_ERR_INVALID_ARG;
+    if (p->C.nx < 3 || p->C.ny < 3) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const EprConsts& C = p->C;
+    const size_t npix = (size_t)C.nx * C.ny, n = (size_t)batch * npix;
+    const int nblk = 256;
+    if (batch > p->vjp_cap) {
+        EPR_TRY(cudaStreamSynchronize(s));
+        if (p->vjp_vx) cudaFree(p->vjp_vx);
+        if (p->vjp_vy) cudaFree(p->vjp_vy);
+        if (p->vjp_part) cudaFree(p->vjp_part);
+        if (p->h_vjp_part) cudaFreeHost(p->h_vjp_part);
+        p->vjp_vx = p->vjp_vy = nullptr;
+        p->vjp_part = p->h_vjp_part = nullptr;
+        p->vjp_cap = 0;
+        EPR_TRY(cudaMalloc((void**)&p->vjp_vx, n * sizeof(float)));
+        EPR_TRY(cudaMalloc((void**)&p->vjp_vy, n * sizeof(float)));
+        EPR_TRY(cudaMalloc((void**)&p->vjp_part, (size_t)batch * nblk * 2 * C.ns * sizeof(double)));
+        EPR_TRY(cudaMallocHost((void**)&p->h_vjp_part, (size_t)batch * nblk * 2 * C.ns * sizeof(double)));
+        p->vjp_cap = batch;
+    }
+    float *Td, *gd, *Tbd;
+    bool sT, sg, sTb;
+    epr_status st = resolve(p, 0, T, n, true, s, &Td, &sT);
+    if (st == EPR_OK) st = resolve(p, 1, gbar, n, true, s, &gd, &sg);
+    if (st == EPR_OK) st = resolve(p, 2, Tbar, n, false, s, &Tbd, &sTb);
+    if (st != EPR_OK) return st;
+    {
+        ProfScope ps(p, EPR_KERNEL_OTHER, s);
+        EPR_TRY(epr_launch_vjp(C, Td, gd, Tbd, p->vjp_vx, p->vjp_vy, p->vjp_part, nblk, batch, s));
+    }
+    if (sTb) EPR_TRY(cudaMemcpyAsync(Tbar, Tbd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    const bool scalars = delta_bar || beta_bar || L_bar;
+    if (scalars) {
+        const size_t np = (size_t)batch * nblk * 2 * C.ns;
+        EPR_TRY(cudaMemcpyAsync(p->h_vjp_part, p->vjp_part, np * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    }
+    if (scalars || sTb) EPR_TRY(cudaStreamSynchronize(s));
+    if (scalars) {
+        const double p2 = p->pixel * p->pixel;
+        for (int b = 0; b < batch; ++b) {
+            double lbar = 0.0;
+            for (int l = 0; l < C.ns; ++l) {
+                double cbar = 0.0, mubar = 0.0;
+                for (int k = 0; k < nblk; ++k) {
+                    const double* q = p->h_vjp_part + ((size_t)b * nblk + k) * 2 * C.ns;
+                    cbar += q[2 * l];
+                    mubar += q[2 * l + 1];
+                }
+                const double lam = kHcEvM / (p->E[l] * 1e3);
+                const double kk = 2.0 * kPi / lam;
+                if (delta_bar) delta_bar[(size_t)b * C.ns + l] = -p->L / p2 * cbar;
+                if (beta_bar) beta_bar[(size_t)b * C.ns + l] = 2.0 * kk * mubar;
+                lbar += -p->delta[l] / p2 * cbar;
+            }
+            if (L_bar) L_bar[b] = lbar;
+        }
+    }
+    return EPR_OK;
 }
 
 epr_status epr_check_device_status(epr_plan_t p, void* stream)

@@ -38,7 +38,7 @@ EPR_MODEL_LOCAL2 = 2
 SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
            "epr_precondition", "epr_solve_nonlocal", "epr_solve_local",
            "epr_check_device_status", "epr_status_string", "epr_launch_count",
-           "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc")
+           "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc", "epr_vjp")
 
 KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 
@@ -109,6 +109,8 @@ def load(path: str | None = None):
         lib.epr_profile_read.restype = i
         lib.epr_precondition_noalloc.argtypes = [vp, i, i, d, d, d, d, d, i, vp]
         lib.epr_precondition_noalloc.restype = i
+        lib.epr_vjp.argtypes = [vp, vp, vp, vp, dp, dp, dp, i, vp]
+        lib.epr_vjp.restype = i
         lib.epr_launch_count.argtypes = []
         lib.epr_launch_count.restype = ctypes.c_longlong
         _lib = lib
@@ -204,6 +206,21 @@ def epr_precondition_noalloc(g, nx, ny, pixel_m, L_m, energy_keV, delta, beta, b
                                            float(energy_keV), float(delta), float(beta),
                                            int(batch), _stream(stream)),
            "epr_precondition_noalloc")
+
+
+def epr_vjp(plan, T, gbar, Tbar, n_lines, batch=1, scalars=True, stream=None):
+    """Tbar <- dF/dT for F = <gbar, P(T)>; returns (delta_bar [batch][n_lines],
+    beta_bar [batch][n_lines], L_bar [batch]) when `scalars`, else None."""
+    if scalars:
+        db = np.zeros((batch, n_lines))
+        bb = np.zeros((batch, n_lines))
+        lb = np.zeros(batch)
+        ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in (db, bb, lb)]
+    else:
+        ptrs = [None, None, None]
+    _check(load().epr_vjp(plan, _ptr(T), _ptr(gbar), _ptr(Tbar), *ptrs, int(batch),
+                          _stream(stream)), "epr_vjp")
+    return (db, bb, lb) if scalars else None
 
 
 def _solve_opts(n_iter, omega, tol, eps_I, init):
