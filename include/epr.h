@@ -76,7 +76,12 @@ typedef struct {
                               EPR_ERR_SHIFT_OVERFLOW. */
     int use_graphs;        /* 1 = capture solver iterations in a CUDA graph
                               and replay it (default 1). */
-    int reserved[8];       /* must be zero */
+    int autotune;          /* 1 = after the first solve, time the splat's tile
+                              shapes and reach on that solve's result and keep
+                              the fastest for later solves (default 0).  The
+                              choice changes only the summation order of the
+                              float splat (fixed-point results are unchanged). */
+    int reserved[7];       /* must be zero */
 } epr_options;
 
 /* Solver options. */
@@ -206,6 +211,32 @@ typedef enum {
  * records. */
 epr_status epr_profile_enable(epr_plan_t plan, int enable);
 epr_status epr_profile_read(epr_plan_t plan, int* launches, double* total_ms);
+
+/* Batched solve of projections of uneven sizes (not in the paper: serving
+ * many projections of a scan at once).  A batch object holds the geometry
+ * and spectrum shared by all projections and one plan per projection size,
+ * created on first use.  Each size group is gathered into plan-owned device
+ * memory and solved as one batched, graph-replayed solve on its own stream;
+ * the groups run concurrently and join the caller's stream.  Every
+ * projection stops on its own convergence test (opts->tol).  info, when
+ * not NULL, is filled per projection in the order of `descs` (histories are
+ * [n][opts->n_iter]); the call then synchronises. */
+typedef struct epr_batch_s* epr_batch_t;
+
+typedef struct {
+    int nx, ny;        /* size of this projection (2^a 3^b, a >= 3, 16..4096) */
+    const float* D;    /* measured data [ny][nx], device or host */
+    float* T;          /* thickness [ny][nx]: initial value when opts->init = 1,
+                          result on return; device or host */
+} epr_batch_desc;
+
+epr_status epr_batch_create(epr_batch_t* out, double pixel_m, double L_m, int n_lines,
+                            const double* energy_keV, const double* delta, const double* beta,
+                            const double* weights, const epr_options* opt);
+void epr_batch_destroy(epr_batch_t batch);
+epr_status epr_solve_nonlocal_batched(epr_batch_t batch, const epr_batch_desc* descs, int n,
+                                      const epr_solve_opts* opts, epr_solve_info* info,
+                                      void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* epr_status_string(epr_status s);

@@ -118,6 +118,7 @@ struct epr_plan_s {
     int gkernels;
     bool has_graph;
     cudaGraphExec_t prof_exec;   // last profiled solve
+    bool tuned;                  // autotuner has run
     // vector-Jacobian product workspace (allocated on first use)
     float* vjp_vx;
     float* vjp_vy;
@@ -379,6 +380,103 @@ epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, cons
     return EPR_OK;
 }
 
+// Per-projection results of the last solve of plan p (batch projections),
+// written at offset `first` of the caller's arrays.  Synchronises s.
+epr_status collect_info(epr_plan_s* p, int batch, int n_iter, epr_solve_info* info, cudaStream_t s,
+                        int first)
+{
+    const int nh = p->W.hist_len;
+    EPR_TRY(cudaMemcpyAsync(p->h_st, p->W.st, (size_t)batch * sizeof(EprProjState),
+                            cudaMemcpyDeviceToHost, s));
+    EPR_TRY(cudaMemcpyAsync(p->h_hist, p->W.rho_hist, (size_t)batch * nh * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    EPR_TRY(cudaMemcpyAsync(p->h_hist + (size_t)batch * nh, p->W.kappa_hist,
+                            (size_t)batch * nh * sizeof(double), cudaMemcpyDeviceToHost, s));
+    unsigned int herr = 0;
+    EPR_TRY(cudaMemcpyAsync(&herr, p->W.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    EPR_TRY(cudaStreamSynchronize(s));
+    long long ovf = 0;
+    for (int b = 0; b < batch; ++b) {
+        const EprProjState& ps = p->h_st[b];
+        const int k = ps.iters;
+        const int j = first + b;
+        if (info->iters) info->iters[j] = k;
+        if (info->rho) info->rho[j] = k > 0 ? p->h_hist[(size_t)b * nh + k - 1] : 0.0;
+        if (info->kappa) info->kappa[j] = k > 0 ? p->h_hist[(size_t)(batch + b) * nh + k - 1] : 0.0;
+        for (int i = 0; i < n_iter; ++i) {
+            const bool ran = i < k;
+            if (info->rho_hist)
+                info->rho_hist[(size_t)j * n_iter + i] = ran ? p->h_hist[(size_t)b * nh + i] : 0.0;
+            if (info->kappa_hist)
+                info->kappa_hist[(size_t)j * n_iter + i] =
+                    ran ? p->h_hist[(size_t)(batch + b) * nh + i] : 0.0;
+        }
+        ovf += ps.ovf_total;
+    }
+    if (first == 0) info->overflow_sources = 0;
+    info->overflow_sources += ovf;
+    if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
+    return EPR_OK;
+}
+
+// Times the splat's tile shapes and reach on the thickness T of the solve
+// that just ran (the real shift field), keeps the fastest and drops the
+// cached graph.  Changes only the float summation order of the splat.
+epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int batch, cudaStream_t s)
+{
+    p->tuned = true;
+    const bool resid = p->C.ns == 1 && !p->C.det;
+    const int tiles[4][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}};
+    const int reaches[3] = {3, 4, 6};
+    const EprConsts saved = p->C;
+    const int sTH = p->splat_TH, sTW = p->splat_TW;
+    int optin = 0;
+    EPR_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    float best = 1e30f;
+    int bTH = sTH, bTW = sTW, bR = saved.smax;
+    cudaEvent_t e0, e1;
+    EPR_TRY(cudaEventCreate(&e0));
+    EPR_TRY(cudaEventCreate(&e1));
+    for (const auto& t : tiles) {
+        for (int r : reaches) {
+            p->C.smax = r;
+            if ((size_t)p->C.ns * t[0] * t[1] * (p->C.det ? 8 : 4) > 65536) continue;
+            if (epr_splat_smem(p->C, t[0], t[1]) + 4096 > (size_t)optin) continue;
+            p->splat_TH = t[0];
+            p->splat_TW = t[1];
+            EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)batch * sizeof(EprProjState), s));
+            epr_status st = launch_forward(p, T, resid ? D : nullptr, 0, batch, EPR_MODEL_NONLOCAL, 0, s);
+            if (st != EPR_OK) return st;
+            EPR_TRY(cudaEventRecord(e0, s));
+            for (int k = 0; k < 4; ++k) {
+                st = launch_forward(p, T, resid ? D : nullptr, (k + 1) & 1, batch, EPR_MODEL_NONLOCAL, 0, s);
+                if (st != EPR_OK) return st;
+            }
+            EPR_TRY(cudaEventRecord(e1, s));
+            EPR_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            EPR_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bTH = t[0];
+                bTW = t[1];
+                bR = r;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->C = saved;
+    p->C.smax = bR;
+    p->splat_TH = bTH;
+    p->splat_TW = bTW;
+    if (p->has_graph) {
+        cudaGraphExecDestroy(p->gexec);
+        p->has_graph = false;
+    }
+    return EPR_OK;
+}
+
 epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int model,
                         const epr_solve_opts* o, epr_solve_info* info, cudaStream_t s)
 {
@@ -454,37 +552,11 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
     }
     if (sT) EPR_TRY(cudaMemcpyAsync(T, Td, n * sizeof(float), cudaMemcpyDeviceToHost, s));
 
-    if (info) {
-        const int nh = p->W.hist_len;
-        EPR_TRY(cudaMemcpyAsync(p->h_st, p->W.st, (size_t)batch * sizeof(EprProjState),
-                                cudaMemcpyDeviceToHost, s));
-        EPR_TRY(cudaMemcpyAsync(p->h_hist, p->W.rho_hist, (size_t)batch * nh * sizeof(double),
-                                cudaMemcpyDeviceToHost, s));
-        EPR_TRY(cudaMemcpyAsync(p->h_hist + (size_t)batch * nh, p->W.kappa_hist,
-                                (size_t)batch * nh * sizeof(double), cudaMemcpyDeviceToHost, s));
-        unsigned int herr = 0;
-        EPR_TRY(cudaMemcpyAsync(&herr, p->W.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
-        EPR_TRY(cudaStreamSynchronize(s));
-        long long ovf = 0;
-        for (int b = 0; b < batch; ++b) {
-            const EprProjState& ps = p->h_st[b];
-            const int k = ps.iters;
-            if (info->iters) info->iters[b] = k;
-            if (info->rho) info->rho[b] = k > 0 ? p->h_hist[(size_t)b * nh + k - 1] : 0.0;
-            if (info->kappa) info->kappa[b] = k > 0 ? p->h_hist[(size_t)(batch + b) * nh + k - 1] : 0.0;
-            for (int i = 0; i < o->n_iter; ++i) {
-                const bool ran = i < k;
-                if (info->rho_hist)
-                    info->rho_hist[(size_t)b * o->n_iter + i] = ran ? p->h_hist[(size_t)b * nh + i] : 0.0;
-                if (info->kappa_hist)
-                    info->kappa_hist[(size_t)b * o->n_iter + i] =
-                        ran ? p->h_hist[(size_t)(batch + b) * nh + i] : 0.0;
-            }
-            ovf += ps.ovf_total;
-        }
-        info->overflow_sources = ovf;
-        if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
+    if (p->opt.autotune && !p->tuned && model == EPR_MODEL_NONLOCAL && o->n_iter > 0) {
+        st = autotune_splat(p, Dd, Td, batch, s);
+        if (st != EPR_OK) return st;
     }
+    if (info) return collect_info(p, batch, o->n_iter, info, s, 0);
     return EPR_OK;
 }
 
@@ -534,11 +606,11 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     if (n_lines < 1 || n_lines > EPR_MAX_LINES || !(pixel_m > 0.0) || !(L_m >= 0.0))
         return EPR_ERR_INVALID_ARG;
     if (!size_ok(nx) || !size_ok(ny)) return EPR_ERR_UNSUPPORTED_SIZE;
-    epr_options o = {4, 0, 0, 1, {0}};
+    epr_options o = {4, 0, 0, 1, 0, {0}};
     if (opt) o = *opt;
     if (o.max_shift_px < 1 || o.max_shift_px > EPR_MAX_SHIFT || o.overflow_capacity < 0)
         return EPR_ERR_INVALID_ARG;
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 7; ++i)
         if (o.reserved[i] != 0) return EPR_ERR_INVALID_ARG;
     double wsum = 0.0;
     for (int s = 0; s < n_lines; ++s) {
@@ -877,6 +949,223 @@ epr_status epr_profile_read(epr_plan_t p, int* launches, double* total_ms)
         p->pool.push_back(r.b);
     }
     p->recs.clear();
+    return EPR_OK;
+}
+
+}  // extern "C"
+
+// --- batched solve of uneven sizes ----------------------------------------------
+struct epr_batch_s {
+    double pixel, L;
+    int ns;
+    double E[EPR_MAX_LINES], delta[EPR_MAX_LINES], beta[EPR_MAX_LINES], w[EPR_MAX_LINES];
+    epr_options opt;
+    int device;
+    struct Group {
+        int nx, ny;
+        epr_plan_t plan;
+        float* D;       // gathered data [cap][ny][nx]
+        float* T;       // gathered thickness
+        int cap;
+        cudaStream_t stream;
+        cudaEvent_t done;
+    };
+    std::vector<Group> groups;
+    cudaEvent_t start;
+};
+
+namespace {
+
+// Index of the group for size nx x ny with room for `count` projections
+// (created or grown on demand), or -1 with *st set.
+int batch_group(epr_batch_s* bp, int nx, int ny, int count, epr_status* st)
+{
+    *st = EPR_OK;
+    for (size_t gi = 0; gi < bp->groups.size(); ++gi) {
+        epr_batch_s::Group& g = bp->groups[gi];
+        if (g.nx == nx && g.ny == ny) {
+            if (g.cap < count) {
+                cudaStreamSynchronize(g.stream);
+                cudaFree(g.D);
+                cudaFree(g.T);
+                g.D = g.T = nullptr;
+                g.cap = 0;
+                const size_t n = (size_t)count * nx * ny;
+                if (cudaMalloc((void**)&g.D, n * sizeof(float)) != cudaSuccess ||
+                    cudaMalloc((void**)&g.T, n * sizeof(float)) != cudaSuccess) {
+                    *st = EPR_ERR_OOM;
+                    return -1;
+                }
+                g.cap = count;
+            }
+            return (int)gi;
+        }
+    }
+    epr_batch_s::Group g = {};
+    g.nx = nx;
+    g.ny = ny;
+    *st = epr_plan_create(&g.plan, nx, ny, bp->pixel, bp->L, bp->ns, bp->E, bp->delta, bp->beta,
+                          bp->w, &bp->opt);
+    if (*st != EPR_OK) return -1;
+    const size_t n = (size_t)count * nx * ny;
+    if (cudaMalloc((void**)&g.D, n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&g.T, n * sizeof(float)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) {
+        *st = EPR_ERR_OOM;
+        if (g.D) cudaFree(g.D);
+        if (g.T) cudaFree(g.T);
+        epr_plan_destroy(g.plan);
+        return -1;
+    }
+    g.cap = count;
+    bp->groups.push_back(g);
+    return (int)bp->groups.size() - 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+epr_status epr_batch_create(epr_batch_t* out, double pixel_m, double L_m, int n_lines,
+                            const double* energy_keV, const double* delta, const double* beta,
+                            const double* weights, const epr_options* opt)
+{
+    if (!out) return EPR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!energy_keV || !delta || !beta || !weights || n_lines < 1 || n_lines > EPR_MAX_LINES ||
+        !(pixel_m > 0.0) || !(L_m >= 0.0))
+        return EPR_ERR_INVALID_ARG;
+    epr_batch_s* bp = new (std::nothrow) epr_batch_s();
+    if (!bp) return EPR_ERR_OOM;
+    bp->pixel = pixel_m;
+    bp->L = L_m;
+    bp->ns = n_lines;
+    for (int s = 0; s < n_lines; ++s) {
+        bp->E[s] = energy_keV[s];
+        bp->delta[s] = delta[s];
+        bp->beta[s] = beta[s];
+        bp->w[s] = weights[s];
+    }
+    epr_options o = {4, 0, 0, 1, 0, {0}};
+    if (opt) o = *opt;
+    bp->opt = o;
+    if (cudaGetDevice(&bp->device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bp->start, cudaEventDisableTiming) != cudaSuccess) {
+        delete bp;
+        return EPR_ERR_CUDA;
+    }
+    *out = bp;
+    return EPR_OK;
+}
+
+void epr_batch_destroy(epr_batch_t bp)
+{
+    if (!bp) return;
+    cudaSetDevice(bp->device);
+    cudaDeviceSynchronize();
+    for (auto& g : bp->groups) {
+        epr_plan_destroy(g.plan);
+        cudaFree(g.D);
+        cudaFree(g.T);
+        cudaStreamDestroy(g.stream);
+        cudaEventDestroy(g.done);
+    }
+    cudaEventDestroy(bp->start);
+    delete bp;
+}
+
+epr_status epr_solve_nonlocal_batched(epr_batch_t bp, const epr_batch_desc* descs, int n,
+                                      const epr_solve_opts* opts, epr_solve_info* info,
+                                      void* stream)
+{
+    if (!bp || !descs || n <= 0 || !opts) return EPR_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!descs[i].D || !descs[i].T) return EPR_ERR_INVALID_ARG;
+        if (!size_ok(descs[i].nx) || !size_ok(descs[i].ny)) return EPR_ERR_UNSUPPORTED_SIZE;
+    }
+    EPR_TRY(cudaSetDevice(bp->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // size groups, in order of first appearance
+    std::vector<std::pair<int, int>> sizes;
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < n; ++i) {
+        size_t k = 0;
+        while (k < sizes.size() && !(sizes[k].first == descs[i].nx && sizes[k].second == descs[i].ny)) ++k;
+        if (k == sizes.size()) {
+            sizes.push_back({descs[i].nx, descs[i].ny});
+            members.emplace_back();
+        }
+        members[k].push_back(i);
+    }
+    EPR_TRY(cudaEventRecord(bp->start, s));
+    std::vector<int> used;
+    for (size_t k = 0; k < sizes.size(); ++k) {
+        const int cnt = (int)members[k].size();
+        epr_status st;
+        const int gi = batch_group(bp, sizes[k].first, sizes[k].second, cnt, &st);
+        if (gi < 0) return st;
+        used.push_back(gi);
+        epr_batch_s::Group* g = &bp->groups[gi];
+        const size_t npix = (size_t)g->nx * g->ny;
+        EPR_TRY(cudaStreamWaitEvent(g->stream, bp->start, 0));
+        for (int j = 0; j < cnt; ++j) {
+            const epr_batch_desc& d = descs[members[k][j]];
+            EPR_TRY(cudaMemcpyAsync(g->D + j * npix, d.D, npix * sizeof(float), cudaMemcpyDefault,
+                                    g->stream));
+            if (opts->init)
+                EPR_TRY(cudaMemcpyAsync(g->T + j * npix, d.T, npix * sizeof(float),
+                                        cudaMemcpyDefault, g->stream));
+        }
+        st = solve_common(g->plan, g->D, g->T, cnt, EPR_MODEL_NONLOCAL, opts, nullptr, g->stream);
+        if (st != EPR_OK) return st;
+        for (int j = 0; j < cnt; ++j) {
+            const epr_batch_desc& d = descs[members[k][j]];
+            EPR_TRY(cudaMemcpyAsync(d.T, g->T + j * npix, npix * sizeof(float), cudaMemcpyDefault,
+                                    g->stream));
+        }
+        EPR_TRY(cudaEventRecord(g->done, g->stream));
+        EPR_TRY(cudaStreamWaitEvent(s, g->done, 0));
+    }
+    if (info) {
+        // per-projection results in the order of descs
+        epr_solve_info part = *info;
+        std::vector<int> it_tmp;
+        std::vector<double> r_tmp, k_tmp, rh_tmp, kh_tmp;
+        epr_status worst = EPR_OK;
+        info->overflow_sources = 0;
+        for (size_t k = 0; k < sizes.size(); ++k) {
+            const int cnt = (int)members[k].size();
+            const int nh = opts->n_iter > 0 ? opts->n_iter : 1;
+            it_tmp.assign(cnt, 0);
+            r_tmp.assign(cnt, 0.0);
+            k_tmp.assign(cnt, 0.0);
+            rh_tmp.assign((size_t)cnt * nh, 0.0);
+            kh_tmp.assign((size_t)cnt * nh, 0.0);
+            part.iters = it_tmp.data();
+            part.rho = r_tmp.data();
+            part.kappa = k_tmp.data();
+            part.rho_hist = rh_tmp.data();
+            part.kappa_hist = kh_tmp.data();
+            part.overflow_sources = 0;
+            const epr_batch_s::Group& g = bp->groups[used[k]];
+            epr_status st = collect_info(g.plan, cnt, opts->n_iter, &part, g.stream, 0);
+            if (st != EPR_OK) worst = st;
+            for (int j = 0; j < cnt; ++j) {
+                const int i = members[k][j];
+                if (info->iters) info->iters[i] = it_tmp[j];
+                if (info->rho) info->rho[i] = r_tmp[j];
+                if (info->kappa) info->kappa[i] = k_tmp[j];
+                for (int q = 0; q < opts->n_iter; ++q) {
+                    if (info->rho_hist) info->rho_hist[(size_t)i * opts->n_iter + q] = rh_tmp[(size_t)j * opts->n_iter + q];
+                    if (info->kappa_hist) info->kappa_hist[(size_t)i * opts->n_iter + q] = kh_tmp[(size_t)j * opts->n_iter + q];
+                }
+            }
+            info->overflow_sources += part.overflow_sources;
+        }
+        EPR_TRY(cudaStreamSynchronize(s));
+        return worst;
+    }
     return EPR_OK;
 }
 

@@ -38,7 +38,8 @@ EPR_MODEL_LOCAL2 = 2
 SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
            "epr_precondition", "epr_solve_nonlocal", "epr_solve_local",
            "epr_check_device_status", "epr_status_string", "epr_launch_count",
-           "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc", "epr_vjp")
+           "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc", "epr_vjp",
+           "epr_batch_create", "epr_batch_destroy", "epr_solve_nonlocal_batched")
 
 KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 
@@ -46,7 +47,12 @@ KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 class epr_options(ctypes.Structure):
     _fields_ = [("max_shift_px", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("overflow_capacity", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class epr_batch_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("D", ctypes.c_void_p),
+                ("T", ctypes.c_void_p)]
 
 
 class epr_solve_opts(ctypes.Structure):
@@ -111,6 +117,15 @@ def load(path: str | None = None):
         lib.epr_precondition_noalloc.restype = i
         lib.epr_vjp.argtypes = [vp, vp, vp, vp, dp, dp, dp, i, vp]
         lib.epr_vjp.restype = i
+        lib.epr_batch_create.argtypes = [ctypes.POINTER(vp), d, d, i, dp, dp, dp, dp,
+                                         ctypes.POINTER(epr_options)]
+        lib.epr_batch_create.restype = i
+        lib.epr_batch_destroy.argtypes = [vp]
+        lib.epr_batch_destroy.restype = None
+        lib.epr_solve_nonlocal_batched.argtypes = [vp, ctypes.POINTER(epr_batch_desc), i,
+                                                   ctypes.POINTER(epr_solve_opts),
+                                                   ctypes.POINTER(epr_solve_info), vp]
+        lib.epr_solve_nonlocal_batched.restype = i
         lib.epr_launch_count.argtypes = []
         lib.epr_launch_count.restype = ctypes.c_longlong
         _lib = lib
@@ -163,16 +178,21 @@ def _darr(x):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune):
+    return epr_options(int(max_shift_px), int(bool(deterministic)), int(overflow_capacity),
+                       int(bool(use_graphs)), int(bool(autotune)), (ctypes.c_int * 7)())
+
+
 def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
-                    max_shift_px=4, deterministic=False, overflow_capacity=0, use_graphs=True):
+                    max_shift_px=4, deterministic=False, overflow_capacity=0, use_graphs=True,
+                    autotune=False):
     """Returns an opaque plan handle (int)."""
     lib = load()
     E, Ep = _darr(energy_keV)
     dl, dp_ = _darr(delta)
     bt, bp = _darr(beta)
     w, wp = _darr(np.ones(E.size) if weights is None else weights)
-    opt = epr_options(int(max_shift_px), int(bool(deterministic)), int(overflow_capacity),
-                      int(bool(use_graphs)), (ctypes.c_int * 8)())
+    opt = _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune)
     h = ctypes.c_void_p()
     _check(lib.epr_plan_create(ctypes.byref(h), int(nx), int(ny), float(pixel_m), float(L_m),
                                int(E.size), Ep, dp_, bp, wp, ctypes.byref(opt)), "epr_plan_create")
@@ -264,6 +284,45 @@ def epr_solve_local(plan, D, T, batch=1, order=2, n_iter=20, omega=1.0, tol=0.0,
                                 ctypes.byref(info) if info is not None else None,
                                 _stream(stream))
     _check(st, "epr_solve_local")
+    if arrs is not None:
+        arrs["overflow_sources"] = int(info.overflow_sources)
+    return arrs
+
+
+def epr_batch_create(pixel_m, L_m, energy_keV, delta, beta, weights=None, max_shift_px=4,
+                     deterministic=False, overflow_capacity=0, use_graphs=True, autotune=False):
+    """Returns an opaque batch handle (int) for epr_solve_nonlocal_batched."""
+    lib = load()
+    E, Ep = _darr(energy_keV)
+    dl, dp_ = _darr(delta)
+    bt, bp = _darr(beta)
+    w, wp = _darr(np.ones(E.size) if weights is None else weights)
+    opt = _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune)
+    h = ctypes.c_void_p()
+    _check(lib.epr_batch_create(ctypes.byref(h), float(pixel_m), float(L_m), int(E.size), Ep, dp_,
+                                bp, wp, ctypes.byref(opt)), "epr_batch_create")
+    return h.value
+
+
+def epr_batch_destroy(batch):
+    load().epr_batch_destroy(batch)
+
+
+def epr_solve_nonlocal_batched(batch, Ds, Ts, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8,
+                               init=0, want_info=True, stream=None):
+    """Solve projections of uneven sizes: Ds[i], Ts[i] are [ny_i][nx_i] maps.
+    Returns per-projection info (in the order given) when want_info."""
+    n = len(Ds)
+    descs = (epr_batch_desc * n)()
+    for i, (D, T) in enumerate(zip(Ds, Ts)):
+        ny, nx = D.shape[-2], D.shape[-1]
+        descs[i] = epr_batch_desc(int(nx), int(ny), _ptr(D), _ptr(T))
+    opts = _solve_opts(n_iter, omega, tol, eps_I, init)
+    info, arrs = _info(n, n_iter) if want_info else (None, None)
+    st = load().epr_solve_nonlocal_batched(batch, descs, n, ctypes.byref(opts),
+                                           ctypes.byref(info) if info is not None else None,
+                                           _stream(stream))
+    _check(st, "epr_solve_nonlocal_batched")
     if arrs is not None:
         arrs["overflow_sources"] = int(info.overflow_sources)
     return arrs
