@@ -68,6 +68,29 @@ def _dist():
     return rank, world, local
 
 
+def rank_seed(rank: int) -> int:
+    """Replica sharding: every rank solves its own projection (independent
+    units, no data exchanged between ranks)."""
+    return 2000 + rank
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's figure (the job is done when every rank is)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ms_per_step: float, world: int, npix: int) -> float:
+    """2048^2-equivalent projections per second over all ranks: each of the
+    `world` ranks solves one npix projection per step."""
+    return world * (npix / REF_PIX) / (ms_per_step / 1000.0)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -188,7 +211,7 @@ def run_ours(a):
     B.build()
     epr.load()
 
-    wl, tau = ph.ellipsoids_mono(seed=2000 + rank)
+    wl, tau = ph.ellipsoids_mono(seed=rank_seed(rank))
     npix = wl.nx * wl.ny
     plan = epr.Plan(wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights)
     stream = torch.cuda.current_stream()
@@ -240,12 +263,8 @@ def run_ours(a):
     clk = clocks.stop()
     barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * (npix / REF_PIX) / (ms / 1000.0)
+    ms = max_over_ranks(float(np.mean(step_ms)), world, device="cuda")
+    value = whole_job_rate(ms, world, npix)
 
     # convergence figures of this workload
     info = epr.epr_solve_nonlocal(plan.handle, D, T, n_iter=wl.n_iter, omega=wl.omega)
@@ -306,12 +325,8 @@ def run_ours(a):
         e_end.record(stream)
         e_end.synchronize()
         e_times.append(e_start.elapsed_time(e_end))
-    e_ms = float(np.mean(e_times))
-    if world > 1:
-        t = torch.tensor([e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e2e = {"value": round(world * (npix / REF_PIX) / (e_ms / 1000.0), 3), "unit": UNIT,
+    e_ms = max_over_ranks(float(np.mean(e_times)), world, device="cuda")
+    e2e = {"value": round(whole_job_rate(e_ms, world, npix), 3), "unit": UNIT,
            "h2d_bytes_per_step": int(D_host.nbytes), "d2h_bytes_per_step": int(Th.numel() * 4),
            "ms_per_step": round(e_ms, 4)}
 
