@@ -69,8 +69,11 @@ typedef struct {
                               overflow list and are added with global atomics. */
     int deterministic;     /* 1 = accumulate the splat in int64 fixed point
                               (value * 2^40, round to nearest even): results are
-                              bit-identical across runs.  0 = float32 shared
-                              memory atomics (default). */
+                              bit-identical across runs.  0 (default) = the
+                              tile accumulators hold round(value * 2^S) in
+                              uint32, S = 32 - ceil(log2(2 (2 max_shift_px + 3)^2))
+                              (24 at the default reach), and the long-shift
+                              sources are added with float atomics. */
     int overflow_capacity; /* overflow entries per projection (default
                               max(4096, nx*ny/16)); a fuller list sets
                               EPR_ERR_SHIFT_OVERFLOW. */
@@ -79,9 +82,15 @@ typedef struct {
     int autotune;          /* 1 = after the first solve, time the splat's tile
                               shapes and reach on that solve's result and keep
                               the fastest for later solves (default 0).  The
-                              choice changes only the summation order of the
-                              float splat (fixed-point results are unchanged). */
-    int reserved[7];       /* must be zero */
+                              choice changes only the rounding of the float
+                              splat (fixed-point results are unchanged). */
+    int serial_launches;   /* 1 = launch every kernel only after its predecessor
+                              has finished.  0 (default) = the solver kernels use
+                              programmatic dependent launch: a kernel starts
+                              its independent loads while its predecessor
+                              drains, and waits on the device for the
+                              predecessor's results.  Results are identical. */
+    int reserved[6];       /* must be zero */
 } epr_options;
 
 /* Solver options. */

@@ -33,7 +33,9 @@ __global__ void __launch_bounds__(512, 2) k_col(const EprConsts C, const ColArgs
 {
     extern __shared__ __align__(16) float2 buf[];
     const int b = blockIdx.z, sl = blockIdx.y;
+    epr_grid_wait();
     if (A.check_done && A.st[b].done) return;
+    epr_grid_release();
     const int s = A.line0 + sl;
     const int ny = C.ny, half = C.half, CW = A.CW, lgCW = A.lgCW;
     const int T = blockDim.x, tid = threadIdx.x;
@@ -91,6 +93,7 @@ k_col_ct(const EprConsts C, const ColArgs A)
     constexpr int LGCW = CW == 1 ? 0 : CW == 2 ? 1 : CW == 4 ? 2 : CW == 8 ? 3 : 4;
     extern __shared__ __align__(16) float2 buf[];
     const int b = blockIdx.z, sl = blockIdx.y;
+    epr_grid_wait();
     if (A.check_done && A.st[b].done) return;
     const int s = A.line0 + sl;
     const int half = C.half, tid = threadIdx.x;
@@ -132,6 +135,7 @@ k_col_ct(const EprConsts C, const ColArgs A)
     for (int k = 0; k < EPT; ++k) buf[PC::idx(tid + k * T)] = nv[k];
     __syncthreads();
     eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
+    epr_grid_release();
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
         const int e = tid + k * T;
@@ -178,11 +182,14 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     A.line0 = line0;
     A.nl = nl;
     A.check_done = check_done;
-    dim3 grid(C.half / L.CW, nl, batch);
+    const dim3 grid(C.half / L.CW, nl, batch);
+    const bool pdl = C.pdl != 0;
+    cudaError_t e = cudaSuccess;
     bool done = false;
 #define EPR_COL_CASE(NYV, CWV, EPTV)                                                           \
     if (!done && C.ny == NYV && L.CW == CWV && L.EPT == EPTV) {                               \
-        k_col_ct<NYV, CWV, EPTV><<<grid, NYV * CWV / EPTV, L.smem, stream>>>(C, A);           \
+        e = epr_launch_kernel(pdl, k_col_ct<NYV, CWV, EPTV>, grid, dim3(NYV * CWV / EPTV),    \
+                              L.smem, stream, C, A);                                          \
         done = true;                                                                          \
     }
     EPR_COL_CASE(256, 4, 8)
@@ -192,11 +199,13 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     EPR_COL_CASE(4096, 1, 8)
 #undef EPR_COL_CASE
     if (!done) {
-        if (L.EPT == 8) k_col<8><<<grid, L.threads, L.smem, stream>>>(C, A);
-        else k_col<16><<<grid, L.threads, L.smem, stream>>>(C, A);
+        if (L.EPT == 8)
+            e = epr_launch_kernel(pdl, k_col<8>, grid, dim3(L.threads), L.smem, stream, C, A);
+        else
+            e = epr_launch_kernel(pdl, k_col<16>, grid, dim3(L.threads), L.smem, stream, C, A);
     }
     epr_count_launch(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t epr_col_init()

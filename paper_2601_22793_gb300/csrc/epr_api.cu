@@ -606,11 +606,11 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     if (n_lines < 1 || n_lines > EPR_MAX_LINES || !(pixel_m > 0.0) || !(L_m >= 0.0))
         return EPR_ERR_INVALID_ARG;
     if (!size_ok(nx) || !size_ok(ny)) return EPR_ERR_UNSUPPORTED_SIZE;
-    epr_options o = {4, 0, 0, 1, 0, {0}};
+    epr_options o = {4, 0, 0, 1, 0, 0, {0}};
     if (opt) o = *opt;
     if (o.max_shift_px < 1 || o.max_shift_px > EPR_MAX_SHIFT || o.overflow_capacity < 0)
         return EPR_ERR_INVALID_ARG;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (o.reserved[i] != 0) return EPR_ERR_INVALID_ARG;
     double wsum = 0.0;
     for (int s = 0; s < n_lines; ++s) {
@@ -638,6 +638,7 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     C.half = nx / 2;
     C.smax = o.max_shift_px;
     C.det = o.deterministic ? 1 : 0;
+    C.pdl = o.serial_launches ? 0 : 1;
     const size_t npix = (size_t)nx * ny;
     C.ovf_cap = o.overflow_capacity > 0 ? o.overflow_capacity
                                         : (int)(npix / 16 > 4096 ? npix / 16 : 4096);
@@ -663,6 +664,7 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
         C.hb[s] = mu[s] > 0.0 ? (float)(Ld * 4.0 * kPi * kPi * fy1 * fy1 / mu[s]) : 0.f;
         const double eps = L_m / k;
         C.qc[s] = (float)(eps * eps / (4.0 * pixel_m * pixel_m * pixel_m * pixel_m));
+        C.tneg[s] = mu[s] > 0.0 ? (float)(-0.6931471805599453 / mu[s]) : -3.0e38f;
     }
     if (!(den > 0.0)) {
         delete p;
@@ -1047,7 +1049,7 @@ epr_status epr_batch_create(epr_batch_t* out, double pixel_m, double L_m, int n_
         bp->beta[s] = beta[s];
         bp->w[s] = weights[s];
     }
-    epr_options o = {4, 0, 0, 1, 0, {0}};
+    epr_options o = {4, 0, 0, 1, 0, 0, {0}};
     if (opt) o = *opt;
     bp->opt = o;
     if (cudaGetDevice(&bp->device) != cudaSuccess ||

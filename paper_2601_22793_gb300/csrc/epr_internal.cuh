@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "epr.h"
 
 #define EPR_MAX_LINES 16
@@ -24,6 +26,8 @@ struct EprConsts {
     int half;            // nx / 2 (complex columns of the packed half spectrum)
     int smax;            // fast-path splat reach in pixels
     int det;             // 1 = int64 fixed-point splat accumulation
+    int pdl;             // host side: launch the solver kernels with
+                         // programmatic dependent launch
     int ovf_cap;         // overflow list entries per projection
     float inv_n;         // 1 / (nx * ny), folded into the filter
     float f[EPR_MAX_LINES];     // spectral weights, sum 1
@@ -33,6 +37,7 @@ struct EprConsts {
     float ha[EPR_MAX_LINES];    // Paganin: L delta 4 pi^2 / (mu (nx p)^2)
     float hb[EPR_MAX_LINES];    // Paganin: L delta 4 pi^2 / (mu (ny p)^2)
     float qc[EPR_MAX_LINES];    // local closure: eps^2 / (4 p^4), eps = L / k
+    float tneg[EPR_MAX_LINES];  // -ln 2 / mu: below it f exp(-mu T) > 2 f (splat bound)
 };
 
 // Per-projection solver state in device memory.
@@ -70,6 +75,19 @@ struct EprWork {
 };
 
 // --- small helpers ---------------------------------------------------------
+
+// a[s] for a per-line constant array held in kernel parameters.  A runtime
+// index into a by-value parameter array makes the compiler copy the array to
+// local memory; selecting through compile-time indices keeps every operand a
+// constant-bank read.
+__device__ __forceinline__ float line_const(const float (&a)[EPR_MAX_LINES], int s)
+{
+    float v = a[0];
+#pragma unroll
+    for (int i = 1; i < EPR_MAX_LINES; ++i)
+        if (s == i) v = a[i];
+    return v;
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -149,6 +167,47 @@ __device__ __forceinline__ bool last_block_reduce(unsigned int* cnt, unsigned in
     B_out = block_sum_d(sb, s_red);
     if (threadIdx.x == 0) *cnt = 0u;
     return true;
+}
+
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may start while its predecessor in the
+// stream is still running.  Every kernel of the solver loop therefore
+// (1) loads, before epr_grid_wait(), only data that neither its predecessor
+//     nor anything later writes (D, and T in the passes after the splat),
+// (2) calls epr_grid_wait(), which returns once the predecessor grid has
+//     completed and its writes are visible, and only then
+// (3) calls epr_grid_release(), which lets its own successor launch.
+// Because of (3) at most two consecutive kernels of the loop are resident at
+// once, so (1) only has to hold against the immediate predecessor.  Without
+// the attribute both instructions return at once.
+__device__ __forceinline__ void epr_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void epr_grid_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// 16-byte asynchronous global -> shared copies (completion per thread).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Kernel launch with the programmatic attribute when `pdl` is set.
+template <typename... KArgs, typename... Args>
+inline cudaError_t epr_launch_kernel(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                                     size_t smem, cudaStream_t stream, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Launch-accounting hook (defined in epr_api.cu).

@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, cons
     float* CYQ = CXQ + kLN;
 
     const int nx = C.nx, ny = C.ny, ns = C.ns, b = blockIdx.z;
+    epr_grid_wait();
     if (A.check_done && A.st[b].done) return;
+    epr_grid_release();
     const int ty0 = blockIdx.y * kLT, tx0 = blockIdx.x * kLT;
     const int gy0 = ty0 - kLH, gx0 = tx0 - kLH;
     const size_t npix = (size_t)nx * ny;
@@ -180,9 +182,10 @@ cudaError_t epr_launch_local(const EprConsts& C, const EprWork& W, const float* 
     A.order = order;
     A.check_done = check_done;
     dim3 grid((C.nx + kLT - 1) / kLT, (C.ny + kLT - 1) / kLT, batch);
-    k_local<<<grid, kLocalThreads, epr_local_smem(), stream>>>(C, A);
+    const cudaError_t e = epr_launch_kernel(C.pdl != 0, k_local, grid, dim3(kLocalThreads),
+                                            epr_local_smem(), stream, C, A);
     epr_count_launch(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t epr_local_init() { return epr_allow_max_smem(k_local); }

@@ -83,7 +83,7 @@ __device__ __forceinline__ float resid(const EprConsts& C, const RowArgs& A, siz
         const size_t npix = (size_t)C.nx * C.ny;
         const size_t ps = pb * C.ns + (size_t)s * npix + q;
         const float pl = ldP<DET>(A.Ps, A.Psq, ps);
-        return (p > 1e-30f) ? r * (pl / p) : r * C.f[s];
+        return (p > 1e-30f) ? r * (pl / p) : r * line_const(C.f, s);
     }
 }
 
@@ -123,7 +123,6 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
     const int b = blockIdx.y;
-    if (A.check_done && A.st[b].done) return;
     const int nx = C.nx, ny = C.ny, half = C.half;
     const int T = blockDim.x, tid = threadIdx.x;
     const int RP = A.RP, sm = nx + kPad;
@@ -135,16 +134,26 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
     float* Ts = reinterpret_cast<float*>(zs + ((PR::len(RP * sm) + 1) & ~1));
     const int nrows = 2 * RP + 2;
 
-    if constexpr (MODE == FWD_SOLVE_NL) {
+    if constexpr (MODE == FWD_SOLVE_NL) {   // T is not written by the predecessor
         const float* Tb = A.T + pb;
         const int q4 = nx >> 2;
         const float inv_q4 = 1.f / (float)q4;
         for (int i = tid; i < nrows * q4; i += T) {
             const int r = fdiv(i, inv_q4), c4 = i - r * q4;
             const int gy = min(max(yb - 1 + r, 0), ny - 1);
-            reinterpret_cast<float4*>(Ts)[i] =
-                __ldg(reinterpret_cast<const float4*>(Tb + (size_t)gy * nx) + c4);
+            cp_async16(reinterpret_cast<float4*>(Ts) + i,
+                       reinterpret_cast<const float4*>(Tb + (size_t)gy * nx) + c4);
         }
+        cp_async_commit();
+    }
+    epr_grid_wait();
+    if (A.check_done && A.st[b].done) {
+        cp_async_wait_all();   // no copy may land after the block has left
+        return;
+    }
+    epr_grid_release();
+    if constexpr (MODE == FWD_SOLVE_NL) {
+        cp_async_wait_all();
         __syncthreads();
     }
 
@@ -173,7 +182,7 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
                     if (y == 0) gy = tr[nx + x] - t;
                     else if (y == ny - 1) gy = t - tr[x - nx];
                     else gy = 0.5f * (tr[nx + x] - tr[x - nx]);
-                    const float cs = C.c[s];
+                    const float cs = line_const(C.c, s);
                     v[r0] = gather_px<DET, RESID>(C, A, pb, y, x, cs * gy, cs * gx, s);
                 } else if constexpr (MODE == FWD_SOLVE_LOCAL) {
                     v[r0] = resid<DET, false>(C, A, pb, (size_t)y * nx + x, s);
@@ -255,7 +264,9 @@ __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const Row
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
     const int b = blockIdx.y;
+    epr_grid_wait();
     if (A.check_done && A.st[b].done) return;
+    epr_grid_release();
     const int nx = C.nx, ny = C.ny, half = C.half;
     const int T = blockDim.x, tid = threadIdx.x;
     const int RP = A.RP, sm = nx + kPad;
@@ -296,7 +307,8 @@ __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const Row
             const float2 h = zs[PR::idx(m * sm + x)];
             const size_t q0 = pb + (size_t)(yb + 2 * m) * nx + x;
             if constexpr (MODE == INV_UPDATE) {
-                const float fs = C.f[s], mus = C.mu[s], w = C.wproj[s];
+                const float fs = line_const(C.f, s), mus = line_const(C.mu, s),
+                            w = line_const(C.wproj, s);
                 const float t0 = A.Out[q0], t1 = A.Out[q0 + nx];
                 const float l0 = w * log_ratio(t0, h.x, fs, mus, A.omega, A.eps);
                 const float l1 = w * log_ratio(t1, h.y, fs, mus, A.omega, A.eps);
@@ -402,13 +414,12 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
     const int b = blockIdx.y;
-    if (A.check_done && A.st[b].done) return;
     const int ny = C.ny, tid = threadIdx.x;
     const size_t npix = (size_t)NX * ny;
     const size_t pb = (size_t)b * npix;
     const int yb = blockIdx.x * RP * 2;
     float* Ts = reinterpret_cast<float*>(zs + ((PR::len(RP * SM) + 1) & ~1));
-    {
+    {   // T is not written by the predecessor: fetch it before the wait
         const float* Tb = A.T + pb;
         constexpr int Q4 = NX / 4;
         constexpr int NROWS = 2 * RP + 2;
@@ -418,11 +429,18 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
             if (NROWS * Q4 % T == 0 || i < NROWS * Q4) {
                 const int r = i / Q4, c4 = i % Q4;
                 const int gy = min(max(yb - 1 + r, 0), ny - 1);
-                reinterpret_cast<float4*>(Ts)[i] =
-                    __ldg(reinterpret_cast<const float4*>(Tb + (size_t)gy * NX) + c4);
+                cp_async16(reinterpret_cast<float4*>(Ts) + i,
+                           reinterpret_cast<const float4*>(Tb + (size_t)gy * NX) + c4);
             }
         }
+        cp_async_commit();
     }
+    epr_grid_wait();
+    if (A.check_done && A.st[b].done) {
+        cp_async_wait_all();   // no copy may land after the block has left
+        return;
+    }
+    cp_async_wait_all();
     __syncthreads();
     const float cs = C.c[0];
     const float* Rb = A.P + pb;   // residual D - P
@@ -473,6 +491,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     }
     __syncthreads();
     eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
+    epr_grid_release();
     float2* Sb = A.S + (size_t)b * (size_t)ny * HALF;
 #pragma unroll 2
     for (int i0 = 0; i0 < RP * HALF; i0 += T) {
@@ -520,10 +539,26 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
     const int b = blockIdx.y;
-    if (A.check_done && A.st[b].done) return;
     const int ny = C.ny, tid = threadIdx.x;
     const size_t pb = (size_t)b * NX * ny;
     const int yb = blockIdx.x * RP * 2;
+    // rows yb .. yb + 2RP - 1 of T, copied while the spectrum is transformed
+    float* Tsh = reinterpret_cast<float*>(zs + ((PR::len(RP * SM) + 1) & ~1));
+    {
+        constexpr int Q4 = 2 * RP * NX / 4;
+        const float4* src = reinterpret_cast<const float4*>(A.Out + pb + (size_t)yb * NX);
+#pragma unroll
+        for (int i0 = 0; i0 < Q4; i0 += T) {
+            const int i = i0 + tid;
+            if (Q4 % T == 0 || i < Q4) cp_async16(reinterpret_cast<float4*>(Tsh) + i, src + i);
+        }
+        cp_async_commit();
+    }
+    epr_grid_wait();
+    if (A.check_done && A.st[b].done) {
+        cp_async_wait_all();
+        return;
+    }
     const float2* Sb = A.S + (size_t)b * (size_t)ny * HALF;
 #pragma unroll 2
     for (int i0 = 0; i0 < RP * HALF; i0 += T) {
@@ -543,6 +578,9 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
     }
     __syncthreads();
     eprfft::fft_ct<PR, +1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
+    epr_grid_release();
+    cp_async_wait_all();
+    __syncthreads();
     const float fs = C.f[0], mus = C.mu[0], w = C.wproj[0];
     float da = 0.f, db = 0.f;
 #pragma unroll 2
@@ -551,7 +589,7 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
         const int m = e >> LGNX, x = e & (NX - 1);
         const float2 h = zs[PR::idx(m * SM + x)];
         const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
-        const float t0 = A.Out[q0], t1 = A.Out[q0 + NX];
+        const float t0 = Tsh[(2 * m) * NX + x], t1 = Tsh[(2 * m + 1) * NX + x];
         const float l0 = w * log_ratio(t0, h.x, fs, mus, A.omega, A.eps);
         const float l1 = w * log_ratio(t1, h.y, fs, mus, A.omega, A.eps);
         const float n0 = t0 - l0, n1 = t1 - l1;
@@ -577,12 +615,15 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
 // launch a specialised mono kernel when nx has one; returns false otherwise
 template <bool FWD>
 bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream, const EprConsts& C,
-                    const RowArgs& A)
+                    const RowArgs& A, cudaError_t& err)
 {
 #define EPR_MONO_CASE(NXV, RPV)                                                              \
     if (nx == NXV && rp == RPV) {                                                            \
-        if (FWD) k_row_fwd_mono<NXV, RPV><<<grid, NXV * RPV / kEPT, smem, stream>>>(C, A);   \
-        else k_row_inv_mono<NXV, RPV><<<grid, NXV * RPV / kEPT, smem, stream>>>(C, A);       \
+        const dim3 blk(NXV * RPV / kEPT);                                                    \
+        if (FWD) err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV>, grid, blk,     \
+                                         smem, stream, C, A);                                \
+        else err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<NXV, RPV>, grid, blk, smem,   \
+                                     stream, C, A);                                          \
         return true;                                                                         \
     }
     EPR_MONO_CASE(256, 8)
@@ -649,30 +690,31 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, i
     A.hist = W.rho_hist; A.hist_len = W.hist_len; A.max_blocks = W.max_blocks;
     A.tw = W.tw_x; A.RP = L.RP; A.lgRP = L.lgRP; A.line0 = line0; A.nl = nl; A.it = it;
     A.check_done = check_done;
-    dim3 grid(C.ny / (2 * L.RP), batch);
-    const bool mono = nl == 1;
+    const dim3 grid(C.ny / (2 * L.RP), batch), blk(L.threads);
+    const bool mono = nl == 1, pdl = C.pdl != 0;
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kernel) { e = epr_launch_kernel(pdl, kernel, grid, blk, L.smem, stream, C, A); };
     if (mode == FWD_SOLVE_NL) {
         if (C.det) {
-            if (mono) k_row_fwd<FWD_SOLVE_NL, true, false, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
-            else k_row_fwd<FWD_SOLVE_NL, true, false, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
+            if (mono) go(k_row_fwd<FWD_SOLVE_NL, true, false, 1>);
+            else go(k_row_fwd<FWD_SOLVE_NL, true, false, 0>);
         } else if (resid && mono) {
-            if (!launch_mono_ct<true>(C.nx, L.RP, grid, L.smem, stream, C, A))
-                k_row_fwd<FWD_SOLVE_NL, false, true, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+            if (!launch_mono_ct<true>(C.nx, L.RP, grid, L.smem, stream, C, A, e))
+                go(k_row_fwd<FWD_SOLVE_NL, false, true, 1>);
         } else {
-            if (mono) k_row_fwd<FWD_SOLVE_NL, false, false, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
-            else k_row_fwd<FWD_SOLVE_NL, false, false, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
+            if (mono) go(k_row_fwd<FWD_SOLVE_NL, false, false, 1>);
+            else go(k_row_fwd<FWD_SOLVE_NL, false, false, 0>);
         }
     } else if (mode == FWD_SOLVE_LOCAL) {
         // the local closure writes float maps in both accumulation modes
-        k_row_fwd<FWD_SOLVE_LOCAL, false, false, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
+        go(k_row_fwd<FWD_SOLVE_LOCAL, false, false, 0>);
     } else {
-        k_row_fwd<FWD_LOAD, false, false, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+        go(k_row_fwd<FWD_LOAD, false, false, 1>);
     }
     epr_count_launch(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// mode: 0 = update T in place (Out = T), 1 = store the filtered real map to Out
 cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, float* Out,
                                int line0, int nl, int it, float omega, float eps, float tol,
                                int batch, int check_done, cudaStream_t stream)
@@ -683,16 +725,19 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
     A.hist = W.kappa_hist; A.hist_len = W.hist_len; A.max_blocks = W.max_blocks;
     A.tw = W.tw_x; A.RP = L.RP; A.lgRP = L.lgRP; A.line0 = line0; A.nl = nl; A.it = it;
     A.omega = omega; A.eps = eps; A.tol = tol; A.check_done = check_done;
-    dim3 grid(C.ny / (2 * L.RP), batch);
+    const dim3 grid(C.ny / (2 * L.RP), batch), blk(L.threads);
+    const bool pdl = C.pdl != 0;
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kernel) { e = epr_launch_kernel(pdl, kernel, grid, blk, L.smem, stream, C, A); };
     if (mode == INV_UPDATE) {
-        if (nl == 1 && !C.det && launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A)) {
-        } else if (nl == 1) k_row_inv<INV_UPDATE, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
-        else k_row_inv<INV_UPDATE, 0><<<grid, L.threads, L.smem, stream>>>(C, A);
+        if (nl == 1 && !C.det && launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A, e)) {
+        } else if (nl == 1) go(k_row_inv<INV_UPDATE, 1>);
+        else go(k_row_inv<INV_UPDATE, 0>);
     } else {
-        k_row_inv<INV_STORE, 1><<<grid, L.threads, L.smem, stream>>>(C, A);
+        go(k_row_inv<INV_STORE, 1>);
     }
     epr_count_launch(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // |D|^2 of each projection into the solver state (two small launches).

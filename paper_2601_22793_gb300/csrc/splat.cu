@@ -17,12 +17,23 @@
 //    f_s exp(-mu_s T) times the four bilinear weights to the corners inside
 //    the tile with shared-memory atomics.  exp is evaluated only when the
 //    source reaches the tile.
+//  * The shared accumulators are integers, because integer shared-memory
+//    atomics are single instructions while float ones are not.  The float
+//    mode adds round(v * 2^S) in uint32 with S chosen from the reach so that
+//    no pixel can overflow: at most (2 reach + 3)^2 sources reach a pixel,
+//    each with a contribution <= f_s <= 1, so 2^(32-S) >= (2 reach + 3)^2.
+//    With a factor 2 of headroom, 2^(32-S) >= 2 (2 reach + 3)^2 holds for
+//    contributions up to 2 f_s, and a source whose intensity exceeds that
+//    (T < -ln 2 / mu_s, a negative thickness far outside any physical
+//    iterate) takes the overflow path with the long shifts.  For reach 4,
+//    S = 24: a rounding error of at most 3e-8 per contribution, half an fp32
+//    ulp of a unit intensity.
 //  * Every destination pixel is written exactly once, with plain coalesced
 //    stores: no zero fill and no global atomics on the fast path.  In the
 //    monochromatic float solve the flush stores the residual D - P instead
 //    of P (the adjoint gather then reads one value per corner).
-//  * A source-line with |u| > reach in either axis is never splatted by the
-//    scan; the block that owns the source pixel appends it (with a bit mask
+//  * A source-line with |u| > reach in either axis (or T below the bound
+//    above) is never splatted by the scan; the block that owns the source pixel appends it (with a bit mask
 //    of its long lines) to a per-projection overflow list, and a second
 //    kernel adds those contributions with global atomics.  No mass is lost,
 //    whatever the shift.  The list fill counter alternates between two slots
@@ -49,6 +60,7 @@ struct SplatArgs {
     unsigned int* err;
     int TH, TW, lgTW, parity;
     int check_done;
+    float fxs, fxs_inv;      // float mode: scale 2^S of the uint32 accumulators
 };
 
 // numpy.gradient semantics along one axis from three neighbours.
@@ -63,13 +75,13 @@ __device__ __forceinline__ float grad1(float lo, float mid, float hi, int i, int
 __device__ __forceinline__ int fdiv(int i, float inv_d) { return (int)(((float)i + 0.5f) * inv_d); }
 
 template <bool DET>
-__device__ __forceinline__ void acc_add(void* acc, int idx, float v)
+__device__ __forceinline__ void acc_add(void* acc, int idx, float v, float fxs)
 {
     if constexpr (DET) {
         unsigned long long q = (unsigned long long)__float2ll_rn(v * EPR_FX_SCALE);
         atomicAdd(reinterpret_cast<unsigned long long*>(acc) + idx, q);
     } else {
-        atomicAdd(reinterpret_cast<float*>(acc) + idx, v);
+        atomicAdd(reinterpret_cast<unsigned int*>(acc) + idx, __float2uint_rn(v * fxs));
     }
 }
 
@@ -88,7 +100,6 @@ k_splat(const EprConsts C, const SplatArgs A)
     __shared__ unsigned int s_far_mask[kFarList];
     __shared__ int s_far_n, s_far_base;
     const int b = blockIdx.z;
-    if (A.check_done && A.st[b].done) return;
     const int nx = C.nx, ny = C.ny;
     const int ns = NS ? NS : C.ns;
     const int TH = A.TH, TW = A.TW;
@@ -127,6 +138,17 @@ k_splat(const EprConsts C, const SplatArgs A)
         }
     }
 
+    if constexpr (DET) {
+        unsigned long long* a = reinterpret_cast<unsigned long long*>(acc);
+        for (int i = tid; i < ns * tile; i += kSplatThreads) a[i] = 0ull;
+    } else {
+        float4* a = reinterpret_cast<float4*>(acc);
+        for (int i = tid; i < ns * tile / 4; i += kSplatThreads) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // T, the done flags and the overflow counters come from earlier kernels
+    epr_grid_wait();
+    if (A.check_done && A.st[b].done) return;
+
     const int sy0 = ty0 - R - 1, sx0 = tx0 - R - 1, ax0 = tx0 - HX;
     const bool interior = sy0 >= 0 && sx0 >= 0 && sy0 + SH <= ny && sx0 + RW + 2 <= nx;
     {
@@ -141,16 +163,10 @@ k_splat(const EprConsts C, const SplatArgs A)
             reinterpret_cast<float4*>(Ts)[i] = v;
         }
     }
-    if constexpr (DET) {
-        unsigned long long* a = reinterpret_cast<unsigned long long*>(acc);
-        for (int i = tid; i < ns * tile; i += kSplatThreads) a[i] = 0ull;
-    } else {
-        float4* a = reinterpret_cast<float4*>(acc);
-        for (int i = tid; i < ns * tile / 4; i += kSplatThreads) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     __syncthreads();
 
     const float fsmax = (float)C.smax;
+    const float fxs = A.fxs;
     const int nsrc = RH * RW;
     const float inv_RW = 1.f / (float)RW;
     for (int i = tid; i < nsrc; i += kSplatThreads) {
@@ -172,7 +188,7 @@ k_splat(const EprConsts C, const SplatArgs A)
         for (int s = 0; s < ns; ++s) {
             const float cs = C.c[s];
             const float ux = cs * gx, uy = cs * gy;
-            if (!(fabsf(ux) <= fsmax && fabsf(uy) <= fsmax)) {
+            if (!(fabsf(ux) <= fsmax && fabsf(uy) <= fsmax && t >= C.tneg[s])) {
                 far |= 1u << s;
                 continue;
             }
@@ -185,12 +201,12 @@ k_splat(const EprConsts C, const SplatArgs A)
             const int idx = s * tile + cy * TW + cx;
             if (cy >= 0) {
                 const float w = 1.f - dy;
-                if (cx >= 0) acc_add<DET>(acc, idx, mx0 * w);
-                if (cx + 1 < TW) acc_add<DET>(acc, idx + 1, mx1 * w);
+                if (cx >= 0) acc_add<DET>(acc, idx, mx0 * w, fxs);
+                if (cx + 1 < TW) acc_add<DET>(acc, idx + 1, mx1 * w, fxs);
             }
             if (cy + 1 < TH) {
-                if (cx >= 0) acc_add<DET>(acc, idx + TW, mx0 * dy);
-                if (cx + 1 < TW) acc_add<DET>(acc, idx + TW + 1, mx1 * dy);
+                if (cx >= 0) acc_add<DET>(acc, idx + TW, mx0 * dy, fxs);
+                if (cx + 1 < TW) acc_add<DET>(acc, idx + TW + 1, mx1 * dy, fxs);
             }
         }
         if (far && (unsigned)(ly - R) < (unsigned)TH && (unsigned)(lx - R) < (unsigned)TW) {
@@ -210,6 +226,7 @@ k_splat(const EprConsts C, const SplatArgs A)
         }
     }
     __syncthreads();
+    epr_grid_release();
 
     // far sources of this block: one reservation in the global list
     const int nfar = s_far_n < kFarList ? s_far_n : kFarList;
@@ -229,7 +246,8 @@ k_splat(const EprConsts C, const SplatArgs A)
 
     // flush: every pixel of the tile inside the grid, once, coalesced
     if constexpr (RESID) {
-        const float4* a4 = reinterpret_cast<const float4*>(acc);
+        const uint4* a4 = reinterpret_cast<const uint4*>(acc);
+        const float inv = A.fxs_inv;
 #pragma unroll
         for (int k = 0; k < kDq; ++k) {
             const int i4 = tid + k * kSplatThreads;
@@ -237,9 +255,11 @@ k_splat(const EprConsts C, const SplatArgs A)
             const int ly = i4 / tw4, lx = (i4 - ly * tw4) << 2;
             const int gy = ty0 + ly, gx = tx0 + lx;
             if (gy >= ny || gx >= nx) continue;
-            const float4 v = a4[i4], d = dreg[k];
+            const uint4 v = a4[i4];
+            const float4 d = dreg[k];
             *reinterpret_cast<float4*>(A.P + (size_t)b * npix + (size_t)gy * nx + gx) =
-                make_float4(d.x - v.x, d.y - v.y, d.z - v.z, d.w - v.w);
+                make_float4(d.x - (float)v.x * inv, d.y - (float)v.y * inv,
+                            d.z - (float)v.z * inv, d.w - (float)v.w * inv);
         }
     } else {
         for (int i = tid; i < tile; i += kSplatThreads) {
@@ -257,14 +277,16 @@ k_splat(const EprConsts C, const SplatArgs A)
                 }
                 A.Pq[o] = sum;
             } else {
-                const float* a = reinterpret_cast<const float*>(acc);
-                float sum = 0.f;
+                // sum <= 2 (2 reach + 3)^2 sum_s f_s: no overflow either
+                const unsigned int* a = reinterpret_cast<const unsigned int*>(acc);
+                unsigned int sum = 0u;
                 for (int s = 0; s < ns; ++s) {
-                    const float q = a[s * tile + i];
+                    const unsigned int q = a[s * tile + i];
                     sum += q;
-                    if (ns > 1) A.Ps[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = q;
+                    if (ns > 1)
+                        A.Ps[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = (float)q * A.fxs_inv;
                 }
-                A.P[o] = sum;
+                A.P[o] = (float)sum * A.fxs_inv;
             }
         }
     }
@@ -275,7 +297,9 @@ template <bool DET, bool RESID>
 __global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const SplatArgs A)
 {
     const int b = blockIdx.y;
+    epr_grid_wait();
     if (A.check_done && A.st[b].done) return;
+    epr_grid_release();
     const int nx = C.nx, ny = C.ny, ns = C.ns;
     const size_t npix = (size_t)nx * ny;
     const int cnt_raw = A.st[b].ovf_count[A.parity];
@@ -323,11 +347,15 @@ __global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const
 }
 
 template <int NS, bool DET, bool RESID>
-void launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
-              cudaStream_t stream)
+cudaError_t launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
+                     cudaStream_t stream)
 {
-    k_splat<NS, DET, RESID><<<grid, kSplatThreads, smem, stream>>>(C, A);
-    k_splat_overflow<DET, RESID><<<dim3(128, batch), 128, 0, stream>>>(C, A);
+    const bool pdl = C.pdl != 0;
+    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID>, grid,
+                                            dim3(kSplatThreads), smem, stream, C, A);
+    if (e != cudaSuccess) return e;
+    return epr_launch_kernel(pdl, k_splat_overflow<DET, RESID>, dim3(128, batch), dim3(128), 0,
+                             stream, C, A);
 }
 
 }  // namespace
@@ -364,20 +392,28 @@ cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* 
     while ((1 << A.lgTW) < TW) ++A.lgTW;
     A.parity = parity & 1;
     A.check_done = check_done;
+    {   // 2^(32 - S) >= 2 (2 reach + 3)^2: the largest pixel sum fits in uint32
+        const int win = 2 * (2 * C.smax + 3) * (2 * C.smax + 3);
+        int bits = 0;
+        while ((1 << bits) < win) ++bits;
+        A.fxs = ldexpf(1.f, 32 - bits);
+        A.fxs_inv = ldexpf(1.f, bits - 32);
+    }
     const size_t smem = epr_splat_smem(C, TH, TW);
     dim3 grid((C.nx + TW - 1) / TW, (C.ny + TH - 1) / TH, batch);
     const bool mono = C.ns == 1;
+    cudaError_t e;
     if (C.det) {
-        if (mono) launch_t<1, true, false>(C, A, grid, smem, batch, stream);
-        else launch_t<0, true, false>(C, A, grid, smem, batch, stream);
+        if (mono) e = launch_t<1, true, false>(C, A, grid, smem, batch, stream);
+        else e = launch_t<0, true, false>(C, A, grid, smem, batch, stream);
     } else if (resid && mono) {
-        launch_t<1, false, true>(C, A, grid, smem, batch, stream);
+        e = launch_t<1, false, true>(C, A, grid, smem, batch, stream);
     } else {
-        if (mono) launch_t<1, false, false>(C, A, grid, smem, batch, stream);
-        else launch_t<0, false, false>(C, A, grid, smem, batch, stream);
+        if (mono) e = launch_t<1, false, false>(C, A, grid, smem, batch, stream);
+        else e = launch_t<0, false, false>(C, A, grid, smem, batch, stream);
     }
     epr_count_launch(2);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t epr_splat_init()

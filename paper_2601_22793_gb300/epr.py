@@ -47,7 +47,8 @@ KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 class epr_options(ctypes.Structure):
     _fields_ = [("max_shift_px", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("overflow_capacity", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("autotune", ctypes.c_int), ("serial_launches", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class epr_batch_desc(ctypes.Structure):
@@ -178,21 +179,24 @@ def _darr(x):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune):
+def _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune,
+             serial_launches=False):
     return epr_options(int(max_shift_px), int(bool(deterministic)), int(overflow_capacity),
-                       int(bool(use_graphs)), int(bool(autotune)), (ctypes.c_int * 7)())
+                       int(bool(use_graphs)), int(bool(autotune)), int(bool(serial_launches)),
+                       (ctypes.c_int * 6)())
 
 
 def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
                     max_shift_px=4, deterministic=False, overflow_capacity=0, use_graphs=True,
-                    autotune=False):
+                    autotune=False, serial_launches=False):
     """Returns an opaque plan handle (int)."""
     lib = load()
     E, Ep = _darr(energy_keV)
     dl, dp_ = _darr(delta)
     bt, bp = _darr(beta)
     w, wp = _darr(np.ones(E.size) if weights is None else weights)
-    opt = _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune)
+    opt = _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune,
+                   serial_launches)
     h = ctypes.c_void_p()
     _check(lib.epr_plan_create(ctypes.byref(h), int(nx), int(ny), float(pixel_m), float(L_m),
                                int(E.size), Ep, dp_, bp, wp, ctypes.byref(opt)), "epr_plan_create")
@@ -290,14 +294,16 @@ def epr_solve_local(plan, D, T, batch=1, order=2, n_iter=20, omega=1.0, tol=0.0,
 
 
 def epr_batch_create(pixel_m, L_m, energy_keV, delta, beta, weights=None, max_shift_px=4,
-                     deterministic=False, overflow_capacity=0, use_graphs=True, autotune=False):
+                     deterministic=False, overflow_capacity=0, use_graphs=True, autotune=False,
+                     serial_launches=False):
     """Returns an opaque batch handle (int) for epr_solve_nonlocal_batched."""
     lib = load()
     E, Ep = _darr(energy_keV)
     dl, dp_ = _darr(delta)
     bt, bp = _darr(beta)
     w, wp = _darr(np.ones(E.size) if weights is None else weights)
-    opt = _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune)
+    opt = _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune,
+                   serial_launches)
     h = ctypes.c_void_p()
     _check(lib.epr_batch_create(ctypes.byref(h), float(pixel_m), float(L_m), int(E.size), Ep, dp_,
                                 bp, wp, ctypes.byref(opt)), "epr_batch_create")

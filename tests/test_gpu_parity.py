@@ -109,6 +109,26 @@ def test_forward_overflow_path_keeps_all_mass(torch, E, oracle):
     assert rel(host(P), ref) < 1e-5
 
 
+def test_forward_negative_thickness_keeps_the_accumulators_in_range(torch, E, oracle):
+    """Where f_s exp(-mu_s T) exceeds 2 f_s (T < -ln 2 / mu_s) a source would
+    not fit the float mode's 32-bit tile accumulators; such sources take the
+    overflow path, so the prediction still equals the oracle's."""
+    wl, tau = ph.spheres_mono_256()
+    ln = lines_of(oracle, wl)
+    f, mu, *_ = ln.params()
+    yy, xx = np.mgrid[0:wl.ny, 0:wl.nx].astype(np.float64)
+    bump = 1.5 * np.log(2.0) / mu[0] * np.exp(-((yy - 90.0) ** 2 + (xx - 170.0) ** 2) / 20.0 ** 2)
+    T32 = (tau - bump).astype(np.float32)
+    assert (T32 < -np.log(2.0) / mu[0]).sum() > 300   # ~500 heavy sources
+    with plan_of(E, wl) as p:
+        T = cuda(torch, T32)
+        P = torch.empty_like(T)
+        E.epr_forward(p.handle, T, P)
+        E.epr_check_device_status(p.handle)
+    ref = oracle.forward(ln, T32.astype(np.float64))
+    assert rel(host(P), ref) < 1e-5
+
+
 def test_forward_fixed_point_is_bit_exact(torch, E, oracle):
     wl, T32 = small_poly(seed=7)
     outs = []
@@ -233,6 +253,45 @@ def test_solve_fixed_point_bit_exact_and_graph_replay(torch, E, oracle):
     assert all(np.array_equal(res[0], r) for r in res[1:])
     Tr, _ = oracle.solve(ln, D.astype(np.float64), n_iter=6, omega=0.4)
     assert rel(res[0], Tr) < 1e-4
+
+
+def test_programmatic_launch_matches_serial_launches(torch, E, oracle):
+    """Programmatic dependent launch changes only when kernels start.  In the
+    fixed-point mode every solve (graph replay or stream launches, with one
+    projection retiring after its first iteration) is bit-identical to the
+    serial launches; the monochromatic float solve agrees to float atomics
+    ordering."""
+    wl, T32 = small_poly(seed=11)
+    ln = lines_of(oracle, wl)
+    D = np.stack([
+        ph.poisson(oracle.forward(ln, T32.astype(np.float64)), wl.photons, 4),
+        ph.poisson(oracle.forward(ln, 0.3 * T32.astype(np.float64)), wl.photons, 5),
+        oracle.forward(ln, np.zeros_like(T32, dtype=np.float64)),   # retires at once
+    ]).astype(np.float32)
+    out = {}
+    for serial in (False, True):
+        for graphs in (False, True):
+            with plan_of(E, wl, deterministic=True, serial_launches=serial, use_graphs=graphs) as p:
+                Dd = cuda(torch, D)
+                T = torch.empty_like(Dd)
+                info = E.epr_solve_nonlocal(p.handle, Dd, T, batch=3, n_iter=8, omega=0.4,
+                                            tol=1e-3)
+                out[(serial, graphs)] = (T.cpu().numpy().copy(), tuple(info["iters"]))
+    ref = out[(True, False)]
+    assert ref[1][2] == 1 and ref[1][0] > 1
+    for key, (T_k, it_k) in out.items():
+        assert it_k == ref[1], key
+        assert np.array_equal(T_k, ref[0]), key
+
+    wl, ln, Dm = _spheres_data(oracle)
+    res = []
+    for serial in (False, True):
+        with plan_of(E, wl, serial_launches=serial) as p:
+            Dd = cuda(torch, Dm)
+            T = torch.empty_like(Dd)
+            E.epr_solve_nonlocal(p.handle, Dd, T, n_iter=wl.n_iter, omega=wl.omega)
+            res.append(host(T))
+    assert rel(res[0], res[1]) < 1e-5
 
 
 def test_solve_tolerance_stops_like_the_oracle(torch, E, oracle):
