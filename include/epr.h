@@ -48,7 +48,7 @@ typedef enum {
     EPR_ERR_OOM = 3,              /* device allocation failed           */
     EPR_ERR_CUDA = 4,             /* a CUDA runtime or launch error     */
     EPR_ERR_NONFINITE = 5,        /* NaN or Inf in an input map         */
-    EPR_ERR_TIMEOUT = 6,          /* reserved: a bounded device wait ran out */
+    EPR_ERR_TIMEOUT = 6,          /* a bounded device wait on a bulk copy ran out */
     EPR_ERR_NOT_CONVERGED = 7,    /* reserved                           */
     EPR_ERR_SHIFT_OVERFLOW = 8    /* more large-shift sources than the overflow list holds */
 } epr_status;

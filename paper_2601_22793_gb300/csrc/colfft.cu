@@ -12,8 +12,11 @@
 // transform the two are separated with C[ky] and conj C[-ky], filtered with
 // their own symbols and packed again:
 //   C'[ky] = (H0 + HN)/2 C[ky] + (H0 - HN)/2 conj C[-ky].
+#include <cudaTypedefs.h>
+
 #include "epr_internal.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -23,10 +26,46 @@ struct ColArgs {
     float2* S;            // [B][nl][ny][nx/2]
     const EprProjState* st;
     const float2* tw;     // exp(-2 pi i t / ny)
+    unsigned int* err;    // device error word
     int CW, lgCW;
     int line0, nl;
     int check_done;
 };
+
+// Filter value of frequency row y of the tile, in place in buf (two phases:
+// column 0 reads the mirrored frequency, so all reads precede all writes).
+template <int NY, int CW, int EPT, int T, int LGCW>
+__device__ __forceinline__ void col_filter(float2* buf, const EprConsts& C, int s, int kx0, int tid)
+{
+    const float ha = line_const(C.ha, s), hb = line_const(C.hb, s), inv_n = C.inv_n;
+    const int half = C.half;
+    float2 nv[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int e = tid + k * T;
+        const int y = e >> LGCW, c = e & (CW - 1);
+        const int kx = kx0 + c;
+        const float ky = (float)(y <= NY / 2 ? y : y - NY);
+        const float qy = hb * ky * ky;
+        const float2 v = buf[eprfft::PadCol::idx(e)];
+        if (kx != 0) {
+            const float H = inv_n / (1.f + ha * (float)kx * (float)kx + qy);
+            nv[k] = cscale(v, H);
+        } else {
+            const float kn = (float)half;
+            const float H0 = inv_n / (1.f + qy);
+            const float HN = inv_n / (1.f + ha * kn * kn + qy);
+            const int yneg = (NY - y) & (NY - 1);
+            const float2 w = cconj(buf[eprfft::PadCol::idx((yneg << LGCW) + c)]);
+            const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
+            nv[k] = make_float2(hp * v.x + hm * w.x, hp * v.y + hm * w.y);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) buf[eprfft::PadCol::idx(tid + k * T)] = nv[k];
+    __syncthreads();
+}
 
 template <int EPT>
 __global__ void __launch_bounds__(512, 2) k_col(const EprConsts C, const ColArgs A)
@@ -107,33 +146,7 @@ k_col_ct(const EprConsts C, const ColArgs A)
     }
     __syncthreads();
     eprfft::fft_ct<PC, -1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
-    const float ha = C.ha[s], hb = C.hb[s], inv_n = C.inv_n;
-    float2 nv[EPT];
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-        const int e = tid + k * T;
-        const int y = e >> LGCW, c = e & (CW - 1);
-        const int kx = kx0 + c;
-        const float ky = (float)(y <= NY / 2 ? y : y - NY);
-        const float qy = hb * ky * ky;
-        const float2 v = buf[PC::idx(e)];
-        if (kx != 0) {
-            const float H = inv_n / (1.f + ha * (float)kx * (float)kx + qy);
-            nv[k] = cscale(v, H);
-        } else {
-            const float kn = (float)half;
-            const float H0 = inv_n / (1.f + qy);
-            const float HN = inv_n / (1.f + ha * kn * kn + qy);
-            const int yneg = (NY - y) & (NY - 1);
-            const float2 w = cconj(buf[PC::idx((yneg << LGCW) + c)]);
-            const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
-            nv[k] = make_float2(hp * v.x + hm * w.x, hp * v.y + hm * w.y);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) buf[PC::idx(tid + k * T)] = nv[k];
-    __syncthreads();
+    col_filter<NY, CW, EPT, T, LGCW>(buf, C, s, kx0, tid);
     eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
     epr_grid_release();
 #pragma unroll
@@ -141,6 +154,73 @@ k_col_ct(const EprConsts C, const ColArgs A)
         const int e = tid + k * T;
         const int y = e >> LGCW, c = e & (CW - 1);
         Sb[(size_t)y * half + kx0 + c] = buf[PC::idx(e)];
+    }
+}
+
+// The same pass with the [NY][CW] tile moved by the tensor memory
+// accelerator: BOXES bulk loads of [NY / BOXES][CW] into a dense staging tile
+// (no L1 traffic, one elected thread), the first FFT stage reading from it,
+// and the result copied back to the staging tile and stored in bulk.  The
+// tile's row pitch is CW * 8 bytes, which keeps the strided 16-byte row
+// segments of the column off the load/store unit.
+constexpr unsigned int kTmaWaitPolls = 1u << 22;
+
+template <int NY, int CW, int EPT>
+__global__ void __launch_bounds__(NY * CW / EPT, (65536 / 64) / (NY * CW / EPT))
+k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMap map)
+{
+    constexpr int T = NY * CW / EPT;
+    constexpr int LGCW = CW == 2 ? 1 : CW == 4 ? 2 : 3;
+    constexpr int BOXY = NY < 256 ? NY : 256;
+    constexpr int BOXES = NY / BOXY;
+    constexpr unsigned int BYTES = NY * CW * sizeof(float2);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ alignas(8) uint64_t bar;
+    // 128-byte aligned staging tile, then the padded FFT buffer
+    const size_t base = ((size_t)__cvta_generic_to_shared(smem_raw) + 127) & ~size_t(127);
+    float2* stg = reinterpret_cast<float2*>(smem_raw + (base - (size_t)__cvta_generic_to_shared(smem_raw)));
+    float2* buf = stg + NY * CW;
+    const int b = blockIdx.z, sl = blockIdx.y, tid = threadIdx.x;
+    const int kx0 = blockIdx.x * CW;
+    if (tid == 0) {
+        epr_tma::mbar_init(&bar, 1);
+        epr_tma::fence_async_shared();
+    }
+    __syncthreads();
+    epr_grid_wait();
+    if (A.check_done && A.st[b].done) return;
+    const int row0 = (b * A.nl + sl) * NY;
+    if (tid == 0) {
+        epr_tma::fence_async_global();
+        epr_tma::mbar_arrive_expect_tx(&bar, BYTES);
+#pragma unroll
+        for (int i = 0; i < BOXES; ++i)
+            epr_tma::load_2d(stg + i * BOXY * CW, &map, 2 * kx0, row0 + i * BOXY, &bar);
+    }
+    if (!epr_tma::mbar_wait(&bar, 0, kTmaWaitPolls)) {
+        // the copy did not arrive: report, and wait once more (bounded) so
+        // that no copy lands after the block has left
+        if (tid == 0) atomicOr(A.err, EPR_DEVERR_TIMEOUT);
+        epr_tma::mbar_wait(&bar, 0, kTmaWaitPolls);
+        return;
+    }
+    eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1>(stg, buf, A.tw, tid);
+    col_filter<NY, CW, EPT, T, LGCW>(buf, C, A.line0 + sl, kx0, tid);
+    eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
+    epr_grid_release();
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int e = tid + k * T;
+        stg[e] = buf[PC::idx(e)];
+    }
+    epr_tma::fence_async_shared();
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < BOXES; ++i)
+            epr_tma::store_2d(&map, 2 * kx0, row0 + i * BOXY, stg + i * BOXY * CW);
+        epr_tma::bulk_commit();
+        epr_tma::bulk_wait_all();
     }
 }
 
@@ -169,6 +249,48 @@ EprColLaunch epr_col_config(const EprConsts& C, int cw_hint)
     return L;
 }
 
+// The column passes that move their tile by bulk tensor copies.
+static bool col_tma_case(const EprConsts& C, const EprColLaunch& L)
+{
+    if (L.EPT != 8) return false;
+    return (L.CW == 4 && (C.ny == 256 || C.ny == 512 || C.ny == 1024)) ||
+           (L.CW == 2 && C.ny == 2048);
+}
+
+static size_t col_tma_smem(const EprConsts& C, const EprColLaunch& L)
+{
+    return 128 + (size_t)C.ny * L.CW * sizeof(float2) + (size_t)PC::len(C.ny * L.CW) * sizeof(float2);
+}
+
+// Tensor map of S seen as `rows` rows of nx floats, with [ny or 256][2 CW]
+// boxes, for the bulk-copy column pass.  Returns false (and leaves the plain
+// pass in use) when the size has no such pass or the driver offers no
+// encoder.
+bool epr_col_make_map(const EprConsts& C, const float2* S, long long rows, CUtensorMap* out)
+{
+    const EprColLaunch L = epr_col_config(C, 0);
+    if (!col_tma_case(C, L) || !S || rows <= 0 || rows > (1ll << 31)) return false;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)C.nx, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)C.nx * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * L.CW), (cuuint32_t)(C.ny < 256 ? C.ny : 256)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(S), dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int nl, int batch,
                            int check_done, int cw_hint, cudaStream_t stream)
 {
@@ -177,6 +299,7 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     A.S = W.S;
     A.st = W.st;
     A.tw = W.tw_y;
+    A.err = W.err;
     A.CW = L.CW;
     A.lgCW = L.lgCW;
     A.line0 = line0;
@@ -186,6 +309,21 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     const bool pdl = C.pdl != 0;
     cudaError_t e = cudaSuccess;
     bool done = false;
+    if (W.col_map && cw_hint == 0 && col_tma_case(C, L)) {
+        const CUtensorMap& map = *static_cast<const CUtensorMap*>(W.col_map);
+        const size_t smem = col_tma_smem(C, L);
+#define EPR_COL_TMA_CASE(NYV, CWV)                                                             \
+        if (!done && C.ny == NYV && L.CW == CWV) {                                            \
+            e = epr_launch_kernel(pdl, k_col_tma<NYV, CWV, 8>, grid, dim3(NYV * CWV / 8), smem, \
+                                  stream, C, A, map);                                         \
+            done = true;                                                                      \
+        }
+        EPR_COL_TMA_CASE(256, 4)
+        EPR_COL_TMA_CASE(512, 4)
+        EPR_COL_TMA_CASE(1024, 4)
+        EPR_COL_TMA_CASE(2048, 2)
+#undef EPR_COL_TMA_CASE
+    }
 #define EPR_COL_CASE(NYV, CWV, EPTV)                                                           \
     if (!done && C.ny == NYV && L.CW == CWV && L.EPT == EPTV) {                               \
         e = epr_launch_kernel(pdl, k_col_ct<NYV, CWV, EPTV>, grid, dim3(NYV * CWV / EPTV),    \
@@ -216,6 +354,10 @@ cudaError_t epr_col_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<512, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1024, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<2048, 2, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<256, 4, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<512, 4, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1024, 4, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<4096, 1, 8>);
     return e;
 }

@@ -21,6 +21,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+
 #include "epr_internal.cuh"
 
 // --- launchers from the other translation units -----------------------------
@@ -43,6 +45,7 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
                                int nl, int it, float omega, float eps, float tol, int batch,
                                int check_done, cudaStream_t stream);
 cudaError_t epr_row_init();
+bool epr_col_make_map(const EprConsts& C, const float2* S, long long rows, CUtensorMap* out);
 cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int nl, int batch,
                            int check_done, int cw_hint, cudaStream_t stream);
 cudaError_t epr_col_init();
@@ -89,6 +92,7 @@ struct epr_plan_s {
     double E[EPR_MAX_LINES], delta[EPR_MAX_LINES], beta[EPR_MAX_LINES], w[EPR_MAX_LINES];
     // workspace
     EprWork W;
+    alignas(64) CUtensorMap col_map;   // S for the column pass's bulk copies
     int cap_batch;       // batch the workspace is sized for
     int cap_hist;        // history length it is sized for
     std::vector<void*> allocs;
@@ -229,6 +233,8 @@ epr_status ensure_workspace(epr_plan_s* p, int batch, int hist)
     }
     W.tw_x = p->tw_x;
     W.tw_y = p->tw_y;
+    W.col_map = epr_col_make_map(C, W.S, (long long)nb * C.ns * C.ny, &p->col_map) ? &p->col_map
+                                                                                   : nullptr;
     p->cap_batch = nb;
     p->cap_hist = nh;
     // pinned host mirrors for solve info
@@ -415,6 +421,7 @@ epr_status collect_info(epr_plan_s* p, int batch, int n_iter, epr_solve_info* in
     }
     if (first == 0) info->overflow_sources = 0;
     info->overflow_sources += ovf;
+    if (herr & EPR_DEVERR_TIMEOUT) return EPR_ERR_TIMEOUT;
     if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
     return EPR_OK;
 }
@@ -904,6 +911,7 @@ epr_status epr_check_device_status(epr_plan_t p, void* stream)
     EPR_TRY(cudaMemcpyAsync(&herr, p->W.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     EPR_TRY(cudaMemsetAsync(p->W.err, 0, sizeof(unsigned int), s));
     EPR_TRY(cudaStreamSynchronize(s));
+    if (herr & EPR_DEVERR_TIMEOUT) return EPR_ERR_TIMEOUT;
     if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
     return EPR_OK;
 }

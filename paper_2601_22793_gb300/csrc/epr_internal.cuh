@@ -14,6 +14,7 @@
 
 // Device-side error bits (OR-ed into the plan's error word).
 #define EPR_DEVERR_OVERFLOW 1u
+#define EPR_DEVERR_TIMEOUT 2u    // a bounded wait on a bulk copy gave up
 
 // Fixed-point scale of the deterministic splat: value * 2^40.
 #define EPR_FX_SCALE 1099511627776.0f
@@ -72,6 +73,8 @@ struct EprWork {
     const float2* tw_y;  // twiddles exp(-2 pi i t / ny), t < ny
     int hist_len;        // columns of rho_hist / kappa_hist
     int max_blocks;      // columns of part_a / part_b
+    const void* col_map; // host: CUtensorMap of S for the column pass's bulk
+                         // copies (NULL: the column pass uses plain loads)
 };
 
 // --- small helpers ---------------------------------------------------------

@@ -48,6 +48,12 @@ struct PadCol {
     __host__ __device__ static __forceinline__ int len(int n) { return n + 2 * (n >> 4) + 2; }
 };
 
+// Plain dense layout (a tile written by a bulk copy).
+struct Dense {
+    __host__ __device__ static __forceinline__ int idx(int i) { return i; }
+    __host__ __device__ static __forceinline__ int len(int n) { return n; }
+};
+
 // R-point DFTs in registers, sign DIR (-1 forward, +1 inverse).
 template <int DIR>
 __device__ __forceinline__ void dft2(float2& a, float2& b)
@@ -243,8 +249,11 @@ __host__ __device__ constexpr int ct_ns(int n, int s)
     return v;
 }
 
-template <class PAD, int R, int DIR, int EPT, int N, int NS, int LGSEQ, int SJ, int SM>
-__device__ __forceinline__ void stage_ct(float2* buf, const float2* __restrict__ tw, int tid)
+// Reads its operands from `in` (layout PADI) and writes to `buf` (layout
+// PAD); in == buf for every stage but a first one fed from another tile.
+template <class PADI, class PAD, int R, int DIR, int EPT, int N, int NS, int LGSEQ, int SJ, int SM>
+__device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const float2* __restrict__ tw,
+                                         int tid)
 {
     constexpr int NSEQ = 1 << LGSEQ;
     constexpr int T = (N * NSEQ) / EPT;
@@ -265,7 +274,7 @@ __device__ __forceinline__ void stage_ct(float2* buf, const float2* __restrict__
             const int jd = j / NS;
             const int base = m * SM;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][r] = buf[PAD::idx((j + r * NR) * SJ + base)];
+            for (int r = 0; r < R; ++r) v[k][r] = in[PADI::idx((j + r * NR) * SJ + base)];
             if constexpr (NS > 1) {
                 float2 w = __ldg(&tw[jm * TWSTEP]);
                 if (DIR > 0) w.y = -w.y;
@@ -295,9 +304,19 @@ template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int S =
 __device__ __forceinline__ void fft_ct(float2* buf, const float2* __restrict__ tw, int tid)
 {
     if constexpr (S < ct_n_stages(N)) {
-        stage_ct<PAD, ct_radix(N, S), DIR, EPT, N, ct_ns(N, S), LGSEQ, SJ, SM>(buf, tw, tid);
+        stage_ct<PAD, PAD, ct_radix(N, S), DIR, EPT, N, ct_ns(N, S), LGSEQ, SJ, SM>(buf, buf, tw, tid);
         fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, S + 1>(buf, tw, tid);
     }
+}
+
+// The same transform with its input in a separate dense tile `in` (element
+// j of sequence m at in[j * SJ + m * SM]); the result is in buf.
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM>
+__device__ __forceinline__ void fft_ct_from(const float2* in, float2* buf, const float2* __restrict__ tw,
+                                            int tid)
+{
+    stage_ct<Dense, PAD, ct_radix(N, 0), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid);
+    fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, 1>(buf, tw, tid);
 }
 
 }  // namespace eprfft
