@@ -110,11 +110,14 @@ k_splat(const EprConsts C, const SplatArgs A)
     const int SH = RH + 2, SWa = TW + 2 * HX;        // staged thickness
     const int coff = HX - R - 1;                     // staged column of source column tx0 - R - 1
     const int tile = TH * TW;
+    // accumulators [ns][TH + 2][TW + 2]: the tile with a one-pixel apron, so
+    // the four corners of any source that touches the tile have a slot
+    const int AP = TW + 2, ACC = (TH + 2) * AP;
     const size_t npix = (size_t)nx * ny;
     const int tid = threadIdx.x;
 
     void* acc = smem;
-    const size_t acc_bytes = (size_t)ns * tile * (DET ? 8 : 4);
+    const size_t acc_bytes = (size_t)ns * ACC * (DET ? 8 : 4);
     float* Ts = reinterpret_cast<float*>(smem + ((acc_bytes + 15) & ~size_t(15)));
     const float* Tb = A.T + (size_t)b * npix;
     if (tid == 0) s_far_n = 0;
@@ -140,10 +143,10 @@ k_splat(const EprConsts C, const SplatArgs A)
 
     if constexpr (DET) {
         unsigned long long* a = reinterpret_cast<unsigned long long*>(acc);
-        for (int i = tid; i < ns * tile; i += kSplatThreads) a[i] = 0ull;
-    } else {
-        float4* a = reinterpret_cast<float4*>(acc);
-        for (int i = tid; i < ns * tile / 4; i += kSplatThreads) a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = tid; i < ns * ACC; i += kSplatThreads) a[i] = 0ull;
+    } else {   // ACC = 4 (TH/2 + 1)(TW/2 + 1)
+        uint4* a = reinterpret_cast<uint4*>(acc);
+        for (int i = tid; i < ns * ACC / 4; i += kSplatThreads) a[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     // T, the done flags and the overflow counters come from earlier kernels
     epr_grid_wait();
@@ -168,9 +171,11 @@ k_splat(const EprConsts C, const SplatArgs A)
     const float fsmax = (float)C.smax;
     const float fxs = A.fxs;
     const int nsrc = RH * RW;
-    const float inv_RW = 1.f / (float)RW;
-    for (int i = tid; i < nsrc; i += kSplatThreads) {
-        const int ly = fdiv(i, inv_RW), lx = i - ly * RW;
+    // (ly, lx) of source i, advanced by kSplatThreads = dly rows + dlx columns
+    const int dly = kSplatThreads / RW, dlx = kSplatThreads - dly * RW;
+    int ly = tid / RW, lx = tid - (tid / RW) * RW;
+    for (int i = tid; i < nsrc;
+         i += kSplatThreads, lx += dlx, ly += dly + (lx >= RW ? 1 : 0), lx -= (lx >= RW ? RW : 0)) {
         const int sy = ty0 - R + ly, sx = tx0 - R + lx;
         const float* tp = Ts + (ly + 1) * SWa + (lx + 1 + coff);
         const float t = tp[0];
@@ -195,19 +200,16 @@ k_splat(const EprConsts C, const SplatArgs A)
             const float fx = floorf(ux), fy = floorf(uy);
             const float dx = ux - fx, dy = uy - fy;
             const int cx = lx - R + (int)fx, cy = ly - R + (int)fy;  // corner 00, tile-local
+            // no corner in the tile; otherwise all four have a slot (apron)
             if ((unsigned)(cx + 1) > (unsigned)TW || (unsigned)(cy + 1) > (unsigned)TH) continue;
             const float m = C.f[s] * __expf(-C.mu[s] * t);
             const float mx1 = m * dx, mx0 = m - mx1;          // m (1 - dx), m dx
-            const int idx = s * tile + cy * TW + cx;
-            if (cy >= 0) {
-                const float w = 1.f - dy;
-                if (cx >= 0) acc_add<DET>(acc, idx, mx0 * w, fxs);
-                if (cx + 1 < TW) acc_add<DET>(acc, idx + 1, mx1 * w, fxs);
-            }
-            if (cy + 1 < TH) {
-                if (cx >= 0) acc_add<DET>(acc, idx + TW, mx0 * dy, fxs);
-                if (cx + 1 < TW) acc_add<DET>(acc, idx + TW + 1, mx1 * dy, fxs);
-            }
+            const float w = 1.f - dy;
+            const int idx = s * ACC + (cy + 1) * AP + (cx + 1);
+            acc_add<DET>(acc, idx, mx0 * w, fxs);
+            acc_add<DET>(acc, idx + 1, mx1 * w, fxs);
+            acc_add<DET>(acc, idx + AP, mx0 * dy, fxs);
+            acc_add<DET>(acc, idx + AP + 1, mx1 * dy, fxs);
         }
         if (far && (unsigned)(ly - R) < (unsigned)TH && (unsigned)(lx - R) < (unsigned)TW) {
             const int pos = atomicAdd(&s_far_n, 1);
@@ -246,7 +248,7 @@ k_splat(const EprConsts C, const SplatArgs A)
 
     // flush: every pixel of the tile inside the grid, once, coalesced
     if constexpr (RESID) {
-        const uint4* a4 = reinterpret_cast<const uint4*>(acc);
+        const unsigned int* a = reinterpret_cast<const unsigned int*>(acc);
         const float inv = A.fxs_inv;
 #pragma unroll
         for (int k = 0; k < kDq; ++k) {
@@ -255,11 +257,11 @@ k_splat(const EprConsts C, const SplatArgs A)
             const int ly = i4 / tw4, lx = (i4 - ly * tw4) << 2;
             const int gy = ty0 + ly, gx = tx0 + lx;
             if (gy >= ny || gx >= nx) continue;
-            const uint4 v = a4[i4];
+            const unsigned int* v = a + (ly + 1) * AP + lx + 1;
             const float4 d = dreg[k];
             *reinterpret_cast<float4*>(A.P + (size_t)b * npix + (size_t)gy * nx + gx) =
-                make_float4(d.x - (float)v.x * inv, d.y - (float)v.y * inv,
-                            d.z - (float)v.z * inv, d.w - (float)v.w * inv);
+                make_float4(d.x - (float)v[0] * inv, d.y - (float)v[1] * inv,
+                            d.z - (float)v[2] * inv, d.w - (float)v[3] * inv);
         }
     } else {
         for (int i = tid; i < tile; i += kSplatThreads) {
@@ -271,7 +273,7 @@ k_splat(const EprConsts C, const SplatArgs A)
                 const unsigned long long* a = reinterpret_cast<const unsigned long long*>(acc);
                 unsigned long long sum = 0ull;
                 for (int s = 0; s < ns; ++s) {
-                    const unsigned long long q = a[s * tile + i];
+                    const unsigned long long q = a[s * ACC + (ly + 1) * AP + lx + 1];
                     sum += q;
                     if (ns > 1) A.Psq[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = q;
                 }
@@ -281,7 +283,7 @@ k_splat(const EprConsts C, const SplatArgs A)
                 const unsigned int* a = reinterpret_cast<const unsigned int*>(acc);
                 unsigned int sum = 0u;
                 for (int s = 0; s < ns; ++s) {
-                    const unsigned int q = a[s * tile + i];
+                    const unsigned int q = a[s * ACC + (ly + 1) * AP + lx + 1];
                     sum += q;
                     if (ns > 1)
                         A.Ps[(size_t)s * npix + o + (size_t)b * (ns - 1) * npix] = (float)q * A.fxs_inv;
@@ -364,7 +366,7 @@ size_t epr_splat_smem(const EprConsts& C, int TH, int TW)
 {
     const int R = C.smax + 1;
     const int HX = (R + 1 + 3) & ~3;
-    const size_t acc_bytes = (size_t)C.ns * TH * TW * (C.det ? 8 : 4);
+    const size_t acc_bytes = (size_t)C.ns * (TH + 2) * (TW + 2) * (C.det ? 8 : 4);
     return ((acc_bytes + 15) & ~size_t(15)) + (size_t)(TH + 2 * R + 2) * (TW + 2 * HX) * sizeof(float);
 }
 
