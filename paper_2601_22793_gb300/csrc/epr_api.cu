@@ -36,9 +36,11 @@ struct EprRowLaunch {
     size_t smem;
 };
 EprRowLaunch epr_row_config(const EprConsts& C);
-cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, int resid,
-                               const float* T, const float* D, const float* G, int line0, int nl,
-                               int it, int batch, int check_done, cudaStream_t stream);
+cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
+                               const float* D, const float* G, int line0, int nl, int it,
+                               int batch, int check_done, cudaStream_t stream);
+cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* D, int batch,
+                             int check_done, cudaStream_t stream);
 cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* D, int batch,
                              cudaStream_t stream);
 cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, float* Out, int line0,
@@ -362,16 +364,22 @@ epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, cons
         EPR_TRY(epr_launch_dnorm(C, p->W, D, batch, s));
     }
     const int fwd_mode = model == EPR_MODEL_NONLOCAL ? 0 : 1;
-    // monochromatic float transport: the splat stores the residual D - P
-    const bool resid = model == EPR_MODEL_NONLOCAL && C.ns == 1 && !C.det;
+    // non-local: the residual D - P (and its split over the lines) is stored
+    // by the splat flush (one line, float accumulation) or by the split
+    // kernel after the overflow sources (several lines, or fixed point)
+    const bool nl = model == EPR_MODEL_NONLOCAL;
+    const bool resid_in_splat = nl && C.ns == 1 && !C.det;
     const float eps = (float)(o->eps_I > 0 ? o->eps_I : 1e-8);
     for (int it = 0; it < o->n_iter; ++it) {
-        epr_status st = launch_forward(p, T, resid ? D : nullptr, it & 1, batch, model, 1, s);
+        epr_status st = launch_forward(p, T, resid_in_splat ? D : nullptr, it & 1, batch, model, 1, s);
         if (st != EPR_OK) return st;
+        if (nl && !resid_in_splat) {
+            ProfScope ps(p, EPR_KERNEL_OTHER, s);
+            EPR_TRY(epr_launch_split(C, p->W, D, batch, 1, s));
+        }
         {
             ProfScope ps(p, EPR_KERNEL_ROW_FWD, s);
-            EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, resid, T, D, nullptr, 0, C.ns, it, batch,
-                                       1, s));
+            EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, T, D, nullptr, 0, C.ns, it, batch, 1, s));
         }
         {
             ProfScope ps(p, EPR_KERNEL_COL, s);
@@ -501,7 +509,6 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
     st = resolve(p, 1, T, n, o->init != 0, s, &Td, &sT);
     if (st != EPR_OK) return st;
 
-    const int kernels_per_iter = model == EPR_MODEL_NONLOCAL ? 5 : 4;
     if (p->profiling && o->n_iter > 0) {
         // profiled solve: capture a fresh graph whose kernels are bracketed by
         // event-record nodes, so the kernels run back to back as in the timed
@@ -515,6 +522,7 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
         const long long before = g_launches.load();
         epr_status ls = launch_solve(p, Dd, Td, batch, o, model, p->cap_stream);
         cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+        const long long captured = g_launches.load() - before;
         g_launches.store(before);
         if (ls != EPR_OK) {
             if (ce == cudaSuccess) cudaGraphDestroy(g);
@@ -525,7 +533,7 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
         cudaGraphDestroy(g);
         EPR_TRY(ie);
         EPR_TRY(cudaGraphLaunch(p->prof_exec, s));
-        epr_count_launch(kernels_per_iter * o->n_iter + 2);
+        epr_count_launch((int)captured);
     } else if (p->opt.use_graphs && o->n_iter > 0) {
         GraphKey key{Dd, Td, batch, o->n_iter, o->init, model, o->omega, o->tol, o->eps_I};
         if (!(p->has_graph && p->gkey == key)) {
@@ -538,6 +546,7 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
             const long long before = g_launches.load();
             epr_status ls = launch_solve(p, Dd, Td, batch, o, model, p->cap_stream);
             cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+            const long long captured = g_launches.load() - before;
             g_launches.store(before);  // captured launches did not run
             if (ls != EPR_OK) {
                 if (ce == cudaSuccess) cudaGraphDestroy(g);
@@ -548,7 +557,7 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
             cudaGraphDestroy(g);
             EPR_TRY(ie);
             p->gkey = key;
-            p->gkernels = kernels_per_iter * o->n_iter + 2;
+            p->gkernels = (int)captured;
             p->has_graph = true;
         }
         EPR_TRY(cudaGraphLaunch(p->gexec, s));
@@ -812,7 +821,7 @@ epr_status epr_precondition(epr_plan_t p, float* g, int line, int batch, void* s
     bool sg;
     st = resolve(p, 0, g, n, true, s, &gd, &sg);
     if (st != EPR_OK) return st;
-    EPR_TRY(epr_launch_row_fwd(p->C, p->W, 2, 0, nullptr, nullptr, gd, line, 1, 0, batch, 0, s));
+    EPR_TRY(epr_launch_row_fwd(p->C, p->W, 2, nullptr, nullptr, gd, line, 1, 0, batch, 0, s));
     EPR_TRY(epr_launch_col(p->C, p->W, line, 1, batch, 0, 0, s));
     EPR_TRY(epr_launch_row_inv(p->C, p->W, 1, gd, line, 1, 0, 1.f, 0.f, 0.f, batch, 0, s));
     if (sg) {

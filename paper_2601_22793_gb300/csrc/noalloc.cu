@@ -37,9 +37,9 @@ constexpr size_t kNoallocBytes = kNoallocSpectrum + kNoallocTwiddles;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 // launchers of the preconditioner passes (rowfft.cu, colfft.cu)
-cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, int resid,
-                               const float* T, const float* D, const float* G, int line0, int nl,
-                               int it, int batch, int check_done, cudaStream_t stream);
+cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
+                               const float* D, const float* G, int line0, int nl, int it,
+                               int batch, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, float* Out,
                                int line0, int nl, int it, float omega, float eps, float tol,
                                int batch, int check_done, cudaStream_t stream);
@@ -144,7 +144,7 @@ extern "C" epr_status epr_precondition_noalloc(float* g, int nx, int ny, double 
     k_noalloc_twiddles<<<(ny + 255) / 256, 256, 0, s>>>(tw_y, ny);
     epr_count_launch(2);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = epr_launch_row_fwd(C, W, 2, 0, nullptr, nullptr, g, 0, 1, 0, batch, 0, s);
+    if (e == cudaSuccess) e = epr_launch_row_fwd(C, W, 2, nullptr, nullptr, g, 0, 1, 0, batch, 0, s);
     if (e == cudaSuccess) e = epr_launch_col(C, W, 0, 1, batch, 0, 0, s);
     if (e == cudaSuccess) e = epr_launch_row_inv(C, W, 1, g, 0, 1, 0, 1.f, 0.f, 0.f, batch, 0, s);
     return e == cudaSuccess ? EPR_OK : EPR_ERR_CUDA;

@@ -73,8 +73,9 @@ template <bool DET, bool RESID>
 __device__ __forceinline__ float resid(const EprConsts& C, const RowArgs& A, size_t pb, size_t q,
                                        int s)
 {
-    if constexpr (RESID) {
-        return __ldg(&A.P[pb + q]);
+    if constexpr (RESID) {   // the split residuals of the splat / split kernels
+        if (C.ns == 1) return __ldg(&A.P[pb + q]);
+        return __ldg(&A.Ps[pb * C.ns + (size_t)s * C.nx * C.ny + q]);
     } else {
         const float d = __ldg(&A.D[pb + q]);
         const float p = ldP<DET>(A.P, A.Pq, pb + q);
@@ -402,7 +403,7 @@ __global__ void k_sumsq_final(const double* part, int nparts, int max_blocks, Ep
 template <int NX>
 __host__ __device__ constexpr int ct_lg(int v) { return v <= 1 ? 0 : 1 + ct_lg<NX>(v / 2); }
 
-template <int NX, int RP>
+template <int NX, int RP, bool POLY>
 __global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
 k_row_fwd_mono(const EprConsts C, const RowArgs A)
 {
@@ -414,6 +415,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
     const int b = blockIdx.y;
+    const int sl = POLY ? (int)blockIdx.z : 0;   // line of this block (polychromatic)
     const int ny = C.ny, tid = threadIdx.x;
     const size_t npix = (size_t)NX * ny;
     const size_t pb = (size_t)b * npix;
@@ -442,8 +444,10 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     }
     cp_async_wait_all();
     __syncthreads();
-    const float cs = C.c[0];
-    const float* Rb = A.P + pb;   // residual D - P
+    const float cs = POLY ? line_const(C.c, A.line0 + sl) : C.c[0];
+    // residual D - P (one line) or the line's split residual
+    const float* Rb = POLY ? A.Ps + (pb * C.ns + (size_t)(A.line0 + sl) * npix) : A.P + pb;
+    const float* Rt = A.P + pb;   // D - P, for |D - P|^2
     float ra = 0.f;
 #pragma unroll 2
     for (int k = 0; k < kEPT; ++k) {
@@ -484,15 +488,17 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
             const float top = r00 + dx * (r10 - r00);
             const float bot = r01 + dx * (r11 - r01);
             v[r0] = (1.f - dy) * top + dy * bot;
-            const float own = __ldg(Rb + (size_t)y * NX + x);
-            ra += own * own;
+            if (!POLY || sl == 0) {
+                const float own = __ldg(Rt + (size_t)y * NX + x);
+                ra += own * own;
+            }
         }
         zs[PR::idx(m * SM + x)] = make_float2(v[0], v[1]);
     }
     __syncthreads();
     eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
     epr_grid_release();
-    float2* Sb = A.S + (size_t)b * (size_t)ny * HALF;
+    float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * HALF;
 #pragma unroll 2
     for (int i0 = 0; i0 < RP * HALF; i0 += T) {
         const int e = i0 + tid;
@@ -513,6 +519,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
         Sb[(size_t)y0 * HALF + k] = X0;
         Sb[(size_t)(y0 + 1) * HALF + k] = X1;
     }
+    if (POLY && sl != 0) return;   // the residual norm is line 0's
     float rb = 0.f;
     block_sum2(ra, rb, red);
     double sa, sb;
@@ -612,18 +619,142 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
     }
 }
 
+// Polychromatic update on the compile-time engine: for each line, the C2R
+// rows of its filtered spectrum and w_s ln(I'_s / I_s), accumulated per
+// pixel in shared memory (each thread owns its pixels); then T' = T - sum
+// and the kappa partial sums.
+template <int NX, int RP>
+__global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
+k_row_inv_poly(const EprConsts C, const RowArgs A)
+{
+    constexpr int T = NX * RP / kEPT;
+    constexpr int SM = NX + kPad;
+    constexpr int HALF = NX / 2;
+    constexpr int LGRP = ct_lg<NX>(RP);
+    constexpr int LGNX = ct_lg<NX>(NX);
+    extern __shared__ __align__(16) float2 zs[];
+    __shared__ float red[64];
+    const int b = blockIdx.y;
+    const int ny = C.ny, tid = threadIdx.x;
+    const size_t pb = (size_t)b * NX * ny;
+    const int yb = blockIdx.x * RP * 2;
+    float* Tsh = reinterpret_cast<float*>(zs + ((PR::len(RP * SM) + 1) & ~1));   // [2 RP][NX]
+    float* acc = Tsh + 2 * RP * NX;                                              // [2 RP][NX]
+    {
+        constexpr int Q4 = 2 * RP * NX / 4;
+        const float4* src = reinterpret_cast<const float4*>(A.Out + pb + (size_t)yb * NX);
+#pragma unroll
+        for (int i0 = 0; i0 < Q4; i0 += T) {
+            const int i = i0 + tid;
+            if (Q4 % T == 0 || i < Q4) cp_async16(reinterpret_cast<float4*>(Tsh) + i, src + i);
+        }
+        cp_async_commit();
+    }
+    epr_grid_wait();
+    if (A.check_done && A.st[b].done) {
+        cp_async_wait_all();
+        return;
+    }
+    for (int sl = 0; sl < A.nl; ++sl) {
+        const int s = A.line0 + sl;
+        const float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * HALF;
+#pragma unroll 2
+        for (int i0 = 0; i0 < RP * HALF; i0 += T) {
+            const int e = i0 + tid;
+            const int m = e / HALF, k = e % HALF;
+            const int y0 = yb + 2 * m;
+            const float2 s0 = Sb[(size_t)y0 * HALF + k];
+            const float2 s1 = Sb[(size_t)(y0 + 1) * HALF + k];
+            const int zb = m * SM;
+            if (k == 0) {
+                zs[PR::idx(zb)] = make_float2(s0.x, s1.x);
+                zs[PR::idx(zb + HALF)] = make_float2(s0.y, s1.y);
+            } else {
+                zs[PR::idx(zb + k)] = make_float2(s0.x - s1.y, s0.y + s1.x);
+                zs[PR::idx(zb + NX - k)] = make_float2(s0.x + s1.y, s1.x - s0.y);
+            }
+        }
+        __syncthreads();
+        eprfft::fft_ct<PR, +1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
+        if (sl == 0) {
+            epr_grid_release();
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        const float fs = line_const(C.f, s), mus = line_const(C.mu, s), w = line_const(C.wproj, s);
+#pragma unroll 2
+        for (int k = 0; k < kEPT; ++k) {
+            const int e = tid + k * T;
+            const int m = e >> LGNX, x = e & (NX - 1);
+            const float2 h = zs[PR::idx(m * SM + x)];
+            const int i0 = (2 * m) * NX + x;
+            const float l0 = w * log_ratio(Tsh[i0], h.x, fs, mus, A.omega, A.eps);
+            const float l1 = w * log_ratio(Tsh[i0 + NX], h.y, fs, mus, A.omega, A.eps);
+            acc[i0] = sl == 0 ? l0 : acc[i0] + l0;
+            acc[i0 + NX] = sl == 0 ? l1 : acc[i0 + NX] + l1;
+        }
+        __syncthreads();   // the next line's unpack overwrites zs
+    }
+    float da = 0.f, db = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < kEPT; ++k) {
+        const int e = tid + k * T;
+        const int m = e >> LGNX, x = e & (NX - 1);
+        const int i0 = (2 * m) * NX + x;
+        const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
+        const float l0 = acc[i0], l1 = acc[i0 + NX];
+        const float n0 = Tsh[i0] - l0, n1 = Tsh[i0 + NX] - l1;
+        A.Out[q0] = n0;
+        A.Out[q0 + NX] = n1;
+        da += l0 * l0 + l1 * l1;
+        db += n0 * n0 + n1 * n1;
+    }
+    block_sum2(da, db, red);
+    double sa, sb;
+    if (last_block_reduce(&A.st[b].cnt_inv, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
+                          A.part_b + (size_t)b * A.max_blocks, blockIdx.x, da, db, sa, sb)) {
+        if (threadIdx.x == 0) {
+            const double kap = sb > 0.0 ? sqrt(sa / sb) : sqrt(sa);
+            A.st[b].kappa = (float)kap;
+            A.st[b].iters = A.it + 1;
+            if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = kap;
+            if (A.tol > 0.f && kap <= (double)A.tol) A.st[b].done = 1;
+        }
+    }
+}
+
+// dynamic shared memory of k_row_inv_poly: FFT rows, T rows, accumulators
+size_t row_inv_poly_smem(int nx, int rp)
+{
+    return (size_t)((PR::len(rp * (nx + kPad)) + 1) & ~1) * sizeof(float2) +
+           (size_t)2 * (2 * rp * nx) * sizeof(float);
+}
+
 // launch a specialised mono kernel when nx has one; returns false otherwise
 template <bool FWD>
 bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream, const EprConsts& C,
                     const RowArgs& A, cudaError_t& err)
 {
+    // one line: the mono kernels; several: forward with a line per grid z,
+    // inverse looping over the lines
+    const bool poly = A.nl > 1;
 #define EPR_MONO_CASE(NXV, RPV)                                                              \
     if (nx == NXV && rp == RPV) {                                                            \
         const dim3 blk(NXV * RPV / kEPT);                                                    \
-        if (FWD) err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV>, grid, blk,     \
-                                         smem, stream, C, A);                                \
-        else err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<NXV, RPV>, grid, blk, smem,   \
-                                     stream, C, A);                                          \
+        if (FWD && !poly) {                                                                  \
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, false>, grid, blk,   \
+                                    smem, stream, C, A);                                     \
+        } else if (FWD) {                                                                    \
+            const dim3 g3(grid.x, grid.y, A.nl);                                             \
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, true>, g3, blk, smem, \
+                                    stream, C, A);                                           \
+        } else if (!poly) {                                                                  \
+            err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<NXV, RPV>, grid, blk, smem,    \
+                                    stream, C, A);                                           \
+        } else {                                                                             \
+            err = epr_launch_kernel(C.pdl != 0, k_row_inv_poly<NXV, RPV>, grid, blk,          \
+                                    row_inv_poly_smem(NXV, RPV), stream, C, A);              \
+        }                                                                                    \
         return true;                                                                         \
     }
     EPR_MONO_CASE(256, 8)
@@ -642,8 +773,10 @@ cudaError_t init_mono_ct()
 {
     cudaError_t e = cudaSuccess;
 #define EPR_MONO_INIT(NXV, RPV)                                                  \
-    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV>);                    \
-    if (e == cudaSuccess) e = allow(k_row_inv_mono<NXV, RPV>);
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, false>);             \
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, true>);              \
+    if (e == cudaSuccess) e = allow(k_row_inv_mono<NXV, RPV>);                    \
+    if (e == cudaSuccess) e = allow(k_row_inv_poly<NXV, RPV>);
     EPR_MONO_INIT(256, 8)
     EPR_MONO_INIT(512, 4)
     EPR_MONO_INIT(1024, 2)
@@ -677,10 +810,10 @@ EprRowLaunch epr_row_config(const EprConsts& C)
 }
 
 // mode: 0 = non-local solve, 1 = local solve, 2 = load real map G.
-// resid = 1: P holds D - P (mono float solve).
-cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, int resid,
-                               const float* T, const float* D, const float* G, int line0, int nl,
-                               int it, int batch, int check_done, cudaStream_t stream)
+// FWD_SOLVE_NL reads the residual D - P from P and the split residuals from P_s.
+cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
+                               const float* D, const float* G, int line0, int nl, int it,
+                               int batch, int check_done, cudaStream_t stream)
 {
     const EprRowLaunch L = epr_row_config(C);
     RowArgs A = {};
@@ -695,15 +828,11 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, i
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kernel) { e = epr_launch_kernel(pdl, kernel, grid, blk, L.smem, stream, C, A); };
     if (mode == FWD_SOLVE_NL) {
-        if (C.det) {
-            if (mono) go(k_row_fwd<FWD_SOLVE_NL, true, false, 1>);
-            else go(k_row_fwd<FWD_SOLVE_NL, true, false, 0>);
-        } else if (resid && mono) {
-            if (!launch_mono_ct<true>(C.nx, L.RP, grid, L.smem, stream, C, A, e))
-                go(k_row_fwd<FWD_SOLVE_NL, false, true, 1>);
-        } else {
-            if (mono) go(k_row_fwd<FWD_SOLVE_NL, false, false, 1>);
-            else go(k_row_fwd<FWD_SOLVE_NL, false, false, 0>);
+        // the residual D - P is in P and, with several lines, the split
+        // residuals in P_s (written by the splat flush or the split kernel)
+        if (!launch_mono_ct<true>(C.nx, L.RP, grid, L.smem, stream, C, A, e)) {
+            if (mono) go(k_row_fwd<FWD_SOLVE_NL, false, true, 1>);
+            else go(k_row_fwd<FWD_SOLVE_NL, false, true, 0>);
         }
     } else if (mode == FWD_SOLVE_LOCAL) {
         // the local closure writes float maps in both accumulation modes
@@ -730,7 +859,7 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kernel) { e = epr_launch_kernel(pdl, kernel, grid, blk, L.smem, stream, C, A); };
     if (mode == INV_UPDATE) {
-        if (nl == 1 && !C.det && launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A, e)) {
+        if (launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A, e)) {
         } else if (nl == 1) go(k_row_inv<INV_UPDATE, 1>);
         else go(k_row_inv<INV_UPDATE, 0>);
     } else {

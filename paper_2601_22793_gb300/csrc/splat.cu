@@ -348,6 +348,34 @@ __global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const
     }
 }
 
+// The residual and its split over the lines (the weights P_s / P of the
+// "Iteration structure"; r f_s where P vanishes), once per pixel after the
+// overflow sources are in: P <- D - P and P_s <- (D - P) P_s / P as float
+// maps, so that the adjoint gather reads one value per corner and line.  In
+// fixed-point mode the sums are read from the integer maps.
+template <bool DET>
+__global__ void __launch_bounds__(256) k_split(const EprConsts C, const SplatArgs A)
+{
+    const int b = blockIdx.y;
+    epr_grid_wait();
+    if (A.check_done && A.st[b].done) return;
+    epr_grid_release();
+    const int ns = C.ns;
+    const size_t npix = (size_t)C.nx * C.ny, pb = (size_t)b * npix;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < npix;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const float d = __ldg(&A.D[pb + q]);
+        const float p = DET ? (float)A.Pq[pb + q] * EPR_FX_INV : A.P[pb + q];
+        const float r = d - p;
+        for (int s = 0; ns > 1 && s < ns; ++s) {   // one line: r itself
+            const size_t o = (pb * ns) + (size_t)s * npix + q;
+            const float pl = DET ? (float)A.Psq[o] * EPR_FX_INV : A.Ps[o];
+            A.Ps[o] = (p > 1e-30f) ? r * (pl / p) : r * line_const(C.f, s);
+        }
+        A.P[pb + q] = r;
+    }
+}
+
 template <int NS, bool DET, bool RESID>
 cudaError_t launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
                      cudaStream_t stream)
@@ -426,4 +454,27 @@ cudaError_t epr_splat_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, false>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false>);
     return e;
+}
+
+// Residual split after the splat of a polychromatic (or fixed-point) solve.
+cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* D, int batch,
+                             int check_done, cudaStream_t stream)
+{
+    SplatArgs A = {};
+    A.D = D;
+    A.P = W.P;
+    A.Ps = W.Ps;
+    A.Pq = W.Pq;
+    A.Psq = W.Psq;
+    A.st = W.st;
+    A.check_done = check_done;
+    const size_t npix = (size_t)C.nx * C.ny;
+    size_t blocks = (npix + 255) / 256;
+    if (blocks > 1216) blocks = 1216;   // 8 per SM on 152 SMs, grid-stride beyond
+    const dim3 grid((unsigned)blocks, batch);
+    const cudaError_t e =
+        C.det ? epr_launch_kernel(C.pdl != 0, k_split<true>, grid, dim3(256), 0, stream, C, A)
+              : epr_launch_kernel(C.pdl != 0, k_split<false>, grid, dim3(256), 0, stream, C, A);
+    epr_count_launch(1);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
