@@ -213,10 +213,11 @@ def _spheres_data(oracle):
     return wl, ln, D
 
 
-def test_solve_nonlocal_spheres_mono(torch, E, oracle):
+@pytest.mark.parametrize("det", [False, True])
+def test_solve_nonlocal_spheres_mono(torch, E, oracle, det):
     wl, ln, D = _spheres_data(oracle)
     Tr, info_r = oracle.solve(ln, D.astype(np.float64), n_iter=wl.n_iter, omega=wl.omega)
-    with plan_of(E, wl) as p:
+    with plan_of(E, wl, deterministic=det) as p:
         Dd = cuda(torch, D)
         T = torch.empty_like(Dd)
         info = E.epr_solve_nonlocal(p.handle, Dd, T, n_iter=wl.n_iter, omega=wl.omega)
@@ -237,6 +238,24 @@ def test_solve_nonlocal_poly(torch, E, oracle):
         info = E.epr_solve_nonlocal(p.handle, Dd, T, n_iter=wl.n_iter, omega=wl.omega)
     assert rel(host(T), Tr) < 1e-4
     assert np.allclose(info["rho_hist"][0], info_r["rho"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("ny,nx", [(256, 256), (256, 512)])
+@pytest.mark.parametrize("det", [False, True])
+def test_solve_poly_compile_time_row_kernels(torch, E, oracle, ny, nx, det):
+    """Row lengths with compile-time row kernels (the line-per-block gather and
+    the line-looping inverse) against the oracle, float and fixed point."""
+    wl, T32 = small_poly(ny=ny, nx=nx, n_lines=4, seed=12)
+    ln = lines_of(oracle, wl)
+    D = ph.poisson(oracle.forward(ln, T32.astype(np.float64)), wl.photons, 6).astype(np.float32)
+    Tr, info_r = oracle.solve(ln, D.astype(np.float64), n_iter=6, omega=0.4)
+    with plan_of(E, wl, deterministic=det) as p:
+        Dd = cuda(torch, D)
+        T = torch.empty_like(Dd)
+        info = E.epr_solve_nonlocal(p.handle, Dd, T, n_iter=6, omega=0.4)
+    assert rel(host(T), Tr) < 1e-4
+    assert np.allclose(info["rho_hist"][0], info_r["rho"], rtol=1e-3)
+    assert np.allclose(info["kappa_hist"][0][1:], info_r["kappa"][1:], rtol=1e-2)
 
 
 def test_solve_fixed_point_bit_exact_and_graph_replay(torch, E, oracle):
