@@ -41,6 +41,8 @@
 //  * Fixed-point mode accumulates round(v * 2^40) in uint64 (contributions
 //    are non-negative) in shared and global memory: integer addition is
 //    associative, so the result is bit-identical across runs.
+#include <type_traits>
+
 #include "epr_internal.cuh"
 
 namespace {
@@ -173,60 +175,71 @@ k_splat(const EprConsts C, const SplatArgs A)
     const int nsrc = RH * RW;
     // (ly, lx) of source i, advanced by kSplatThreads = dly rows + dlx columns
     const int dly = kSplatThreads / RW, dlx = kSplatThreads - dly * RW;
-    int ly = tid / RW, lx = tid - (tid / RW) * RW;
-    for (int i = tid; i < nsrc;
-         i += kSplatThreads, lx += dlx, ly += dly + (lx >= RW ? 1 : 0), lx -= (lx >= RW ? RW : 0)) {
-        const int sy = ty0 - R + ly, sx = tx0 - R + lx;
-        const float* tp = Ts + (ly + 1) * SWa + (lx + 1 + coff);
-        const float t = tp[0];
-        float gx, gy;
-        if (interior) {
-            gx = 0.5f * (tp[1] - tp[-1]);
-            gy = 0.5f * (tp[SWa] - tp[-SWa]);
-        } else {
-            if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) continue;
-            gx = grad1(tp[-1], t, tp[1], sx, nx);
-            gy = grad1(tp[-SWa], t, tp[SWa], sy, ny);
-        }
-        unsigned int far = 0u;
-#pragma unroll(NS ? NS : 1)
-        for (int s = 0; s < ns; ++s) {
-            const float cs = C.c[s];
-            const float ux = cs * gx, uy = cs * gy;
-            if (!(fabsf(ux) <= fsmax && fabsf(uy) <= fsmax && t >= C.tneg[s])) {
-                far |= 1u << s;
-                continue;
+    // The scan, specialised for blocks whose staged region lies inside the grid
+    // (central differences everywhere, no edge tests) and for edge blocks.
+    // Gradients are kept doubled (hi - lo), and half the shift constant
+    // multiplies them: 0.5 scales exactly, so u is the same float.
+    auto scan = [&](auto interior_tag) {
+        constexpr bool IN = decltype(interior_tag)::value;
+        int ly = tid / RW, lx = tid - (tid / RW) * RW;
+        for (int i = tid; i < nsrc; i += kSplatThreads, lx += dlx,
+                 ly += dly + (lx >= RW ? 1 : 0), lx -= (lx >= RW ? RW : 0)) {
+            const float* tp = Ts + (ly + 1) * SWa + (lx + 1 + coff);
+            const float t = tp[0];
+            float gx2, gy2;   // twice the gradient
+            if constexpr (IN) {
+                gx2 = tp[1] - tp[-1];
+                gy2 = tp[SWa] - tp[-SWa];
+            } else {
+                const int sy = ty0 - R + ly, sx = tx0 - R + lx;
+                if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) continue;
+                gx2 = 2.f * grad1(tp[-1], t, tp[1], sx, nx);
+                gy2 = 2.f * grad1(tp[-SWa], t, tp[SWa], sy, ny);
             }
-            const float fx = floorf(ux), fy = floorf(uy);
-            const float dx = ux - fx, dy = uy - fy;
-            const int cx = lx - R + (int)fx, cy = ly - R + (int)fy;  // corner 00, tile-local
-            // no corner in the tile; otherwise all four have a slot (apron)
-            if ((unsigned)(cx + 1) > (unsigned)TW || (unsigned)(cy + 1) > (unsigned)TH) continue;
-            const float m = C.f[s] * __expf(-C.mu[s] * t);
-            const float mx1 = m * dx, mx0 = m - mx1;          // m (1 - dx), m dx
-            const float w = 1.f - dy;
-            const int idx = s * ACC + (cy + 1) * AP + (cx + 1);
-            acc_add<DET>(acc, idx, mx0 * w, fxs);
-            acc_add<DET>(acc, idx + 1, mx1 * w, fxs);
-            acc_add<DET>(acc, idx + AP, mx0 * dy, fxs);
-            acc_add<DET>(acc, idx + AP + 1, mx1 * dy, fxs);
-        }
-        if (far && (unsigned)(ly - R) < (unsigned)TH && (unsigned)(lx - R) < (unsigned)TW) {
-            const int pos = atomicAdd(&s_far_n, 1);
-            if (pos < kFarList) {
-                s_far_idx[pos] = sy * nx + sx;
-                s_far_mask[pos] = far;
-            } else {   // list full: append to the global list directly
-                const int gpos = atomicAdd(&A.st[b].ovf_count[A.parity], 1);
-                if (gpos < C.ovf_cap) {
-                    A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = sy * nx + sx;
-                    A.ovf_mask[(size_t)b * C.ovf_cap + gpos] = far;
+            unsigned int far = 0u;
+#pragma unroll(NS ? NS : 1)
+            for (int s = 0; s < ns; ++s) {
+                const float ch = 0.5f * C.c[s];
+                const float ux = ch * gx2, uy = ch * gy2;
+                if (fabsf(ux) <= fsmax && fabsf(uy) <= fsmax && t >= C.tneg[s]) {
+                    const float fx = floorf(ux), fy = floorf(uy);
+                    const int cx = lx - R + (int)fx, cy = ly - R + (int)fy;  // corner 00, tile-local
+                    // all four corners have a slot (apron) when one is in the tile
+                    if ((unsigned)(cx + 1) <= (unsigned)TW && (unsigned)(cy + 1) <= (unsigned)TH) {
+                        const float dx = ux - fx, dy = uy - fy;
+                        const float m = C.f[s] * __expf(-C.mu[s] * t);
+                        const float mx1 = m * dx, mx0 = m - mx1;          // m (1 - dx), m dx
+                        const float w = 1.f - dy;
+                        const int idx = s * ACC + (cy + 1) * AP + (cx + 1);
+                        acc_add<DET>(acc, idx, mx0 * w, fxs);
+                        acc_add<DET>(acc, idx + 1, mx1 * w, fxs);
+                        acc_add<DET>(acc, idx + AP, mx0 * dy, fxs);
+                        acc_add<DET>(acc, idx + AP + 1, mx1 * dy, fxs);
+                    }
                 } else {
-                    atomicOr(A.err, EPR_DEVERR_OVERFLOW);
+                    far |= 1u << s;
+                }
+            }
+            if (far && (unsigned)(ly - R) < (unsigned)TH && (unsigned)(lx - R) < (unsigned)TW) {
+                const int sy = ty0 - R + ly, sx = tx0 - R + lx;
+                const int pos = atomicAdd(&s_far_n, 1);
+                if (pos < kFarList) {
+                    s_far_idx[pos] = sy * nx + sx;
+                    s_far_mask[pos] = far;
+                } else {   // list full: append to the global list directly
+                    const int gpos = atomicAdd(&A.st[b].ovf_count[A.parity], 1);
+                    if (gpos < C.ovf_cap) {
+                        A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = sy * nx + sx;
+                        A.ovf_mask[(size_t)b * C.ovf_cap + gpos] = far;
+                    } else {
+                        atomicOr(A.err, EPR_DEVERR_OVERFLOW);
+                    }
                 }
             }
         }
-    }
+    };
+    if (interior) scan(std::true_type{});
+    else scan(std::false_type{});
     __syncthreads();
     epr_grid_release();
 
