@@ -55,7 +55,7 @@ __device__ __forceinline__ void col_filter(float2* buf, const EprConsts& C, int 
             const float kn = (float)half;
             const float H0 = inv_n / (1.f + qy);
             const float HN = inv_n / (1.f + ha * kn * kn + qy);
-            const int yneg = (NY - y) & (NY - 1);
+            const int yneg = y == 0 ? 0 : NY - y;
             const float2 w = cconj(buf[eprfft::PadCol::idx((yneg << LGCW) + c)]);
             const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
             nv[k] = make_float2(hp * v.x + hm * w.x, hp * v.y + hm * w.y);
@@ -254,7 +254,7 @@ static bool col_tma_case(const EprConsts& C, const EprColLaunch& L)
 {
     if (L.EPT != 8) return false;
     return (L.CW == 4 && (C.ny == 256 || C.ny == 512 || C.ny == 1024)) ||
-           (L.CW == 2 && C.ny == 2048);
+           (L.CW == 2 && (C.ny == 1536 || C.ny == 2048));
 }
 
 static size_t col_tma_smem(const EprConsts& C, const EprColLaunch& L)
@@ -321,6 +321,7 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
         EPR_COL_TMA_CASE(256, 4)
         EPR_COL_TMA_CASE(512, 4)
         EPR_COL_TMA_CASE(1024, 4)
+        EPR_COL_TMA_CASE(1536, 2)
         EPR_COL_TMA_CASE(2048, 2)
 #undef EPR_COL_TMA_CASE
     }
@@ -333,7 +334,9 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     EPR_COL_CASE(256, 4, 8)
     EPR_COL_CASE(512, 4, 8)
     EPR_COL_CASE(1024, 4, 8)
+    EPR_COL_CASE(1536, 2, 8)
     EPR_COL_CASE(2048, 2, 8)
+    EPR_COL_CASE(3072, 1, 8)
     EPR_COL_CASE(4096, 1, 8)
 #undef EPR_COL_CASE
     if (!done) {
@@ -357,7 +360,10 @@ cudaError_t epr_col_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<256, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<512, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1024, 4, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1536, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1536, 2, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<3072, 1, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<4096, 1, 8>);
     return e;
 }

@@ -403,6 +403,10 @@ __global__ void k_sumsq_final(const double* part, int nparts, int max_blocks, Ep
 template <int NX>
 __host__ __device__ constexpr int ct_lg(int v) { return v <= 1 ? 0 : 1 + ct_lg<NX>(v / 2); }
 
+// packed row pair of element e (0 <= e < NX RP); NX may be 3 * 2^k with RP = 1
+template <int NX, int RP>
+__device__ __forceinline__ int row_of(int e) { return RP == 1 ? 0 : (int)((unsigned)e / NX); }
+
 template <int NX, int RP, bool POLY>
 __global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
 k_row_fwd_mono(const EprConsts C, const RowArgs A)
@@ -411,7 +415,6 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     constexpr int SM = NX + kPad;
     constexpr int HALF = NX / 2;
     constexpr int LGRP = ct_lg<NX>(RP);
-    constexpr int LGNX = ct_lg<NX>(NX);
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
     const int b = blockIdx.y;
@@ -452,7 +455,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
 #pragma unroll 2
     for (int k = 0; k < kEPT; ++k) {
         const int e = tid + k * T;
-        const int m = e >> LGNX, x = e & (NX - 1);
+        const int m = row_of<NX, RP>(e), x = e - m * NX;
         const int y0 = yb + 2 * m;
         float v[2];
 #pragma unroll
@@ -542,7 +545,6 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
     constexpr int SM = NX + kPad;
     constexpr int HALF = NX / 2;
     constexpr int LGRP = ct_lg<NX>(RP);
-    constexpr int LGNX = ct_lg<NX>(NX);
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
     const int b = blockIdx.y;
@@ -593,7 +595,7 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
 #pragma unroll 2
     for (int k = 0; k < kEPT; ++k) {
         const int e = tid + k * T;
-        const int m = e >> LGNX, x = e & (NX - 1);
+        const int m = row_of<NX, RP>(e), x = e - m * NX;
         const float2 h = zs[PR::idx(m * SM + x)];
         const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
         const float t0 = Tsh[(2 * m) * NX + x], t1 = Tsh[(2 * m + 1) * NX + x];
@@ -631,7 +633,6 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
     constexpr int SM = NX + kPad;
     constexpr int HALF = NX / 2;
     constexpr int LGRP = ct_lg<NX>(RP);
-    constexpr int LGNX = ct_lg<NX>(NX);
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
     const int b = blockIdx.y;
@@ -685,7 +686,7 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
 #pragma unroll 2
         for (int k = 0; k < kEPT; ++k) {
             const int e = tid + k * T;
-            const int m = e >> LGNX, x = e & (NX - 1);
+            const int m = row_of<NX, RP>(e), x = e - m * NX;
             const float2 h = zs[PR::idx(m * SM + x)];
             const int i0 = (2 * m) * NX + x;
             const float l0 = w * log_ratio(Tsh[i0], h.x, fs, mus, A.omega, A.eps);
@@ -699,7 +700,7 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
 #pragma unroll 2
     for (int k = 0; k < kEPT; ++k) {
         const int e = tid + k * T;
-        const int m = e >> LGNX, x = e & (NX - 1);
+        const int m = row_of<NX, RP>(e), x = e - m * NX;
         const int i0 = (2 * m) * NX + x;
         const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
         const float l0 = acc[i0], l1 = acc[i0 + NX];
@@ -760,7 +761,9 @@ bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream,
     EPR_MONO_CASE(256, 8)
     EPR_MONO_CASE(512, 4)
     EPR_MONO_CASE(1024, 2)
+    EPR_MONO_CASE(1536, 1)
     EPR_MONO_CASE(2048, 1)
+    EPR_MONO_CASE(3072, 1)
     EPR_MONO_CASE(4096, 1)
 #undef EPR_MONO_CASE
     return false;
@@ -780,7 +783,9 @@ cudaError_t init_mono_ct()
     EPR_MONO_INIT(256, 8)
     EPR_MONO_INIT(512, 4)
     EPR_MONO_INIT(1024, 2)
+    EPR_MONO_INIT(1536, 1)
     EPR_MONO_INIT(2048, 1)
+    EPR_MONO_INIT(3072, 1)
     EPR_MONO_INIT(4096, 1)
 #undef EPR_MONO_INIT
     return e;

@@ -258,6 +258,23 @@ def test_solve_poly_compile_time_row_kernels(torch, E, oracle, ny, nx, det):
     assert np.allclose(info["kappa_hist"][0][1:], info_r["kappa"][1:], rtol=1e-2)
 
 
+@pytest.mark.parametrize("ny,nx,n_lines", [(96, 1536, 1), (1536, 96, 1), (64, 3072, 2),
+                                           (3072, 64, 2)])
+def test_solve_three_smooth_sizes(torch, E, oracle, ny, nx, n_lines):
+    """Row and column lengths 3 * 2^k on the compile-time kernels (radix-3
+    stages; the 1536-row column pass moves its tile by TMA)."""
+    wl, T32 = small_poly(ny=ny, nx=nx, n_lines=n_lines, seed=13)
+    ln = lines_of(oracle, wl)
+    D = ph.poisson(oracle.forward(ln, T32.astype(np.float64)), wl.photons, 7).astype(np.float32)
+    Tr, info_r = oracle.solve(ln, D.astype(np.float64), n_iter=4, omega=0.4)
+    with plan_of(E, wl) as p:
+        Dd = cuda(torch, D)
+        T = torch.empty_like(Dd)
+        info = E.epr_solve_nonlocal(p.handle, Dd, T, n_iter=4, omega=0.4)
+    assert rel(host(T), Tr) < 1e-4
+    assert np.allclose(info["rho_hist"][0], info_r["rho"], rtol=1e-3)
+
+
 def test_solve_fixed_point_bit_exact_and_graph_replay(torch, E, oracle):
     wl, T32 = small_poly(seed=10)
     ln = lines_of(oracle, wl)
