@@ -369,10 +369,38 @@ def run_ours(a):
     t_b = timeit(batched)
     t_p = timeit(plain_run)
     plain.close()
+    it_bytes = sum(kernel_bytes_per_px(1).values()) * npix   # algorithmic bytes per iteration
+    b_gbs = it_bytes * wl.n_iter * nb / (t_b * 1e-3) / 1e9
     bvp = {"batch": nb, "batched_ms": round(t_b, 3), "plain_ms": round(t_p, 3),
            "factor": round(t_p / t_b, 3),
+           "batched_projections_per_s": round(nb / (t_b * 1e-3), 3),
+           "batched_hbm": {"achieved_gbs": round(b_gbs, 1), "peak": peak,
+                           "frac": round(b_gbs / peak, 4),
+                           "note": "algorithmic bytes of all kernels of all iterations / time; "
+                                   "8 x 64 MiB working set exceeds L2"},
            "plain": "one projection per call, kernels launched one by one (no graph)",
            "batched": "one call for all projections, iteration loop replayed as a CUDA graph"}
+
+    # the same workload with the local O(L^2) closure, and an 8-line polychromatic solve
+    local_ms = timeit(lambda: epr.epr_solve_local(plan.handle, D, T, order=2, n_iter=wl.n_iter,
+                                                  omega=wl.omega, want_info=False))
+    other = {"local_closure_order2": {"ms_per_solve": round(local_ms, 3),
+                                      "projections_per_s": round(1e3 / local_ms, 3),
+                                      "n_iter": wl.n_iter}}
+    wp, ells, angles = ph.ellipsoids_poly()
+    tp = ph.project_ellipsoids(ells, wp.ny, wp.nx, wp.pixel, angles[rank % len(angles)])
+    pplan = epr.Plan(wp.nx, wp.ny, wp.pixel, wp.L, wp.energy_keV, wp.delta, wp.beta, wp.weights)
+    Tp = torch.from_numpy(tp.astype(np.float32)).cuda()
+    Pp = torch.empty_like(Tp)
+    epr.epr_forward(pplan.handle, Tp, Pp)
+    Dp = torch.from_numpy(ph.poisson(Pp.cpu().numpy(), wp.photons, 9).astype(np.float32)).cuda()
+    poly_ms = timeit(lambda: epr.epr_solve_nonlocal(pplan.handle, Dp, Tp, n_iter=wp.n_iter,
+                                                    omega=wp.omega, want_info=False), reps=3)
+    pplan.close()
+    other["polychromatic"] = {"workload": wp.name.replace("x64x", "x1x"),
+                              "n_lines": int(np.size(wp.energy_keV)), "n_iter": wp.n_iter,
+                              "ms_per_solve": round(poly_ms, 3),
+                              "projections_per_s": round(1e3 / poly_ms, 3)}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
@@ -385,7 +413,7 @@ def run_ours(a):
                       "rho_final": round(float(info["rho"][0]), 6),
                       "kappa_final": float(info["kappa"][0]),
                       "parallelism": f"replicas x{world}"},
-           "roofline": roofline, "e2e": e2e, "batched_vs_plain": bvp,
+           "roofline": roofline, "e2e": e2e, "batched_vs_plain": bvp, "other_workloads": other,
            "gpu_launches": int(launches),
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                       "reasons": clk["reasons"], "samples": clk["samples"],
