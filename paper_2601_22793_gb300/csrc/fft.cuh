@@ -35,23 +35,33 @@
 
 namespace eprfft {
 
+// Each policy also states a period P and the address step of adding a
+// multiple c of P to an index: idx(i + c) = idx(i) + step(c) for every i.  A
+// stage whose operand stride is a multiple of P computes one address and adds
+// constants.
 struct PadRow {
     __host__ __device__ static __forceinline__ int idx(int i)
     {
         return (i & ~15) | ((i & 15) ^ (((i >> 4) & 7) ^ (((i >> 6) & 1) << 3)));
     }
     __host__ __device__ static __forceinline__ int len(int n) { return (n + 15) & ~15; }
+    static constexpr int kPeriod = 128;   // the swizzle reads bits 0..6 only
+    __host__ __device__ static constexpr int step(int c) { return c; }
 };
 
 struct PadCol {
     __host__ __device__ static __forceinline__ int idx(int i) { return i + 2 * (i >> 4); }
     __host__ __device__ static __forceinline__ int len(int n) { return n + 2 * (n >> 4) + 2; }
+    static constexpr int kPeriod = 16;
+    __host__ __device__ static constexpr int step(int c) { return c + 2 * (c >> 4); }
 };
 
 // Plain dense layout (a tile written by a bulk copy).
 struct Dense {
     __host__ __device__ static __forceinline__ int idx(int i) { return i; }
     __host__ __device__ static __forceinline__ int len(int n) { return n; }
+    static constexpr int kPeriod = 1;
+    __host__ __device__ static constexpr int step(int c) { return c; }
 };
 
 // R-point DFTs in registers, sign DIR (-1 forward, +1 inverse).
@@ -273,8 +283,14 @@ __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const fl
             const int jm = j % NS;
             const int jd = j / NS;
             const int base = m * SM;
+            if constexpr ((NR * SJ) % PADI::kPeriod == 0) {
+                const int i0 = PADI::idx(j * SJ + base);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][r] = in[PADI::idx((j + r * NR) * SJ + base)];
+                for (int r = 0; r < R; ++r) v[k][r] = in[i0 + PADI::step(r * NR * SJ)];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[k][r] = in[PADI::idx((j + r * NR) * SJ + base)];
+            }
             if constexpr (NS > 1) {
                 float2 w = __ldg(&tw[jm * TWSTEP]);
                 if (DIR > 0) w.y = -w.y;
@@ -293,8 +309,14 @@ __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const fl
     for (int k = 0; k < PER; ++k) {
         if (NB % T == 0 || dst[k] >= 0) {
             dft<R, DIR>(v[k]);
+            if constexpr ((NS * SJ) % PAD::kPeriod == 0) {
+                const int o0 = PAD::idx(dst[k]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[PAD::idx(dst[k] + r * NS * SJ)] = v[k][r];
+                for (int r = 0; r < R; ++r) buf[o0 + PAD::step(r * NS * SJ)] = v[k][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[PAD::idx(dst[k] + r * NS * SJ)] = v[k][r];
+            }
         }
     }
     __syncthreads();
