@@ -40,7 +40,7 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, c
                                const float* D, const float* G, int line0, int nl, int it,
                                int batch, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* D, int batch,
-                             int check_done, cudaStream_t stream);
+                             int fixed_point, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* D, int batch,
                              cudaStream_t stream);
 cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, float* Out, int line0,
@@ -364,18 +364,18 @@ epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, cons
         EPR_TRY(epr_launch_dnorm(C, p->W, D, batch, s));
     }
     const int fwd_mode = model == EPR_MODEL_NONLOCAL ? 0 : 1;
-    // non-local: the residual D - P (and its split over the lines) is stored
-    // by the splat flush (one line, float accumulation) or by the split
-    // kernel after the overflow sources (several lines, or fixed point)
+    // the residual D - P (and its split over the lines) is stored by the
+    // splat flush (non-local, one line, float accumulation) or by the split
+    // kernel after the forward (several lines, fixed point, local closure)
     const bool nl = model == EPR_MODEL_NONLOCAL;
     const bool resid_in_splat = nl && C.ns == 1 && !C.det;
     const float eps = (float)(o->eps_I > 0 ? o->eps_I : 1e-8);
     for (int it = 0; it < o->n_iter; ++it) {
         epr_status st = launch_forward(p, T, resid_in_splat ? D : nullptr, it & 1, batch, model, 1, s);
         if (st != EPR_OK) return st;
-        if (nl && !resid_in_splat) {
+        if (!resid_in_splat) {
             ProfScope ps(p, EPR_KERNEL_OTHER, s);
-            EPR_TRY(epr_launch_split(C, p->W, D, batch, 1, s));
+            EPR_TRY(epr_launch_split(C, p->W, D, batch, nl && C.det, 1, s));
         }
         {
             ProfScope ps(p, EPR_KERNEL_ROW_FWD, s);

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
                     const float cs = line_const(C.c, s);
                     v[r0] = gather_px<DET, RESID>(C, A, pb, y, x, cs * gy, cs * gx, s);
                 } else if constexpr (MODE == FWD_SOLVE_LOCAL) {
-                    v[r0] = resid<DET, false>(C, A, pb, (size_t)y * nx + x, s);
+                    v[r0] = resid<DET, RESID>(C, A, pb, (size_t)y * nx + x, s);
                 } else {
                     v[r0] = __ldg(&A.G[pb + (size_t)y * nx + x]);
                 }
@@ -407,7 +407,7 @@ __host__ __device__ constexpr int ct_lg(int v) { return v <= 1 ? 0 : 1 + ct_lg<N
 template <int NX, int RP>
 __device__ __forceinline__ int row_of(int e) { return RP == 1 ? 0 : (int)((unsigned)e / NX); }
 
-template <int NX, int RP, bool POLY>
+template <int NX, int RP, bool POLY, bool GATHER>
 __global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
 k_row_fwd_mono(const EprConsts C, const RowArgs A)
 {
@@ -424,7 +424,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     const size_t pb = (size_t)b * npix;
     const int yb = blockIdx.x * RP * 2;
     float* Ts = reinterpret_cast<float*>(zs + ((PR::len(RP * SM) + 1) & ~1));
-    {   // T is not written by the predecessor: fetch it before the wait
+    if constexpr (GATHER) {   // T is not written by the predecessor: fetch it before the wait
         const float* Tb = A.T + pb;
         constexpr int Q4 = NX / 4;
         constexpr int NROWS = 2 * RP + 2;
@@ -461,6 +461,9 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
 #pragma unroll
         for (int r0 = 0; r0 < 2; ++r0) {
             const int y = y0 + r0;
+            if constexpr (!GATHER) {   // identity back-transport of the local closure
+                v[r0] = __ldg(Rb + (size_t)y * NX + x);
+            } else {
             const float* tr = Ts + (2 * m + r0 + 1) * NX;
             const float t = tr[x];
             float gx, gy;
@@ -491,6 +494,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
             const float top = r00 + dx * (r10 - r00);
             const float bot = r01 + dx * (r11 - r01);
             v[r0] = (1.f - dy) * top + dy * bot;
+            }
             if (!POLY || sl == 0) {
                 const float own = __ldg(Rt + (size_t)y * NX + x);
                 ra += own * own;
@@ -732,7 +736,7 @@ size_t row_inv_poly_smem(int nx, int rp)
 }
 
 // launch a specialised mono kernel when nx has one; returns false otherwise
-template <bool FWD>
+template <bool FWD, bool GATHER = true>
 bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream, const EprConsts& C,
                     const RowArgs& A, cudaError_t& err)
 {
@@ -743,11 +747,11 @@ bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream,
     if (nx == NXV && rp == RPV) {                                                            \
         const dim3 blk(NXV * RPV / kEPT);                                                    \
         if (FWD && !poly) {                                                                  \
-            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, false>, grid, blk,   \
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, false, GATHER>, grid, blk, \
                                     smem, stream, C, A);                                     \
         } else if (FWD) {                                                                    \
             const dim3 g3(grid.x, grid.y, A.nl);                                             \
-            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, true>, g3, blk, smem, \
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, true, GATHER>, g3, blk, smem, \
                                     stream, C, A);                                           \
         } else if (!poly) {                                                                  \
             err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<NXV, RPV>, grid, blk, smem,    \
@@ -776,8 +780,10 @@ cudaError_t init_mono_ct()
 {
     cudaError_t e = cudaSuccess;
 #define EPR_MONO_INIT(NXV, RPV)                                                  \
-    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, false>);             \
-    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, true>);              \
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, false, true>);       \
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, true, true>);        \
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, false, false>);      \
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, true, false>);       \
     if (e == cudaSuccess) e = allow(k_row_inv_mono<NXV, RPV>);                    \
     if (e == cudaSuccess) e = allow(k_row_inv_poly<NXV, RPV>);
     EPR_MONO_INIT(256, 8)
@@ -840,8 +846,9 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, c
             else go(k_row_fwd<FWD_SOLVE_NL, false, true, 0>);
         }
     } else if (mode == FWD_SOLVE_LOCAL) {
-        // the local closure writes float maps in both accumulation modes
-        go(k_row_fwd<FWD_SOLVE_LOCAL, false, false, 0>);
+        // identity back-transport: the split residuals at the pixel itself
+        if (!launch_mono_ct<true, false>(C.nx, L.RP, grid, L.smem, stream, C, A, e))
+            go(k_row_fwd<FWD_SOLVE_LOCAL, false, true, 0>);
     } else {
         go(k_row_fwd<FWD_LOAD, false, false, 1>);
     }
@@ -893,7 +900,7 @@ cudaError_t epr_row_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, false, true, 1>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, false, false, 1>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, false, false, 0>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_LOCAL, false, false, 0>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_LOCAL, false, true, 0>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_LOAD, false, false, 1>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 1>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 0>);

@@ -469,9 +469,11 @@ cudaError_t epr_splat_init()
     return e;
 }
 
-// Residual split after the splat of a polychromatic (or fixed-point) solve.
+// Residual split after the forward of a solve: fixed_point = 1 reads the
+// integer sums of the fixed-point splat, 0 the float maps (float splat,
+// local closure).
 cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* D, int batch,
-                             int check_done, cudaStream_t stream)
+                             int fixed_point, int check_done, cudaStream_t stream)
 {
     SplatArgs A = {};
     A.D = D;
@@ -486,8 +488,8 @@ cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* 
     if (blocks > 1216) blocks = 1216;   // 8 per SM on 152 SMs, grid-stride beyond
     const dim3 grid((unsigned)blocks, batch);
     const cudaError_t e =
-        C.det ? epr_launch_kernel(C.pdl != 0, k_split<true>, grid, dim3(256), 0, stream, C, A)
-              : epr_launch_kernel(C.pdl != 0, k_split<false>, grid, dim3(256), 0, stream, C, A);
+        fixed_point ? epr_launch_kernel(C.pdl != 0, k_split<true>, grid, dim3(256), 0, stream, C, A)
+                    : epr_launch_kernel(C.pdl != 0, k_split<false>, grid, dim3(256), 0, stream, C, A);
     epr_count_launch(1);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
