@@ -33,31 +33,48 @@ struct LocalArgs {
     int check_done;
 };
 
-__device__ __forceinline__ float dX(const float* F, int l, int gx, int nx)
+// Derivative stencils of a field given as a function of the staged index
+// (a shared array, or a product of shared arrays formed on the fly).
+template <class F>
+__device__ __forceinline__ float dX(F f, int l, int gx, int nx)
 {
-    if (gx == 0) return F[l + 1] - F[l];
-    if (gx == nx - 1) return F[l] - F[l - 1];
-    return 0.5f * (F[l + 1] - F[l - 1]);
+    if (gx == 0) return f(l + 1) - f(l);
+    if (gx == nx - 1) return f(l) - f(l - 1);
+    return 0.5f * (f(l + 1) - f(l - 1));
 }
-__device__ __forceinline__ float dY(const float* F, int l, int gy, int ny)
+template <class F>
+__device__ __forceinline__ float dY(F f, int l, int gy, int ny)
 {
-    if (gy == 0) return F[l + kLE] - F[l];
-    if (gy == ny - 1) return F[l] - F[l - kLE];
-    return 0.5f * (F[l + kLE] - F[l - kLE]);
+    if (gy == 0) return f(l + kLE) - f(l);
+    if (gy == ny - 1) return f(l) - f(l - kLE);
+    return 0.5f * (f(l + kLE) - f(l - kLE));
 }
-__device__ __forceinline__ float dXX(const float* F, int l, int gx, int nx)
+template <class F>
+__device__ __forceinline__ float dXX(F f, int l, int gx, int nx)
 {
-    const float lo = gx == 0 ? F[l] : F[l - 1];
-    const float hi = gx == nx - 1 ? F[l] : F[l + 1];
-    return lo - 2.f * F[l] + hi;
+    const float lo = gx == 0 ? f(l) : f(l - 1);
+    const float hi = gx == nx - 1 ? f(l) : f(l + 1);
+    return lo - 2.f * f(l) + hi;
 }
-__device__ __forceinline__ float dYY(const float* F, int l, int gy, int ny)
+template <class F>
+__device__ __forceinline__ float dYY(F f, int l, int gy, int ny)
 {
-    const float lo = gy == 0 ? F[l] : F[l - kLE];
-    const float hi = gy == ny - 1 ? F[l] : F[l + kLE];
-    return lo - 2.f * F[l] + hi;
+    const float lo = gy == 0 ? f(l) : f(l - kLE);
+    const float hi = gy == ny - 1 ? f(l) : f(l + kLE);
+    return lo - 2.f * f(l) + hi;
 }
 
+struct Arr {
+    const float* a;
+    __device__ __forceinline__ float operator()(int l) const { return a[l]; }
+};
+
+// Shared fields: T, G_x, G_y, I (order 1); also sqrt(I), Q, D_y(I u_x u_y),
+// I D_x Q, I D_y Q (order 2).  The fluxes I u and I u u are formed inside the
+// stencils from I and G.
+constexpr int local_fields(int order) { return order >= 2 ? 9 : 4; }
+
+template <int ORDER>
 __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, const LocalArgs A)
 {
     extern __shared__ __align__(16) float sm[];
@@ -65,13 +82,8 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, cons
     float* GX = Ts + kLN;
     float* GY = GX + kLN;
     float* I = GY + kLN;
-    float* SQ = I + kLN;
-    float* AX = SQ + kLN;
-    float* AY = AX + kLN;
-    float* BXY = AY + kLN;
-    float* BXX = BXY + kLN;
-    float* BYY = BXX + kLN;
-    float* Q = BYY + kLN;
+    float* SQ = I + kLN;      // order 2 only, as the four below
+    float* Q = SQ + kLN;
     float* DYB = Q + kLN;
     float* CXQ = DYB + kLN;
     float* CYQ = CXQ + kLN;
@@ -96,8 +108,8 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, cons
     for (int i = tid; i < kLN; i += kLocalThreads) {
         const int ly = i / kLE, lx = i - ly * kLE;
         if (ly < 1 || ly >= kLE - 1 || lx < 1 || lx >= kLE - 1) continue;
-        GX[i] = dX(Ts, i, gx0 + lx, nx);
-        GY[i] = dY(Ts, i, gy0 + ly, ny);
+        GX[i] = dX(Arr{Ts}, i, gx0 + lx, nx);
+        GY[i] = dY(Arr{Ts}, i, gy0 + ly, ny);
     }
     __syncthreads();
 
@@ -106,37 +118,36 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, cons
     for (int k = 0; k < kLT * kLT / kLocalThreads; ++k) pacc[k] = 0.f;
 
     for (int s = 0; s < ns; ++s) {
-        const float fs = C.f[s], mus = C.mu[s], cs = C.c[s], qc = C.qc[s];
+        const float fs = line_const(C.f, s), mus = line_const(C.mu, s);
+        const float cs = line_const(C.c, s), qc = line_const(C.qc, s);
+        // fluxes I u_x, I u_y and I u_i u_j at staged index j
+        auto AX = [&](int j) { return I[j] * (cs * GX[j]); };
+        auto AY = [&](int j) { return I[j] * (cs * GY[j]); };
+        auto BXX = [&](int j) { const float ux = cs * GX[j]; return I[j] * ux * ux; };
+        auto BYY = [&](int j) { const float uy = cs * GY[j]; return I[j] * uy * uy; };
+        auto BXY = [&](int j) { return I[j] * (cs * GX[j]) * (cs * GY[j]); };
         for (int i = tid; i < kLN; i += kLocalThreads) {
             const float v = fs * __expf(-mus * Ts[i]);
             I[i] = v;
-            SQ[i] = sqrtf(v);
+            if constexpr (ORDER >= 2) SQ[i] = sqrtf(v);
         }
         __syncthreads();
-        for (int i = tid; i < kLN; i += kLocalThreads) {
-            const int ly = i / kLE, lx = i - ly * kLE;
-            if (ly < 1 || ly >= kLE - 1 || lx < 1 || lx >= kLE - 1) continue;
-            const float ux = cs * GX[i], uy = cs * GY[i], Iv = I[i];
-            AX[i] = Iv * ux;
-            AY[i] = Iv * uy;
-            if (A.order >= 2) {
-                BXY[i] = Iv * ux * uy;
-                BXX[i] = Iv * ux * ux;
-                BYY[i] = Iv * uy * uy;
+        if constexpr (ORDER >= 2) {
+            for (int i = tid; i < kLN; i += kLocalThreads) {   // 1-pixel halo
+                const int ly = i / kLE, lx = i - ly * kLE;
+                if (ly < 1 || ly >= kLE - 1 || lx < 1 || lx >= kLE - 1) continue;
                 const float sq = SQ[i];
-                const float lap = dXX(SQ, i, gx0 + lx, nx) + dYY(SQ, i, gy0 + ly, ny);
+                const float lap = dXX(Arr{SQ}, i, gx0 + lx, nx) + dYY(Arr{SQ}, i, gy0 + ly, ny);
                 Q[i] = sq > 0.f ? lap / sq : 0.f;
             }
-        }
-        __syncthreads();
-        if (A.order >= 2) {
-            for (int i = tid; i < kLN; i += kLocalThreads) {
+            __syncthreads();
+            for (int i = tid; i < kLN; i += kLocalThreads) {   // 2-pixel halo
                 const int ly = i / kLE, lx = i - ly * kLE;
                 if (ly < 2 || ly >= kLE - 2 || lx < 2 || lx >= kLE - 2) continue;
                 const int gx = gx0 + lx, gy = gy0 + ly;
                 DYB[i] = dY(BXY, i, gy, ny);
-                CXQ[i] = I[i] * dX(Q, i, gx, nx);
-                CYQ[i] = I[i] * dY(Q, i, gy, ny);
+                CXQ[i] = I[i] * dX(Arr{Q}, i, gx, nx);
+                CYQ[i] = I[i] * dY(Arr{Q}, i, gy, ny);
             }
             __syncthreads();
         }
@@ -148,9 +159,9 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, cons
             if (gy >= ny || gx >= nx) continue;
             const int i = (oy + kLH) * kLE + (ox + kLH);
             float p = I[i] - dX(AX, i, gx, nx) - dY(AY, i, gy, ny);
-            if (A.order >= 2) {
-                p += 0.5f * (dXX(BXX, i, gx, nx) + dYY(BYY, i, gy, ny)) + dX(DYB, i, gx, nx);
-                p -= qc * (dX(CXQ, i, gx, nx) + dY(CYQ, i, gy, ny));
+            if constexpr (ORDER >= 2) {
+                p += 0.5f * (dXX(BXX, i, gx, nx) + dYY(BYY, i, gy, ny)) + dX(Arr{DYB}, i, gx, nx);
+                p -= qc * (dX(Arr{CXQ}, i, gx, nx) + dY(Arr{CYQ}, i, gy, ny));
             }
             pacc[k] += p;
             if (A.Ps) A.Ps[((size_t)b * ns + s) * npix + (size_t)gy * nx + gx] = p;
@@ -169,7 +180,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, cons
 
 }  // namespace
 
-size_t epr_local_smem() { return (size_t)14 * kLN * sizeof(float); }
+size_t epr_local_smem(int order) { return (size_t)local_fields(order) * kLN * sizeof(float); }
 
 cudaError_t epr_launch_local(const EprConsts& C, const EprWork& W, const float* T, float* P,
                              float* Ps, int order, int batch, int check_done, cudaStream_t stream)
@@ -182,10 +193,17 @@ cudaError_t epr_launch_local(const EprConsts& C, const EprWork& W, const float* 
     A.order = order;
     A.check_done = check_done;
     dim3 grid((C.nx + kLT - 1) / kLT, (C.ny + kLT - 1) / kLT, batch);
-    const cudaError_t e = epr_launch_kernel(C.pdl != 0, k_local, grid, dim3(kLocalThreads),
-                                            epr_local_smem(), stream, C, A);
+    const cudaError_t e =
+        order >= 2 ? epr_launch_kernel(C.pdl != 0, k_local<2>, grid, dim3(kLocalThreads),
+                                       epr_local_smem(2), stream, C, A)
+                   : epr_launch_kernel(C.pdl != 0, k_local<1>, grid, dim3(kLocalThreads),
+                                       epr_local_smem(1), stream, C, A);
     epr_count_launch(1);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t epr_local_init() { return epr_allow_max_smem(k_local); }
+cudaError_t epr_local_init()
+{
+    cudaError_t e = epr_allow_max_smem(k_local<1>);
+    return e != cudaSuccess ? e : epr_allow_max_smem(k_local<2>);
+}
