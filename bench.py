@@ -396,7 +396,15 @@ def run_ours(a):
     Dp = torch.from_numpy(ph.poisson(Pp.cpu().numpy(), wp.photons, 9).astype(np.float32)).cuda()
     poly_ms = timeit(lambda: epr.epr_solve_nonlocal(pplan.handle, Dp, Tp, n_iter=wp.n_iter,
                                                     omega=wp.omega, want_info=False), reps=3)
+    # vector-Jacobian product of the 8-line forward (the calibration backward)
+    gbar = torch.randn(wp.ny, wp.nx, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    Tbar = torch.empty_like(Tp)
+    nlp = int(np.size(wp.energy_keV))
+    fwd_ms = timeit(lambda: epr.epr_forward(pplan.handle, Tp, Pp))
+    vjp_ms = timeit(lambda: epr.epr_vjp(pplan.handle, Tp, gbar, Tbar, nlp, scalars=False))
     pplan.close()
+    other["vjp_polychromatic"] = {"workload": "ellipsoids_poly_2048 forward + VJP, 8 lines, 1 map",
+                                  "forward_ms": round(fwd_ms, 3), "vjp_ms": round(vjp_ms, 3)}
     other["polychromatic"] = {"workload": wp.name.replace("x64x", "x1x"),
                               "n_lines": int(np.size(wp.energy_keV)), "n_iter": wp.n_iter,
                               "ms_per_solve": round(poly_ms, 3),
