@@ -245,17 +245,31 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
     }
 }
 
-// ln(I'_s / (f_s exp(-mu_s t))) for the update of one pixel and line
-__device__ __forceinline__ float log_ratio(float t, float h, float fs, float mus, float omega,
-                                           float eps)
+// ln(1 + q) for |q| < 1/4 from ln(1 + q) = 2 atanh(z), z = q / (2 + q), and
+// the Taylor series of atanh: 2 z (1 + z^2/3 + z^4/5 + ... + z^10/11).  Here
+// |z| < 1/7, so the first omitted term, 2 |z|^13 / 13, is below 4e-12 |z|:
+// the error is the rounding of the few operations.
+__device__ __forceinline__ float log1p_atanh(float q)
 {
-    const float E = __expf(-mus * t);          // I_s / f_s
-    const float add = omega * h / fs;          // omega h_s / f_s
-    const float v = E + add;                   // I'_s / f_s before the floor
-    if (v >= eps) {
-        const float q = add / E;
-        return (fabsf(q) < 0.5f) ? log1pf(q) : (logf(v) + mus * t);
-    }
+    const float z = __fdividef(q, 2.f + q);
+    const float w = z * z;
+    float p = fmaf(w, 1.f / 11.f, 1.f / 9.f);
+    p = fmaf(w, p, 1.f / 7.f);
+    p = fmaf(w, p, 1.f / 5.f);
+    p = fmaf(w, p, 1.f / 3.f);
+    p = fmaf(w, p, 1.f);
+    return 2.f * z * p;
+}
+
+// ln(I'_s / I_s) for the update of one pixel and line, I_s = f_s exp(-mu_s t),
+// I'_s = max(I_s + omega h_s, eps f_s).  With q = (omega / f_s) h_s exp(mu_s t)
+// = omega h_s / I_s, the ratio is 1 + q above the floor, and
+// eps f_s / I_s = eps exp(mu_s t) at it.  om_f = omega / f_s.
+__device__ __forceinline__ float log_ratio(float t, float h, float om_f, float mus, float eps)
+{
+    const float Einv = __expf(mus * t);        // f_s / I_s
+    const float q = om_f * h * Einv;
+    if (1.f + q >= eps * Einv) return (fabsf(q) < 0.25f) ? log1p_atanh(q) : logf(1.f + q);
     return logf(eps) + mus * t;
 }
 
@@ -309,10 +323,10 @@ __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const Row
             const size_t q0 = pb + (size_t)(yb + 2 * m) * nx + x;
             if constexpr (MODE == INV_UPDATE) {
                 const float fs = line_const(C.f, s), mus = line_const(C.mu, s),
-                            w = line_const(C.wproj, s);
+                            w = line_const(C.wproj, s), om_f = A.omega / fs;
                 const float t0 = A.Out[q0], t1 = A.Out[q0 + nx];
-                const float l0 = w * log_ratio(t0, h.x, fs, mus, A.omega, A.eps);
-                const float l1 = w * log_ratio(t1, h.y, fs, mus, A.omega, A.eps);
+                const float l0 = w * log_ratio(t0, h.x, om_f, mus, A.eps);
+                const float l1 = w * log_ratio(t1, h.y, om_f, mus, A.eps);
                 if (nl == 1) {
                     const float n0 = t0 - l0, n1 = t1 - l1;
                     A.Out[q0] = n0;
@@ -594,7 +608,7 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
     epr_grid_release();
     cp_async_wait_all();
     __syncthreads();
-    const float fs = C.f[0], mus = C.mu[0], w = C.wproj[0];
+    const float mus = C.mu[0], w = C.wproj[0], om_f = A.omega / C.f[0];
     float da = 0.f, db = 0.f;
 #pragma unroll 2
     for (int k = 0; k < kEPT; ++k) {
@@ -603,8 +617,8 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
         const float2 h = zs[PR::idx(m * SM + x)];
         const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
         const float t0 = Tsh[(2 * m) * NX + x], t1 = Tsh[(2 * m + 1) * NX + x];
-        const float l0 = w * log_ratio(t0, h.x, fs, mus, A.omega, A.eps);
-        const float l1 = w * log_ratio(t1, h.y, fs, mus, A.omega, A.eps);
+        const float l0 = w * log_ratio(t0, h.x, om_f, mus, A.eps);
+        const float l1 = w * log_ratio(t1, h.y, om_f, mus, A.eps);
         const float n0 = t0 - l0, n1 = t1 - l1;
         A.Out[q0] = n0;
         A.Out[q0 + NX] = n1;
@@ -686,15 +700,16 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
             cp_async_wait_all();
             __syncthreads();
         }
-        const float fs = line_const(C.f, s), mus = line_const(C.mu, s), w = line_const(C.wproj, s);
+        const float mus = line_const(C.mu, s), w = line_const(C.wproj, s);
+        const float om_f = A.omega / line_const(C.f, s);
 #pragma unroll 2
         for (int k = 0; k < kEPT; ++k) {
             const int e = tid + k * T;
             const int m = row_of<NX, RP>(e), x = e - m * NX;
             const float2 h = zs[PR::idx(m * SM + x)];
             const int i0 = (2 * m) * NX + x;
-            const float l0 = w * log_ratio(Tsh[i0], h.x, fs, mus, A.omega, A.eps);
-            const float l1 = w * log_ratio(Tsh[i0 + NX], h.y, fs, mus, A.omega, A.eps);
+            const float l0 = w * log_ratio(Tsh[i0], h.x, om_f, mus, A.eps);
+            const float l1 = w * log_ratio(Tsh[i0 + NX], h.y, om_f, mus, A.eps);
             acc[i0] = sl == 0 ? l0 : acc[i0] + l0;
             acc[i0 + NX] = sl == 0 ? l1 : acc[i0 + NX] + l1;
         }
