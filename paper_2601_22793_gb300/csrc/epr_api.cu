@@ -31,11 +31,6 @@ cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* 
                              cudaStream_t stream);
 size_t epr_splat_smem(const EprConsts& C, int TH, int TW);
 cudaError_t epr_splat_init();
-struct EprRowLaunch {
-    int RP, lgRP, threads;
-    size_t smem;
-};
-EprRowLaunch epr_row_config(const EprConsts& C);
 cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
                                const float* D, const float* G, int line0, int nl, int it,
                                int batch, int check_done, cudaStream_t stream);
