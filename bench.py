@@ -405,6 +405,33 @@ def run_ours(a):
     pplan.close()
     other["vjp_polychromatic"] = {"workload": "ellipsoids_poly_2048 forward + VJP, 8 lines, 1 map",
                                   "forward_ms": round(fwd_ms, 3), "vjp_ms": round(vjp_ms, 3)}
+    # uneven batch: projections of four detector sizes, 4 lines, each solved until
+    # kappa <= 1e-4 or 50 iterations, in one batched call
+    shapes = [(1024, 1024), (2048, 1536), (2048, 2048), (3072, 2048)] * 2   # (nx, ny)
+    E4, d4, b4, w4 = ph.spectrum(4, 60.0, 160.0, 95.0, 30.0, ph.BONE[0], ph.BONE[1], 80.0, 4000)
+    bh = epr.epr_batch_create(wp.pixel, wp.L, E4, d4, b4, w4)
+    Du, Tu = [], []
+    for k, (nxu, nyu) in enumerate(shapes):
+        ells_u = ph.random_ellipsoids(nyu, nxu, 60, 8.0, 120.0, seed=4000 + k)
+        tu = torch.from_numpy(ph.project_ellipsoids(ells_u, nyu, nxu, wp.pixel).astype(np.float32)).cuda()
+        with epr.Plan(nxu, nyu, wp.pixel, wp.L, E4, d4, b4, w4) as fp:
+            pu = torch.empty_like(tu)
+            epr.epr_forward(fp.handle, tu, pu)
+        Du.append(torch.from_numpy(ph.poisson(pu.cpu().numpy(), wp.photons, 70 + k).astype(np.float32)).cuda())
+        Tu.append(torch.empty_like(tu))
+    uinfo = {}
+
+    def uneven():
+        uinfo.update(epr.epr_solve_nonlocal_batched(bh, Du, Tu, n_iter=50, omega=0.4, tol=1e-4))
+
+    uneven_ms = timeit(uneven, reps=3)
+    epr.epr_batch_destroy(bh)
+    eq = sum(nxu * nyu for nxu, nyu in shapes) / REF_PIX
+    other["batched_uneven"] = {"projections": len(shapes), "sizes_nx_ny": sorted(set(shapes)),
+                               "n_lines": 4, "tol_kappa": 1e-4, "max_iter": 50,
+                               "iters": [int(v) for v in uinfo["iters"]],
+                               "ms_per_call": round(uneven_ms, 3),
+                               "equiv_2048sq_projections_per_s": round(eq / (uneven_ms * 1e-3), 3)}
     other["polychromatic"] = {"workload": wp.name.replace("x64x", "x1x"),
                               "n_lines": int(np.size(wp.energy_keV)), "n_iter": wp.n_iter,
                               "ms_per_solve": round(poly_ms, 3),
