@@ -154,10 +154,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the library sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+def _traffic(kernel: str, table: str = "dram_traffic.txt"):
+    """Per-launch figure of `kernel` from a committed ncu table (DRAM bytes,
+    or warp instructions), or None when the library sources changed since
+    that capture."""
+    path = os.path.join(ROOT, "profiles", table)
     if not os.path.exists(path):
         return None
     from paper_2601_22793_gb300 import build as B
@@ -305,6 +306,24 @@ def run_ours(a):
                               "gbs": round(iter_bytes / (iter_us * 1e-6) / 1e9, 1),
                               "frac": round(iter_bytes / (iter_us * 1e-6) / 1e9 / peak, 4)},
                 "kernels": per_kernel}
+    # the bound the kernels actually meet: instruction issue (4 warp instructions
+    # per clock per SM), with the instructions ncu counted per launch
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    issue_peak = nsm * 4 * clk["sm_mhz"] * 1e6 / 1e9 if clk["sm_mhz"] else None
+    issue = {}
+    for kname, v in per_kernel.items():
+        ninst = _traffic(kname, "instructions.txt")
+        if ninst is None or not issue_peak:
+            issue[kname] = None
+            continue
+        ach = ninst / (v["avg_us"] * 1e-6) / 1e9
+        issue[kname] = {"warp_inst_per_launch": int(ninst), "achieved_ginst_s": round(ach, 1),
+                        "frac": round(ach / issue_peak, 4)}
+    roofline["issue"] = {"peak_ginst_s": round(issue_peak, 1) if issue_peak else None,
+                         "peak_source": f"{nsm} SMs x 4 schedulers x sampled SM clock",
+                         "kernels": issue,
+                         "note": "informational: the measured bound of these kernels is "
+                                 "instruction issue and load latency, not HBM"}
 
     # end to end through the C ABI with pinned host buffers
     Dh = torch.from_numpy(D_host).pin_memory()
