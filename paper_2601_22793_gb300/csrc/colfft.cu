@@ -166,7 +166,7 @@ k_col_ct(const EprConsts C, const ColArgs A)
 constexpr unsigned int kTmaWaitPolls = 1u << 22;
 
 template <int NY, int CW, int EPT>
-__global__ void __launch_bounds__(NY * CW / EPT, (65536 / 64) / (NY * CW / EPT))
+__global__ void __launch_bounds__(NY * CW / EPT, NY * CW / EPT == 512 ? 3 : (65536 / 64) / (NY * CW / EPT))
 k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMap map)
 {
     constexpr int T = NY * CW / EPT;
