@@ -555,8 +555,10 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     }
 }
 
+// five 256-thread blocks per SM (51 registers): its shared memory is the FFT
+// rows and 2 RP thickness rows only (row_inv_mono_smem)
 template <int NX, int RP>
-__global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
+__global__ void __launch_bounds__(NX * RP / kEPT, NX * RP / kEPT == 256 ? 5 : (65536 / 64) / (NX * RP / kEPT))
 k_row_inv_mono(const EprConsts C, const RowArgs A)
 {
     constexpr int T = NX * RP / kEPT;
@@ -743,6 +745,13 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
     }
 }
 
+// dynamic shared memory of k_row_inv_mono: FFT rows, T rows
+size_t row_inv_mono_smem(int nx, int rp)
+{
+    return (size_t)((PR::len(rp * (nx + kPad)) + 1) & ~1) * sizeof(float2) +
+           (size_t)(2 * rp * nx) * sizeof(float);
+}
+
 // dynamic shared memory of k_row_inv_poly: FFT rows, T rows, accumulators
 size_t row_inv_poly_smem(int nx, int rp)
 {
@@ -769,8 +778,8 @@ bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream,
             err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, true, GATHER>, g3, blk, smem, \
                                     stream, C, A);                                           \
         } else if (!poly) {                                                                  \
-            err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<NXV, RPV>, grid, blk, smem,    \
-                                    stream, C, A);                                           \
+            err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<NXV, RPV>, grid, blk,          \
+                                    row_inv_mono_smem(NXV, RPV), stream, C, A);              \
         } else {                                                                             \
             err = epr_launch_kernel(C.pdl != 0, k_row_inv_poly<NXV, RPV>, grid, blk,          \
                                     row_inv_poly_smem(NXV, RPV), stream, C, A);              \
