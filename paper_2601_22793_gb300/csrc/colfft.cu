@@ -264,8 +264,8 @@ static size_t col_tma_smem(const EprConsts& C, const EprColLaunch& L)
 
 // Tensor map of S seen as `rows` rows of nx floats, with [ny or 256][2 CW]
 // boxes, for the bulk-copy column pass.  Returns false (and leaves the plain
-// pass in use) when the size has no such pass or the driver offers no
-// encoder.
+// pass in use) when the size has no such pass or the CUDA driver API entry
+// point cuTensorMapEncodeTiled is not available.
 bool epr_col_make_map(const EprConsts& C, const float2* S, long long rows, CUtensorMap* out)
 {
     const EprColLaunch L = epr_col_config(C, 0);
