@@ -183,12 +183,14 @@ def kernel_bytes_per_px(ns: int) -> dict:
                   row_fwd reads T and the residual, writes the packed half
                   spectrum (4 B/px); col reads + writes the spectrum;
                   row_inv reads the spectrum and T, writes T'.
-    n_s lines:    splat reads T, writes P and P_s; row_fwd reads T, D, P, P_s,
-                  writes n_s spectra; col 8 B/px/line; row_inv reads n_s
-                  spectra and T, writes T'."""
+    n_s lines:    splat reads T, writes P and P_s; the split kernel reads D, P,
+                  P_s and writes D - P and r_s; row_fwd reads T and r_s, writes
+                  n_s spectra; col 8 B/px/line; row_inv reads n_s spectra and
+                  T, writes T'."""
     if ns == 1:
         return {"splat": 12, "row_fwd": 12, "col": 8, "row_inv": 12}
-    return {"splat": 8 + 4 * ns, "row_fwd": 12 + 8 * ns, "col": 8 * ns, "row_inv": 8 + 4 * ns}
+    return {"splat": 8 + 4 * ns, "split": 12 + 8 * ns, "row_fwd": 4 + 8 * ns, "col": 8 * ns,
+            "row_inv": 8 + 4 * ns}
 
 
 # --------------------------------------------------------------------------
