@@ -33,6 +33,14 @@
  *   R9  mu_s = 2 k_s beta_s, k_s = 2 pi / lambda_s, lambda_s = hc / E_s.
  *   R10 local stencils: D_i central (one-sided at edges), D_ii the compact
  *       [1, -2, 1] with replicated edges, D_ij = D_i D_j for i != j.
+ *   R11 oversampled internal grid ("Results": solves on grids whose pixel is
+ *       the detector pixel divided by o): the thickness and the forward model
+ *       live on the fine grid (o ny) x (o nx) with pixel p / o; the model's
+ *       detector image is the mean of each o x o block of the fine P; the
+ *       residual D - mean(P) is formed at detector resolution and replicated
+ *       to the o x o fine pixels of its block before the split, the
+ *       back-transport, the preconditioner (fine grid) and the update.
+ *       o = 1 is the plain solve.
  *
  * Parity unpinned: the residual split of R5.  The paper only says the
  * weights are "positivity-weighted"; P_s / P and f_s agree at the flat-field
@@ -666,13 +674,20 @@ int orc_vjp(int ny, int nx, double p, double L, int n_lines, const double* E_keV
  * T holds the initial thickness on entry (zeros = start from flat field) and
  * the result on return.  rho and kappa (n_iter values each, may be NULL)
  * receive the history; *iters the number of iterations run. */
-int orc_solve(int ny, int nx, double p, double L, int n_lines,
-              const double* E_keV, const double* delta, const double* beta,
-              const double* weights, int model, const double* D, double* T,
-              int n_iter, double omega, double tol, double eps_I, double* rho,
-              double* kappa, int* iters)
+/* The solver of "Iteration structure" on a grid oversampled by os (R11):
+ * ny, nx and p are the FINE grid's; D is [ny/os][nx/os] at detector
+ * resolution; os = 1 is the plain solve. */
+static int solve_impl(int ny, int nx, int os, double p, double L, int n_lines,
+                      const double* E_keV, const double* delta, const double* beta,
+                      const double* weights, int model, const double* D, double* T,
+                      int n_iter, double omega, double tol, double eps_I, double* rho,
+                      double* kappa, int* iters)
 {
-    if (ny < 2 || nx < 2 || model < 0 || model > 2 || n_iter < 0) return ORC_EINVAL;
+    if (ny < 2 || nx < 2 || model < 0 || model > 2 || n_iter < 0 || os < 1 ||
+        ny % os != 0 || nx % os != 0)
+        return ORC_EINVAL;
+    const int nyd = ny / os, nxd = nx / os;
+    const size_t nd = (size_t)nxd * (size_t)nyd;
     orc_lines ln;
     int st = lines_init(&ln, n_lines, E_keV, delta, beta, weights, L, p);
     size_t n = (size_t)nx * (size_t)ny;
@@ -689,19 +704,27 @@ int orc_solve(int ny, int nx, double p, double L, int n_lines,
         for (int s = 0; s < ns; ++s) den += ln.f[s] * ln.mu[s] * ln.mu[s];
     if (st == ORC_OK && !(den > 0.0)) st = ORC_EINVAL;
     double dnorm = 0.0;
-    for (size_t i = 0; st == ORC_OK && i < n; ++i) dnorm += D[i] * D[i];
+    for (size_t i = 0; st == ORC_OK && i < nd; ++i) dnorm += D[i] * D[i];
     dnorm = sqrt(dnorm);
     int it = 0;
     for (; st == ORC_OK && it < n_iter; ++it) {
         /* 1. forward */
         st = forward_impl(ny, nx, &ln, model, T, P, Ps, NULL, gy, gx, uy, ux, I, Pl);
         if (st != ORC_OK) break;
-        /* 2. residual */
+        /* 2. residual at detector resolution (the mean of each os x os block
+         * of the fine model), replicated to the fine pixels of its block */
         double rr = 0.0;
-        for (size_t i = 0; i < n; ++i) {
-            r[i] = D[i] - P[i];
-            rr += r[i] * r[i];
-        }
+        for (int yd = 0; yd < nyd; ++yd)
+            for (int xd = 0; xd < nxd; ++xd) {
+                double m = 0.0;
+                for (int a = 0; a < os; ++a)
+                    for (int b = 0; b < os; ++b) m += P[IDX(yd * os + a, xd * os + b)];
+                m /= (double)os * (double)os;
+                const double rd = D[(size_t)yd * nxd + xd] - m;
+                rr += rd * rd;
+                for (int a = 0; a < os; ++a)
+                    for (int b = 0; b < os; ++b) r[IDX(yd * os + a, xd * os + b)] = rd;
+            }
         if (rho) rho[it] = dnorm > 0.0 ? sqrt(rr) / dnorm : sqrt(rr);
         for (size_t i = 0; i < n; ++i) num[i] = 0.0;
         for (int s = 0; s < ns; ++s) {
@@ -753,4 +776,40 @@ int orc_solve(int ny, int nx, double p, double L, int n_lines,
     free(r); free(rs); free(g); free(num); free(Ps);
     lines_free(&ln);
     return st;
+}
+
+int orc_solve(int ny, int nx, double p, double L, int n_lines,
+              const double* E_keV, const double* delta, const double* beta,
+              const double* weights, int model, const double* D, double* T,
+              int n_iter, double omega, double tol, double eps_I, double* rho,
+              double* kappa, int* iters)
+{
+    return solve_impl(ny, nx, 1, p, L, n_lines, E_keV, delta, beta, weights, model, D, T,
+                      n_iter, omega, tol, eps_I, rho, kappa, iters);
+}
+
+/* The solve on a grid oversampled by os (R11): D is the detector image
+ * [nyd][nxd] with pixel p_det; T is the fine thickness [os nyd][os nxd]. */
+int orc_solve_os(int nyd, int nxd, int os, double p_det, double L, int n_lines,
+                 const double* E_keV, const double* delta, const double* beta,
+                 const double* weights, int model, const double* D, double* T,
+                 int n_iter, double omega, double tol, double eps_I, double* rho,
+                 double* kappa, int* iters)
+{
+    if (os < 1 || !(p_det > 0.0)) return ORC_EINVAL;
+    return solve_impl(nyd * os, nxd * os, os, p_det / os, L, n_lines, E_keV, delta, beta,
+                      weights, model, D, T, n_iter, omega, tol, eps_I, rho, kappa, iters);
+}
+
+/* Detector image of a fine map: the mean of each os x os block (R11). */
+void orc_bin(int nyd, int nxd, int os, const double* fine, double* det)
+{
+    const int nx = nxd * os;
+    for (int yd = 0; yd < nyd; ++yd)
+        for (int xd = 0; xd < nxd; ++xd) {
+            double m = 0.0;
+            for (int a = 0; a < os; ++a)
+                for (int b = 0; b < os; ++b) m += fine[IDX(yd * os + a, xd * os + b)];
+            det[(size_t)yd * nxd + xd] = m / ((double)os * (double)os);
+        }
 }

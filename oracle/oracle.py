@@ -69,6 +69,10 @@ def _load():
             lib.orc_vjp.argtypes = [i, i, f, f, i, d, d, d, d, d, d, d, d, d, d]
             lib.orc_solve.argtypes = [i, i, f, f, i, d, d, d, d, i, d, d, i, f, f, f,
                                       d, d, ip]
+            lib.orc_solve_os.argtypes = [i, i, i, f, f, i, d, d, d, d, i, d, d, i, f, f, f,
+                                         d, d, ip]
+            lib.orc_bin.argtypes = [i, i, i, d, d]
+            lib.orc_bin.restype = None
             _lib = lib
     return _lib
 
@@ -227,5 +231,32 @@ def solve(lines: Lines, D, T0=None, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8,
                            int(n_iter), float(omega), float(tol), float(eps_I),
                            _p(rho), _p(kappa), ctypes.byref(iters))
     _check(st, "solve")
+    k = iters.value
+    return T, {"rho": rho[:k], "kappa": kappa[:k], "iters": k}
+
+
+def bin_mean(fine, os_):
+    """Detector image of a fine map: the mean of each os x os block."""
+    fine = _c(fine)
+    nyd, nxd = fine.shape[0] // os_, fine.shape[1] // os_
+    det = np.empty((nyd, nxd))
+    _load().orc_bin(nyd, nxd, int(os_), _p(fine), _p(det))
+    return det
+
+
+def solve_os(lines: Lines, D, os_, T0=None, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8,
+             model=MODEL_NONLOCAL):
+    """Solve on a grid oversampled by os_: D is the detector image (pixel
+    lines.p), T the fine thickness [os_ ny][os_ nx].  Returns (T, info)."""
+    D = _c(D)
+    nyd, nxd = D.shape
+    T = np.zeros((nyd * os_, nxd * os_)) if T0 is None else _c(T0).copy()
+    rho = np.zeros(max(n_iter, 1))
+    kappa = np.zeros(max(n_iter, 1))
+    iters = ctypes.c_int(0)
+    st = _load().orc_solve_os(nyd, nxd, int(os_), *lines._args(), model, _p(D), _p(T),
+                              int(n_iter), float(omega), float(tol), float(eps_I),
+                              _p(rho), _p(kappa), ctypes.byref(iters))
+    _check(st, "solve_os")
     k = iters.value
     return T, {"rho": rho[:k], "kappa": kappa[:k], "iters": k}
