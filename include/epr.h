@@ -90,7 +90,19 @@ typedef struct {
                               its independent loads while its predecessor
                               drains, and waits on the device for the
                               predecessor's results.  Results are identical. */
-    int reserved[6];       /* must be zero */
+    int oversample;        /* o >= 1 (0 = 1): solve on an internal grid of
+                              (o ny) x (o nx) pixels of size pixel_m / o
+                              ("Results": the paper's solves run on such grids).
+                              nx, ny and pixel_m of the plan are the detector's;
+                              o nx and o ny must be supported sizes.  With
+                              o > 1 the data D of the solvers and the output P of
+                              epr_forward are detector images (P is the mean of
+                              each o x o block of the fine model), the thickness
+                              T of the solvers and of epr_forward is the fine
+                              map, epr_adjoint and epr_precondition act on fine
+                              maps, and epr_vjp and the batch API are not
+                              available (EPR_ERR_INVALID_ARG). */
+    int reserved[5];       /* must be zero */
 } epr_options;
 
 /* Solver options. */

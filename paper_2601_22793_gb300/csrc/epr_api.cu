@@ -37,7 +37,11 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, c
 cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* D, int batch,
                              int fixed_point, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* D, int batch,
-                             cudaStream_t stream);
+                             size_t npix, double scale, cudaStream_t stream);
+cudaError_t epr_launch_split_os(const EprConsts& C, const EprWork& W, const float* D, int batch,
+                                int fixed_point, int check_done, cudaStream_t stream);
+cudaError_t epr_launch_bin_os(const EprConsts& C, const EprWork& W, int fixed_point, float* out,
+                              float* outs, int batch, cudaStream_t stream);
 cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, float* Out, int line0,
                                int nl, int it, float omega, float eps, float tol, int batch,
                                int check_done, cudaStream_t stream);
@@ -356,19 +360,25 @@ epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, cons
     if (o->init == 0) EPR_TRY(cudaMemsetAsync(T, 0, (size_t)batch * npix * sizeof(float), s));
     {
         ProfScope ps(p, EPR_KERNEL_OTHER, s);
-        EPR_TRY(epr_launch_dnorm(C, p->W, D, batch, s));
+        // |D|^2 at detector resolution; with oversampling the norm of the
+        // residual is taken over its o^2-fold replication, so scale by o^2
+        const size_t npd = npix / ((size_t)C.os * C.os);
+        EPR_TRY(epr_launch_dnorm(C, p->W, D, batch, npd, (double)C.os * C.os, s));
     }
     const int fwd_mode = model == EPR_MODEL_NONLOCAL ? 0 : 1;
     // the residual D - P (and its split over the lines) is stored by the
     // splat flush (non-local, one line, float accumulation) or by the split
     // kernel after the forward (several lines, fixed point, local closure)
     const bool nl = model == EPR_MODEL_NONLOCAL;
-    const bool resid_in_splat = nl && C.ns == 1 && !C.det;
+    const bool resid_in_splat = nl && C.ns == 1 && !C.det && C.os == 1;
     const float eps = (float)(o->eps_I > 0 ? o->eps_I : 1e-8);
     for (int it = 0; it < o->n_iter; ++it) {
         epr_status st = launch_forward(p, T, resid_in_splat ? D : nullptr, it & 1, batch, model, 1, s);
         if (st != EPR_OK) return st;
-        if (!resid_in_splat) {
+        if (C.os > 1) {
+            ProfScope ps(p, EPR_KERNEL_OTHER, s);
+            EPR_TRY(epr_launch_split_os(C, p->W, D, batch, nl && C.det, 1, s));
+        } else if (!resid_in_splat) {
             ProfScope ps(p, EPR_KERNEL_OTHER, s);
             EPR_TRY(epr_launch_split(C, p->W, D, batch, nl && C.det, 1, s));
         }
@@ -435,7 +445,7 @@ epr_status collect_info(epr_plan_s* p, int batch, int n_iter, epr_solve_info* in
 epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int batch, cudaStream_t s)
 {
     p->tuned = true;
-    const bool resid = p->C.ns == 1 && !p->C.det;
+    const bool resid = p->C.ns == 1 && !p->C.det && p->C.os == 1;
     const int tiles[4][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}};
     const int reaches[3] = {3, 4, 6};
     const EprConsts saved = p->C;
@@ -499,7 +509,8 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
     if (st != EPR_OK) return st;
     float *Dd, *Td;
     bool sD, sT;
-    st = resolve(p, 0, D, n, true, s, &Dd, &sD);
+    // D is the detector image (n / o^2 values with oversampling), T the fine map
+    st = resolve(p, 0, D, n / ((size_t)p->C.os * p->C.os), true, s, &Dd, &sD);
     if (st != EPR_OK) return st;
     st = resolve(p, 1, T, n, o->init != 0, s, &Td, &sT);
     if (st != EPR_OK) return st;
@@ -616,13 +627,20 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     if (!energy_keV || !delta || !beta || !weights) return EPR_ERR_INVALID_ARG;
     if (n_lines < 1 || n_lines > EPR_MAX_LINES || !(pixel_m > 0.0) || !(L_m >= 0.0))
         return EPR_ERR_INVALID_ARG;
-    if (!size_ok(nx) || !size_ok(ny)) return EPR_ERR_UNSUPPORTED_SIZE;
-    epr_options o = {4, 0, 0, 1, 0, 0, {0}};
+    epr_options o = {4, 0, 0, 1, 0, 0, 0, {0}};
     if (opt) o = *opt;
-    if (o.max_shift_px < 1 || o.max_shift_px > EPR_MAX_SHIFT || o.overflow_capacity < 0)
+    if (o.max_shift_px < 1 || o.max_shift_px > EPR_MAX_SHIFT || o.overflow_capacity < 0 ||
+        o.oversample < 0 || o.oversample > 16)
         return EPR_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
         if (o.reserved[i] != 0) return EPR_ERR_INVALID_ARG;
+    // oversampled internal grid: everything below is the fine grid's
+    const int os = o.oversample > 1 ? o.oversample : 1;
+    if (nx < 1 || ny < 1 || nx > 4096 / os || ny > 4096 / os) return EPR_ERR_UNSUPPORTED_SIZE;
+    nx *= os;
+    ny *= os;
+    pixel_m /= os;
+    if (!size_ok(nx) || !size_ok(ny)) return EPR_ERR_UNSUPPORTED_SIZE;
     double wsum = 0.0;
     for (int s = 0; s < n_lines; ++s) {
         if (!(energy_keV[s] > 0.0) || !(weights[s] >= 0.0) || !(beta[s] >= 0.0) || !isfinite(delta[s]))
@@ -650,6 +668,7 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     C.smax = o.max_shift_px;
     C.det = o.deterministic ? 1 : 0;
     C.pdl = o.serial_launches ? 0 : 1;
+    C.os = os;
     const size_t npix = (size_t)nx * ny;
     C.ovf_cap = o.overflow_capacity > 0 ? o.overflow_capacity
                                         : (int)(npix / 16 > 4096 ? npix / 16 : 4096);
@@ -755,15 +774,19 @@ epr_status epr_forward(epr_plan_t p, const float* T, float* P, float* Ps, int ba
     if (st != EPR_OK) return st;
     float *Td, *Pd, *Psd = nullptr;
     bool sT, sP, sPs = false;
+    // with oversampling P and Ps are detector images: n / o^2 values per map
+    const size_t nd = n / ((size_t)C.os * C.os);
     st = resolve(p, 0, T, n, true, s, &Td, &sT);
-    if (st == EPR_OK) st = resolve(p, 1, P, n, false, s, &Pd, &sP);
-    if (st == EPR_OK && Ps) st = resolve(p, 2, Ps, n * C.ns, false, s, &Psd, &sPs);
+    if (st == EPR_OK) st = resolve(p, 1, P, nd, false, s, &Pd, &sP);
+    if (st == EPR_OK && Ps) st = resolve(p, 2, Ps, nd * C.ns, false, s, &Psd, &sPs);
     if (st != EPR_OK) return st;
     EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)batch * sizeof(EprProjState), s));
     st = launch_forward(p, Td, nullptr, 0, batch, model, 0, s);
     if (st != EPR_OK) return st;
     const bool fx = (model == EPR_MODEL_NONLOCAL) && C.det;
-    if (fx) {
+    if (C.os > 1) {
+        EPR_TRY(epr_launch_bin_os(C, p->W, fx, Pd, Psd, batch, s));
+    } else if (fx) {
         EPR_TRY(epr_launch_fx_to_float(p->W.Pq, Pd, n, s));
         if (Psd) {
             if (C.ns > 1) EPR_TRY(epr_launch_fx_to_float(p->W.Psq, Psd, n * C.ns, s));
@@ -776,8 +799,8 @@ epr_status epr_forward(epr_plan_t p, const float* T, float* P, float* Ps, int ba
             EPR_TRY(cudaMemcpyAsync(Psd, src, n * C.ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
         }
     }
-    if (sP) EPR_TRY(cudaMemcpyAsync(P, Pd, n * sizeof(float), cudaMemcpyDeviceToHost, s));
-    if (sPs) EPR_TRY(cudaMemcpyAsync(Ps, Psd, n * C.ns * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (sP) EPR_TRY(cudaMemcpyAsync(P, Pd, nd * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (sPs) EPR_TRY(cudaMemcpyAsync(Ps, Psd, nd * C.ns * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (sP || sPs) EPR_TRY(cudaStreamSynchronize(s));
     return EPR_OK;
 }
@@ -843,7 +866,7 @@ epr_status epr_vjp(epr_plan_t p, const float* T, const float* gbar, float* Tbar,
                    double* delta_bar, double* beta_bar, double* L_bar, int batch, void* stream)
 {
     if (!p || !T || !gbar || !Tbar || batch <= 0) return EPR_ERR_INVALID_ARG;
-    if (p->C.nx < 3 || p->C.ny < 3) return EPR_ERR_INVALID_ARG;
+    if (p->C.nx < 3 || p->C.ny < 3 || p->C.os > 1) return EPR_ERR_INVALID_ARG;
     EPR_TRY(cudaSetDevice(p->device));
     cudaStream_t s = (cudaStream_t)stream;
     const EprConsts& C = p->C;
@@ -1061,8 +1084,12 @@ epr_status epr_batch_create(epr_batch_t* out, double pixel_m, double L_m, int n_
         bp->beta[s] = beta[s];
         bp->w[s] = weights[s];
     }
-    epr_options o = {4, 0, 0, 1, 0, 0, {0}};
+    epr_options o = {4, 0, 0, 1, 0, 0, 0, {0}};
     if (opt) o = *opt;
+    if (o.oversample > 1) {   // detector and internal sizes differ: plans only
+        delete bp;
+        return EPR_ERR_INVALID_ARG;
+    }
     bp->opt = o;
     if (cudaGetDevice(&bp->device) != cudaSuccess ||
         cudaEventCreateWithFlags(&bp->start, cudaEventDisableTiming) != cudaSuccess) {

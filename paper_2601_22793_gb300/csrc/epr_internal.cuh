@@ -29,6 +29,8 @@ struct EprConsts {
     int det;             // 1 = int64 fixed-point splat accumulation
     int pdl;             // host side: launch the solver kernels with
                          // programmatic dependent launch
+    int os;              // oversampling: nx, ny are the internal grid, the
+                         // detector image is (ny / os) x (nx / os)
     int ovf_cap;         // overflow list entries per projection
     float inv_n;         // 1 / (nx * ny), folded into the filter
     float f[EPR_MAX_LINES];     // spectral weights, sum 1

@@ -69,10 +69,10 @@ struct Arr {
     __device__ __forceinline__ float operator()(int l) const { return a[l]; }
 };
 
-// Shared fields: T, G_x, G_y, I (order 1); also sqrt(I), Q, D_y(I u_x u_y),
-// I D_x Q, I D_y Q (order 2).  The fluxes I u and I u u are formed inside the
-// stencils from I and G.
-constexpr int local_fields(int order) { return order >= 2 ? 9 : 4; }
+// Shared fields: T, G_x, G_y, I (order 1); also Q, D_y(I u_x u_y), I D_x Q,
+// I D_y Q (order 2).  The fluxes I u and I u u are formed inside the stencils
+// from I and G.
+constexpr int local_fields(int order) { return order >= 2 ? 8 : 4; }
 
 template <int ORDER>
 __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, const LocalArgs A)
@@ -82,8 +82,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, cons
     float* GX = Ts + kLN;
     float* GY = GX + kLN;
     float* I = GY + kLN;
-    float* SQ = I + kLN;      // order 2 only, as the four below
-    float* Q = SQ + kLN;
+    float* Q = I + kLN;       // order 2 only, as the three below
     float* DYB = Q + kLN;
     float* CXQ = DYB + kLN;
     float* CYQ = CXQ + kLN;
@@ -126,19 +125,25 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(const EprConsts C, cons
         auto BXX = [&](int j) { const float ux = cs * GX[j]; return I[j] * ux * ux; };
         auto BYY = [&](int j) { const float uy = cs * GY[j]; return I[j] * uy * uy; };
         auto BXY = [&](int j) { return I[j] * (cs * GX[j]) * (cs * GY[j]); };
-        for (int i = tid; i < kLN; i += kLocalThreads) {
-            const float v = fs * __expf(-mus * Ts[i]);
-            I[i] = v;
-            if constexpr (ORDER >= 2) SQ[i] = sqrtf(v);
-        }
+        for (int i = tid; i < kLN; i += kLocalThreads) I[i] = fs * __expf(-mus * Ts[i]);
         __syncthreads();
         if constexpr (ORDER >= 2) {
+            // Q = (D_xx + D_yy) sqrt(I) / sqrt(I).  With sqrt(I) = sqrt(f) e^(-mu T / 2)
+            // each neighbour n contributes sqrt(I_n) / sqrt(I) - 1 = expm1(-mu (T_n - T) / 2)
+            // (a replicated edge neighbour contributes 0): the same quotient
+            // without the cancellation of second differences of a near-constant.
+            const float hm = -0.5f * mus;
             for (int i = tid; i < kLN; i += kLocalThreads) {   // 1-pixel halo
                 const int ly = i / kLE, lx = i - ly * kLE;
                 if (ly < 1 || ly >= kLE - 1 || lx < 1 || lx >= kLE - 1) continue;
-                const float sq = SQ[i];
-                const float lap = dXX(Arr{SQ}, i, gx0 + lx, nx) + dYY(Arr{SQ}, i, gy0 + ly, ny);
-                Q[i] = sq > 0.f ? lap / sq : 0.f;
+                const int gx = gx0 + lx, gy = gy0 + ly;
+                const float t = Ts[i];
+                float q = 0.f;
+                if (gx > 0) q += expm1f(hm * (Ts[i - 1] - t));
+                if (gx < nx - 1) q += expm1f(hm * (Ts[i + 1] - t));
+                if (gy > 0) q += expm1f(hm * (Ts[i - kLE] - t));
+                if (gy < ny - 1) q += expm1f(hm * (Ts[i + kLE] - t));
+                Q[i] = I[i] > 0.f ? q : 0.f;
             }
             __syncthreads();
             for (int i = tid; i < kLN; i += kLocalThreads) {   // 2-pixel halo

@@ -399,13 +399,14 @@ __global__ void __launch_bounds__(256) k_sumsq_part(const float* __restrict__ D,
     if (threadIdx.x == 0) part[(size_t)b * max_blocks + blockIdx.x] = (double)a;
 }
 
-__global__ void k_sumsq_final(const double* part, int nparts, int max_blocks, EprProjState* st)
+__global__ void k_sumsq_final(const double* part, int nparts, int max_blocks, double scale,
+                              EprProjState* st)
 {
     const int b = blockIdx.x;
     if (threadIdx.x != 0) return;
     double s = 0.0;
     for (int i = 0; i < nparts; ++i) s += part[(size_t)b * max_blocks + i];
-    st[b].dnorm2 = s;
+    st[b].dnorm2 = s * scale;
 }
 
 // ---------------------------------------------------------------------------
@@ -906,13 +907,14 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
 }
 
 // |D|^2 of each projection into the solver state (two small launches).
+// |D|^2 of each projection (D of npix pixels) times scale, into the solver
+// state (two small launches).
 cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* D, int batch,
-                             cudaStream_t stream)
+                             size_t npix, double scale, cudaStream_t stream)
 {
     const int parts = W.max_blocks < 64 ? W.max_blocks : 64;
-    const size_t npix = (size_t)C.nx * C.ny;
     k_sumsq_part<<<dim3(parts, batch), 256, 0, stream>>>(D, npix, W.part_a, W.max_blocks);
-    k_sumsq_final<<<batch, 32, 0, stream>>>(W.part_a, parts, W.max_blocks, W.st);
+    k_sumsq_final<<<batch, 32, 0, stream>>>(W.part_a, parts, W.max_blocks, scale, W.st);
     epr_count_launch(2);
     return cudaGetLastError();
 }

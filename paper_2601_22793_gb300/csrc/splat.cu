@@ -389,6 +389,99 @@ __global__ void __launch_bounds__(256) k_split(const EprConsts C, const SplatArg
     }
 }
 
+// Oversampled grid (os > 1): the detector image of the model is the mean of
+// each os x os block of the fine P; the residual D - mean is formed per
+// detector pixel and replicated to the fine pixels of its block, where it is
+// split over the lines with the fine weights P_s / P.  One thread per
+// detector pixel; P <- replicated residual, P_s <- split residuals.
+template <bool DET>
+__global__ void __launch_bounds__(256) k_split_os(const EprConsts C, const SplatArgs A)
+{
+    const int b = blockIdx.y;
+    epr_grid_wait();
+    if (A.check_done && A.st[b].done) return;
+    epr_grid_release();
+    const int ns = C.ns, os = C.os, nx = C.nx;
+    const int nxd = C.nx / os, nyd = C.ny / os;
+    const size_t npix = (size_t)C.nx * C.ny, pb = (size_t)b * npix;
+    const size_t npd = (size_t)nxd * nyd;
+    const float inv_o2 = 1.f / (float)(os * os);
+    for (size_t qd = (size_t)blockIdx.x * blockDim.x + threadIdx.x; qd < npd;
+         qd += (size_t)gridDim.x * blockDim.x) {
+        const int yd = (int)(qd / nxd), xd = (int)(qd - (size_t)yd * nxd);
+        const size_t f0 = pb + (size_t)yd * os * nx + (size_t)xd * os;   // block corner
+        float mean;
+        if constexpr (DET) {
+            unsigned long long q = 0ull;
+            for (int a = 0; a < os; ++a)
+                for (int c = 0; c < os; ++c) q += A.Pq[f0 + (size_t)a * nx + c];
+            mean = (float)q * EPR_FX_INV * inv_o2;
+        } else {
+            float sum = 0.f;
+            for (int a = 0; a < os; ++a)
+                for (int c = 0; c < os; ++c) sum += A.P[f0 + (size_t)a * nx + c];
+            mean = sum * inv_o2;
+        }
+        const float r = __ldg(&A.D[(size_t)b * npd + qd]) - mean;
+        for (int a = 0; a < os; ++a)
+            for (int c = 0; c < os; ++c) {
+                const size_t i = f0 + (size_t)a * nx + c;
+                if (ns > 1) {
+                    const float p = DET ? (float)A.Pq[i] * EPR_FX_INV : A.P[i];
+                    for (int s = 0; s < ns; ++s) {
+                        const size_t o = pb * ns + (size_t)s * npix + (i - pb);
+                        const float pl = DET ? (float)A.Psq[o] * EPR_FX_INV : A.Ps[o];
+                        A.Ps[o] = (p > 1e-30f) ? r * (pl / p) : r * line_const(C.f, s);
+                    }
+                }
+                A.P[i] = r;
+            }
+    }
+}
+
+// Detector image of the forward model on an oversampled grid: the mean of
+// each os x os block of P (out) and of each P_s (outs, may be NULL).
+template <bool DET>
+__global__ void __launch_bounds__(256) k_bin_os(const EprConsts C, const SplatArgs A, float* out,
+                                                float* outs)
+{
+    const int b = blockIdx.y;
+    const int ns = C.ns, os = C.os, nx = C.nx;
+    const int nxd = C.nx / os, nyd = C.ny / os;
+    const size_t npix = (size_t)C.nx * C.ny, pb = (size_t)b * npix;
+    const size_t npd = (size_t)nxd * nyd;
+    const float inv_o2 = 1.f / (float)(os * os);
+    for (size_t qd = (size_t)blockIdx.x * blockDim.x + threadIdx.x; qd < npd;
+         qd += (size_t)gridDim.x * blockDim.x) {
+        const int yd = (int)(qd / nxd), xd = (int)(qd - (size_t)yd * nxd);
+        const size_t f0 = (size_t)yd * os * nx + (size_t)xd * os;
+        for (int s = -1; s < (outs ? ns : 0); ++s) {   // s = -1: P
+            const bool tot = s < 0;
+            const size_t base = tot ? pb : (pb * ns + (size_t)s * npix);
+            if (!tot && ns == 1) {   // one line: P_s is P
+                outs[(size_t)b * npd + qd] = out[(size_t)b * npd + qd];
+                continue;
+            }
+            float m;
+            if constexpr (DET) {
+                const unsigned long long* q = tot ? A.Pq : A.Psq;
+                unsigned long long sum = 0ull;
+                for (int a = 0; a < os; ++a)
+                    for (int c = 0; c < os; ++c) sum += q[base + f0 + (size_t)a * nx + c];
+                m = (float)sum * EPR_FX_INV * inv_o2;
+            } else {
+                const float* q = tot ? A.P : A.Ps;
+                float sum = 0.f;
+                for (int a = 0; a < os; ++a)
+                    for (int c = 0; c < os; ++c) sum += q[base + f0 + (size_t)a * nx + c];
+                m = sum * inv_o2;
+            }
+            if (tot) out[(size_t)b * npd + qd] = m;
+            else outs[((size_t)b * ns + s) * npd + qd] = m;
+        }
+    }
+}
+
 template <int NS, bool DET, bool RESID>
 cudaError_t launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
                      cudaStream_t stream)
@@ -492,4 +585,47 @@ cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* 
                     : epr_launch_kernel(C.pdl != 0, k_split<false>, grid, dim3(256), 0, stream, C, A);
     epr_count_launch(1);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Oversampled solve: the split at detector resolution (k_split_os).
+cudaError_t epr_launch_split_os(const EprConsts& C, const EprWork& W, const float* D, int batch,
+                                int fixed_point, int check_done, cudaStream_t stream)
+{
+    SplatArgs A = {};
+    A.D = D;
+    A.P = W.P;
+    A.Ps = W.Ps;
+    A.Pq = W.Pq;
+    A.Psq = W.Psq;
+    A.st = W.st;
+    A.check_done = check_done;
+    const size_t npd = (size_t)(C.nx / C.os) * (C.ny / C.os);
+    size_t blocks = (npd + 255) / 256;
+    if (blocks > 1216) blocks = 1216;
+    const dim3 grid((unsigned)blocks, batch), blk(256);
+    const bool pdl = C.pdl != 0;
+    const cudaError_t e =
+        fixed_point ? epr_launch_kernel(pdl, k_split_os<true>, grid, blk, 0, stream, C, A)
+                    : epr_launch_kernel(pdl, k_split_os<false>, grid, blk, 0, stream, C, A);
+    epr_count_launch(1);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Oversampled forward: detector images of P and of each P_s (outs may be NULL).
+cudaError_t epr_launch_bin_os(const EprConsts& C, const EprWork& W, int fixed_point, float* out,
+                              float* outs, int batch, cudaStream_t stream)
+{
+    SplatArgs A = {};
+    A.P = W.P;
+    A.Ps = W.Ps;
+    A.Pq = W.Pq;
+    A.Psq = W.Psq;
+    const size_t npd = (size_t)(C.nx / C.os) * (C.ny / C.os);
+    size_t blocks = (npd + 255) / 256;
+    if (blocks > 1216) blocks = 1216;
+    const dim3 grid((unsigned)blocks, batch), blk(256);
+    if (fixed_point) k_bin_os<true><<<grid, blk, 0, stream>>>(C, A, out, outs);
+    else k_bin_os<false><<<grid, blk, 0, stream>>>(C, A, out, outs);
+    epr_count_launch(1);
+    return cudaGetLastError();
 }
