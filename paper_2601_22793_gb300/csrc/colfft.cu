@@ -238,8 +238,10 @@ EprColLaunch epr_col_config(const EprConsts& C, int cw_hint)
     while (cw > 1 && C.half % cw != 0) cw >>= 1;
     // keep the block at 512 threads or fewer, 8 elements per thread if possible
     int ept = 8;
-    while (C.ny * cw / ept > 512 && cw > 1) cw >>= 1;
-    while (C.ny * cw / ept > 512 && ept < 16) ept *= 2;
+    // 8192-point columns (oversampled internal grids): one column, 1024 threads
+    const int tmax = C.ny >= 8192 ? 1024 : 512;
+    while (C.ny * cw / ept > tmax && cw > 1) cw >>= 1;
+    while (C.ny * cw / ept > tmax && ept < 16) ept *= 2;
     L.CW = cw;
     L.lgCW = 0;
     while ((1 << L.lgCW) < cw) ++L.lgCW;
@@ -338,6 +340,7 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     EPR_COL_CASE(2048, 2, 8)
     EPR_COL_CASE(3072, 1, 8)
     EPR_COL_CASE(4096, 1, 8)
+    EPR_COL_CASE(8192, 1, 8)
 #undef EPR_COL_CASE
     if (!done) {
         if (L.EPT == 8)
@@ -365,5 +368,6 @@ cudaError_t epr_col_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1536, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<3072, 1, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<4096, 1, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<8192, 1, 8>);
     return e;
 }

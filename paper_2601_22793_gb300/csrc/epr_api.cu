@@ -134,9 +134,11 @@ struct epr_plan_s {
 
 namespace {
 
-bool size_ok(int n)
+// 2^a 3^b with a >= 3, from 16 to nmax (4096; 8192 for an oversampled
+// internal grid)
+bool size_ok(int n, int nmax = 4096)
 {
-    if (n < 16 || n > 4096) return false;
+    if (n < 16 || n > nmax) return false;
     int m = n, twos = 0;
     while (m % 2 == 0) {
         m /= 2;
@@ -607,7 +609,9 @@ const char* epr_status_string(epr_status s)
     switch (s) {
     case EPR_OK: return "ok";
     case EPR_ERR_INVALID_ARG: return "invalid argument";
-    case EPR_ERR_UNSUPPORTED_SIZE: return "unsupported size (need 2^a 3^b, a >= 3, 16..4096)";
+    case EPR_ERR_UNSUPPORTED_SIZE:
+        return "unsupported size (need 2^a 3^b, a >= 3, 16..4096; internal grids of an "
+               "oversampled plan up to 8192)";
     case EPR_ERR_OOM: return "out of device memory";
     case EPR_ERR_CUDA: return "CUDA error";
     case EPR_ERR_NONFINITE: return "non-finite input";
@@ -636,11 +640,13 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
         if (o.reserved[i] != 0) return EPR_ERR_INVALID_ARG;
     // oversampled internal grid: everything below is the fine grid's
     const int os = o.oversample > 1 ? o.oversample : 1;
-    if (nx < 1 || ny < 1 || nx > 4096 / os || ny > 4096 / os) return EPR_ERR_UNSUPPORTED_SIZE;
+    if (nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || nx > 8192 / os || ny > 8192 / os)
+        return EPR_ERR_UNSUPPORTED_SIZE;
     nx *= os;
     ny *= os;
     pixel_m /= os;
-    if (!size_ok(nx) || !size_ok(ny)) return EPR_ERR_UNSUPPORTED_SIZE;
+    if (!size_ok(nx, os > 1 ? 8192 : 4096) || !size_ok(ny, os > 1 ? 8192 : 4096))
+        return EPR_ERR_UNSUPPORTED_SIZE;
     double wsum = 0.0;
     for (int s = 0; s < n_lines; ++s) {
         if (!(energy_keV[s] > 0.0) || !(weights[s] >= 0.0) || !(beta[s] >= 0.0) || !isfinite(delta[s]))
@@ -830,6 +836,9 @@ epr_status epr_precondition(epr_plan_t p, float* g, int line, int batch, void* s
 {
     if (!p || !g || batch <= 0 || line < 0 || line >= p->C.ns) return EPR_ERR_INVALID_ARG;
     if (!aligned16(g)) return EPR_ERR_INVALID_ARG;
+    // the stand-alone passes run the runtime-sized engine, whose blocks hold
+    // rows and columns of up to 4096 points
+    if (p->C.nx > 4096 || p->C.ny > 4096) return EPR_ERR_UNSUPPORTED_SIZE;
     EPR_TRY(cudaSetDevice(p->device));
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)batch * p->C.nx * p->C.ny;

@@ -794,6 +794,7 @@ bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream,
     EPR_MONO_CASE(2048, 1)
     EPR_MONO_CASE(3072, 1)
     EPR_MONO_CASE(4096, 1)
+    EPR_MONO_CASE(8192, 1)
 #undef EPR_MONO_CASE
     return false;
 }
@@ -818,6 +819,7 @@ cudaError_t init_mono_ct()
     EPR_MONO_INIT(2048, 1)
     EPR_MONO_INIT(3072, 1)
     EPR_MONO_INIT(4096, 1)
+    EPR_MONO_INIT(8192, 1)
 #undef EPR_MONO_INIT
     return e;
 }

@@ -49,7 +49,8 @@ def _data(oracle, nyd, nxd, os_, n_lines, model, seed, L=10.0):
 # case runs at L = 4 m, where the iteration contracts.
 @pytest.mark.parametrize("nyd,nxd,os_,n_lines,model,det,L", [
     (48, 64, 2, 1, 0, False, 10.0), (48, 64, 2, 1, 0, True, 10.0), (32, 32, 4, 2, 0, False, 10.0),
-    (64, 48, 2, 2, 2, False, 4.0), (32, 48, 2, 1, 1, False, 10.0)])
+    (64, 48, 2, 2, 2, False, 4.0), (32, 48, 2, 1, 1, False, 10.0),
+    (16, 2048, 4, 1, 0, False, 10.0), (2048, 16, 4, 2, 0, False, 10.0)])
 def test_oversampled_solve_vs_oracle(torch, oracle, nyd, nxd, os_, n_lines, model, det, L):
     from paper_2601_22793_gb300 import epr as E
     D, _ = _data(oracle, nyd, nxd, os_, n_lines, model, 80 + nyd + os_, L)
@@ -96,3 +97,16 @@ def test_oversampled_plan_refuses_vjp_and_batches(torch):
             E.epr_vjp(p.handle, T, T, torch.empty_like(T), 1)
     with pytest.raises(E.EprError):
         E.epr_batch_create(P_DET, 10.0, [80.0], [2e-7], [1e-10], [1.0], oversample=2)
+
+
+def test_internal_grid_limits(torch):
+    """Detector sides up to 4096 and internal sides up to 8192; the plain
+    preconditioner entry point, on the runtime-sized engine, refuses 8192."""
+    from paper_2601_22793_gb300 import epr as E
+    phys = (P_DET, 10.0, [80.0], [2e-7], [1e-10], [1.0])
+    with pytest.raises(E.EprError):
+        E.Plan(4096, 16, *phys, oversample=4)          # 16384 internal
+    with E.Plan(2048, 16, *phys, oversample=4) as p:    # 8192 x 64 internal
+        g = torch.zeros((64, 8192), device="cuda")
+        with pytest.raises(E.EprError):
+            E.epr_precondition(p.handle, g, 0)
