@@ -426,11 +426,11 @@ def run_ours(a):
     pplan.close()
     other["vjp_polychromatic"] = {"workload": "ellipsoids_poly_2048 forward + VJP, 8 lines, 1 map",
                                   "forward_ms": round(fwd_ms, 3), "vjp_ms": round(vjp_ms, 3)}
-    # oversampled internal grids (the paper's operating mode: o = 2 local, 4 non-local),
-    # at 4096^2 internal pixels: a 2048^2 detector at o = 2, a 1024^2 detector at o = 4
+    # oversampled internal grids (the paper's operating mode: o = 2 local, 4 non-local):
+    # a 2048^2 detector at o = 4 (8192^2 internal) and at o = 2, a 1024^2 one at o = 4
     ovs = {}
-    for name, nd, os_, model in (("nonlocal_o2_2048", 2048, 2, 0), ("nonlocal_o4_1024", 1024, 4, 0),
-                                 ("local2_o2_2048", 2048, 2, 2)):
+    for name, nd, os_, model in (("nonlocal_o4_2048", 2048, 4, 0), ("nonlocal_o2_2048", 2048, 2, 0),
+                                 ("nonlocal_o4_1024", 1024, 4, 0), ("local2_o2_2048", 2048, 2, 2)):
         # the 2048^2 phantom subsampled to the detector, replicated to the fine grid
         tf = np.kron(tau[::2048 // nd, ::2048 // nd], np.ones((os_, os_)))
         with epr.Plan(nd, nd, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights,
