@@ -467,7 +467,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     const float* Rb = POLY ? A.Ps + (pb * C.ns + (size_t)(A.line0 + sl) * npix) : A.P + pb;
     const float* Rt = A.P + pb;   // D - P, for |D - P|^2
     float ra = 0.f;
-#pragma unroll 2
+#pragma unroll
     for (int k = 0; k < kEPT; ++k) {
         const int e = tid + k * T;
         const int m = row_of<NX, RP>(e), x = e - m * NX;
