@@ -60,7 +60,7 @@ struct SplatArgs {
     unsigned int* ovf_mask;
     EprProjState* st;
     unsigned int* err;
-    int TH, TW, lgTW, parity;
+    int parity;
     int check_done;
     float fxs, fxs_inv;      // float mode: scale 2^S of the uint32 accumulators
 };
@@ -76,27 +76,33 @@ __device__ __forceinline__ float grad1(float lo, float mid, float hi, int i, int
 // i / d for 0 <= i < 2^20 and d < 2^12 without an integer division
 __device__ __forceinline__ int fdiv(int i, float inv_d) { return (int)(((float)i + 0.5f) * inv_d); }
 
+// v is already scaled by the accumulator's 2^S
 template <bool DET>
-__device__ __forceinline__ void acc_add(void* acc, int idx, float v, float fxs)
+__device__ __forceinline__ void acc_add(void* acc, int idx, float v)
 {
     if constexpr (DET) {
-        unsigned long long q = (unsigned long long)__float2ll_rn(v * EPR_FX_SCALE);
+        unsigned long long q = (unsigned long long)__float2ll_rn(v);
         atomicAdd(reinterpret_cast<unsigned long long*>(acc) + idx, q);
     } else {
-        atomicAdd(reinterpret_cast<unsigned int*>(acc) + idx, __float2uint_rn(v * fxs));
+        atomicAdd(reinterpret_cast<unsigned int*>(acc) + idx, __float2uint_rn(v));
     }
 }
 
 // NS = 1: single line known at compile time; NS = 0: C.ns lines.
-// Shared layout: accumulators [ns][TH][TW]; the staged thickness window
+// Shared layout: accumulators [ns][TH + 2][TW + 2]; the staged thickness window
 // [SH][SWa] whose first column ax0 = tx0 - HX is 16-byte aligned (HX = R + 1
 // rounded up to 4) so rows load as float4; a list of far sources.
 constexpr int kFarList = 256;
+constexpr int kQuad = 4;   // sources per scan work item
 
-template <int NS, bool DET, bool RESID>
-__global__ void __launch_bounds__(kSplatThreads)
+// The tile shape is a compile-time parameter (64 x 64, 32 x 64, 64 x 32 or
+// 32 x 32, chosen on the host), so every tile-derived index and offset folds
+// into immediates.
+template <int NS, bool DET, bool RESID, int TH, int TW>
+__global__ void __launch_bounds__(kSplatThreads, (NS == 1 && RESID) ? 4 : 5)
 k_splat(const EprConsts C, const SplatArgs A)
 {
+    static_assert((TW & (TW - 1)) == 0 && TH * TW <= 4 * 4 * kSplatThreads, "tile shape");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_far_idx[kFarList];
     __shared__ unsigned int s_far_mask[kFarList];
@@ -104,17 +110,17 @@ k_splat(const EprConsts C, const SplatArgs A)
     const int b = blockIdx.z;
     const int nx = C.nx, ny = C.ny;
     const int ns = NS ? NS : C.ns;
-    const int TH = A.TH, TW = A.TW;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     const int R = C.smax + 1;
     const int RH = TH + 2 * R, RW = TW + 2 * R;     // source region
+    const int RHq = (RH + kQuad - 1) / kQuad;         // its rows in quads
     const int HX = (R + 1 + 3) & ~3;
-    const int SH = RH + 2, SWa = TW + 2 * HX;        // staged thickness
+    const int SH = RHq * kQuad + 2, SWa = TW + 2 * HX;   // staged thickness
     const int coff = HX - R - 1;                     // staged column of source column tx0 - R - 1
-    const int tile = TH * TW;
+    constexpr int tile = TH * TW;
     // accumulators [ns][TH + 2][TW + 2]: the tile with a one-pixel apron, so
     // the four corners of any source that touches the tile have a slot
-    const int AP = TW + 2, ACC = (TH + 2) * AP;
+    constexpr int AP = TW + 2, ACC = (TH + 2) * AP;
     const size_t npix = (size_t)nx * ny;
     const int tid = threadIdx.x;
 
@@ -127,8 +133,8 @@ k_splat(const EprConsts C, const SplatArgs A)
     // the detector data of the tile, fetched before the scan (residual output)
     constexpr int kDq = 4;   // float4 per thread: tiles up to 64 x 64
     float4 dreg[kDq];
-    const int nq = tile >> 2;
-    const int tw4 = TW >> 2;
+    constexpr int nq = tile >> 2;
+    constexpr int tw4 = TW >> 2;
     if constexpr (RESID) {
 #pragma unroll
         for (int k = 0; k < kDq; ++k) {
@@ -171,70 +177,88 @@ k_splat(const EprConsts C, const SplatArgs A)
     __syncthreads();
 
     const float fsmax = (float)C.smax;
-    const float fxs = A.fxs;
-    const int nsrc = RH * RW;
-    // (ly, lx) of source i, advanced by kSplatThreads = dly rows + dlx columns
+    // the accumulator scale 2^S is folded into the line weight: a power of two
+    // scales exactly, so each contribution rounds to the same integer
+    const float fxs = DET ? EPR_FX_SCALE : A.fxs;
+    // One source at tile-local (ly, lx) with thickness t and twice its
+    // gradient: every line's shift, contributions and far flag.  Gradients
+    // are kept doubled (hi - lo), and half the shift constant multiplies
+    // them: 0.5 scales exactly, so u is the same float.
+    auto source = [&](int ly, int lx, float t, float gx2, float gy2) {
+        unsigned int far = 0u;
+#pragma unroll(NS ? NS : 1)
+        for (int s = 0; s < ns; ++s) {
+            const float ch = 0.5f * C.c[s];
+            const float ux = ch * gx2, uy = ch * gy2;
+            if (fabsf(ux) <= fsmax && fabsf(uy) <= fsmax && t >= C.tneg[s]) {
+                const float fx = floorf(ux), fy = floorf(uy);
+                const int cx = lx - R + (int)fx, cy = ly - R + (int)fy;  // corner 00, tile-local
+                // all four corners have a slot (apron) when one is in the tile
+                if ((unsigned)(cx + 1) <= (unsigned)TW && (unsigned)(cy + 1) <= (unsigned)TH) {
+                    const float dx = ux - fx, dy = uy - fy;
+                    const float m = (C.f[s] * fxs) * __expf(-C.mu[s] * t);   // 2^S f e^(-mu t)
+                    const float mx1 = m * dx, mx0 = m - mx1;          // m (1 - dx), m dx
+                    const float w = 1.f - dy;
+                    const int idx = s * ACC + (cy + 1) * AP + (cx + 1);
+                    acc_add<DET>(acc, idx, mx0 * w);
+                    acc_add<DET>(acc, idx + 1, mx1 * w);
+                    acc_add<DET>(acc, idx + AP, mx0 * dy);
+                    acc_add<DET>(acc, idx + AP + 1, mx1 * dy);
+                }
+            } else {
+                far |= 1u << s;
+            }
+        }
+        if (far && (unsigned)(ly - R) < (unsigned)TH && (unsigned)(lx - R) < (unsigned)TW) {
+            const int sy = ty0 - R + ly, sx = tx0 - R + lx;
+            const int pos = atomicAdd(&s_far_n, 1);
+            if (pos < kFarList) {
+                s_far_idx[pos] = sy * nx + sx;
+                s_far_mask[pos] = far;
+            } else {   // list full: append to the global list directly
+                const int gpos = atomicAdd(&A.st[b].ovf_count[A.parity], 1);
+                if (gpos < C.ovf_cap) {
+                    A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = sy * nx + sx;
+                    A.ovf_mask[(size_t)b * C.ovf_cap + gpos] = far;
+                } else {
+                    atomicOr(A.err, EPR_DEVERR_OVERFLOW);
+                }
+            }
+        }
+    };
+    // The scan: a thread takes kQuad vertically adjacent sources of one
+    // column (rows ly0 .. ly0 + kQuad - 1 of the region, padded to a multiple
+    // of kQuad; padding rows cannot reach the tile and are not owned by it),
+    // reusing the column's thickness values.  Specialised for blocks whose
+    // staged region lies inside the grid (central differences everywhere, no
+    // edge tests) and for edge blocks.  Work item (qy, lx) is advanced by
+    // kSplatThreads = dly quad rows + dlx columns.
+    const int nitem = RHq * RW;
     const int dly = kSplatThreads / RW, dlx = kSplatThreads - dly * RW;
-    // The scan, specialised for blocks whose staged region lies inside the grid
-    // (central differences everywhere, no edge tests) and for edge blocks.
-    // Gradients are kept doubled (hi - lo), and half the shift constant
-    // multiplies them: 0.5 scales exactly, so u is the same float.
     auto scan = [&](auto interior_tag) {
         constexpr bool IN = decltype(interior_tag)::value;
-        int ly = tid / RW, lx = tid - (tid / RW) * RW;
-        for (int i = tid; i < nsrc; i += kSplatThreads, lx += dlx,
-                 ly += dly + (lx >= RW ? 1 : 0), lx -= (lx >= RW ? RW : 0)) {
-            const float* tp = Ts + (ly + 1) * SWa + (lx + 1 + coff);
-            const float t = tp[0];
-            float gx2, gy2;   // twice the gradient
-            if constexpr (IN) {
-                gx2 = tp[1] - tp[-1];
-                gy2 = tp[SWa] - tp[-SWa];
-            } else {
-                const int sy = ty0 - R + ly, sx = tx0 - R + lx;
-                if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) continue;
-                gx2 = 2.f * grad1(tp[-1], t, tp[1], sx, nx);
-                gy2 = 2.f * grad1(tp[-SWa], t, tp[SWa], sy, ny);
-            }
-            unsigned int far = 0u;
-#pragma unroll(NS ? NS : 1)
-            for (int s = 0; s < ns; ++s) {
-                const float ch = 0.5f * C.c[s];
-                const float ux = ch * gx2, uy = ch * gy2;
-                if (fabsf(ux) <= fsmax && fabsf(uy) <= fsmax && t >= C.tneg[s]) {
-                    const float fx = floorf(ux), fy = floorf(uy);
-                    const int cx = lx - R + (int)fx, cy = ly - R + (int)fy;  // corner 00, tile-local
-                    // all four corners have a slot (apron) when one is in the tile
-                    if ((unsigned)(cx + 1) <= (unsigned)TW && (unsigned)(cy + 1) <= (unsigned)TH) {
-                        const float dx = ux - fx, dy = uy - fy;
-                        const float m = C.f[s] * __expf(-C.mu[s] * t);
-                        const float mx1 = m * dx, mx0 = m - mx1;          // m (1 - dx), m dx
-                        const float w = 1.f - dy;
-                        const int idx = s * ACC + (cy + 1) * AP + (cx + 1);
-                        acc_add<DET>(acc, idx, mx0 * w, fxs);
-                        acc_add<DET>(acc, idx + 1, mx1 * w, fxs);
-                        acc_add<DET>(acc, idx + AP, mx0 * dy, fxs);
-                        acc_add<DET>(acc, idx + AP + 1, mx1 * dy, fxs);
-                    }
+        int qy = tid / RW, lx = tid - (tid / RW) * RW;
+        for (int i = tid; i < nitem; i += kSplatThreads, lx += dlx,
+                 qy += dly + (lx >= RW ? 1 : 0), lx -= (lx >= RW ? RW : 0)) {
+            const int ly0 = qy * kQuad;
+            const float* tp = Ts + (ly0 + 1) * SWa + (lx + 1 + coff);   // source (ly0, lx)
+            float col[kQuad + 2];   // the column, rows ly0 - 1 .. ly0 + kQuad
+#pragma unroll
+            for (int j = 0; j < kQuad + 2; ++j) col[j] = tp[(j - 1) * SWa];
+#pragma unroll
+            for (int j = 0; j < kQuad; ++j) {
+                const float t = col[j + 1];
+                float gx2, gy2;   // twice the gradient
+                if constexpr (IN) {
+                    gx2 = tp[j * SWa + 1] - tp[j * SWa - 1];
+                    gy2 = col[j + 2] - col[j];
                 } else {
-                    far |= 1u << s;
+                    const int sy = ty0 - R + ly0 + j, sx = tx0 - R + lx;
+                    if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) continue;
+                    gx2 = 2.f * grad1(tp[j * SWa - 1], t, tp[j * SWa + 1], sx, nx);
+                    gy2 = 2.f * grad1(col[j], t, col[j + 2], sy, ny);
                 }
-            }
-            if (far && (unsigned)(ly - R) < (unsigned)TH && (unsigned)(lx - R) < (unsigned)TW) {
-                const int sy = ty0 - R + ly, sx = tx0 - R + lx;
-                const int pos = atomicAdd(&s_far_n, 1);
-                if (pos < kFarList) {
-                    s_far_idx[pos] = sy * nx + sx;
-                    s_far_mask[pos] = far;
-                } else {   // list full: append to the global list directly
-                    const int gpos = atomicAdd(&A.st[b].ovf_count[A.parity], 1);
-                    if (gpos < C.ovf_cap) {
-                        A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = sy * nx + sx;
-                        A.ovf_mask[(size_t)b * C.ovf_cap + gpos] = far;
-                    } else {
-                        atomicOr(A.err, EPR_DEVERR_OVERFLOW);
-                    }
-                }
+                source(ly0 + j, lx, t, gx2, gy2);
             }
         }
     };
@@ -278,7 +302,7 @@ k_splat(const EprConsts C, const SplatArgs A)
         }
     } else {
         for (int i = tid; i < tile; i += kSplatThreads) {
-            const int ly = i >> A.lgTW, lx = i & (TW - 1);
+            const int ly = i / TW, lx = i & (TW - 1);
             const int gy = ty0 + ly, gx = tx0 + lx;
             if (gy >= ny || gx >= nx) continue;
             const size_t o = (size_t)b * npix + (size_t)gy * nx + gx;
@@ -482,16 +506,40 @@ __global__ void __launch_bounds__(256) k_bin_os(const EprConsts C, const SplatAr
     }
 }
 
-template <int NS, bool DET, bool RESID>
+template <int NS, bool DET, bool RESID, int TH, int TW>
 cudaError_t launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
                      cudaStream_t stream)
 {
     const bool pdl = C.pdl != 0;
-    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID>, grid,
+    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID, TH, TW>, grid,
                                             dim3(kSplatThreads), smem, stream, C, A);
     if (e != cudaSuccess) return e;
     return epr_launch_kernel(pdl, k_splat_overflow<DET, RESID>, dim3(128, batch), dim3(128), 0,
                              stream, C, A);
+}
+
+template <int TH, int TW>
+cudaError_t launch_shape(const EprConsts& C, const SplatArgs& A, int resid, dim3 grid, size_t smem,
+                         int batch, cudaStream_t stream)
+{
+    const bool mono = C.ns == 1;
+    if (C.det)
+        return mono ? launch_t<1, true, false, TH, TW>(C, A, grid, smem, batch, stream)
+                    : launch_t<0, true, false, TH, TW>(C, A, grid, smem, batch, stream);
+    if (resid && mono) return launch_t<1, false, true, TH, TW>(C, A, grid, smem, batch, stream);
+    return mono ? launch_t<1, false, false, TH, TW>(C, A, grid, smem, batch, stream)
+                : launch_t<0, false, false, TH, TW>(C, A, grid, smem, batch, stream);
+}
+
+template <int TH, int TW>
+cudaError_t init_shape()
+{
+    cudaError_t e = epr_allow_max_smem(k_splat<1, true, false, TH, TW>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, true, false, TH, TW>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true, TH, TW>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, false, TH, TW>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW>);
+    return e;
 }
 
 }  // namespace
@@ -500,8 +548,9 @@ size_t epr_splat_smem(const EprConsts& C, int TH, int TW)
 {
     const int R = C.smax + 1;
     const int HX = (R + 1 + 3) & ~3;
+    const int SH = (TH + 2 * R + kQuad - 1) / kQuad * kQuad + 2;
     const size_t acc_bytes = (size_t)C.ns * (TH + 2) * (TW + 2) * (C.det ? 8 : 4);
-    return ((acc_bytes + 15) & ~size_t(15)) + (size_t)(TH + 2 * R + 2) * (TW + 2 * HX) * sizeof(float);
+    return ((acc_bytes + 15) & ~size_t(15)) + (size_t)SH * (TW + 2 * HX) * sizeof(float);
 }
 
 // Host launcher: the tile kernel, then the overflow kernel (2 launches).
@@ -522,10 +571,6 @@ cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* 
     A.ovf_mask = W.ovf_mask;
     A.st = W.st;
     A.err = W.err;
-    A.TH = TH;
-    A.TW = TW;
-    A.lgTW = 0;
-    while ((1 << A.lgTW) < TW) ++A.lgTW;
     A.parity = parity & 1;
     A.check_done = check_done;
     {   // 2^(32 - S) >= 2 (2 reach + 3)^2: the largest pixel sum fits in uint32
@@ -537,28 +582,22 @@ cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* 
     }
     const size_t smem = epr_splat_smem(C, TH, TW);
     dim3 grid((C.nx + TW - 1) / TW, (C.ny + TH - 1) / TH, batch);
-    const bool mono = C.ns == 1;
     cudaError_t e;
-    if (C.det) {
-        if (mono) e = launch_t<1, true, false>(C, A, grid, smem, batch, stream);
-        else e = launch_t<0, true, false>(C, A, grid, smem, batch, stream);
-    } else if (resid && mono) {
-        e = launch_t<1, false, true>(C, A, grid, smem, batch, stream);
-    } else {
-        if (mono) e = launch_t<1, false, false>(C, A, grid, smem, batch, stream);
-        else e = launch_t<0, false, false>(C, A, grid, smem, batch, stream);
-    }
+    if (TH == 64 && TW == 64) e = launch_shape<64, 64>(C, A, resid, grid, smem, batch, stream);
+    else if (TH == 32 && TW == 64) e = launch_shape<32, 64>(C, A, resid, grid, smem, batch, stream);
+    else if (TH == 64 && TW == 32) e = launch_shape<64, 32>(C, A, resid, grid, smem, batch, stream);
+    else if (TH == 32 && TW == 32) e = launch_shape<32, 32>(C, A, resid, grid, smem, batch, stream);
+    else return cudaErrorInvalidValue;
     epr_count_launch(2);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t epr_splat_init()
 {
-    cudaError_t e = epr_allow_max_smem(k_splat<1, true, false>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, true, false>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, false>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false>);
+    cudaError_t e = init_shape<64, 64>();
+    if (e == cudaSuccess) e = init_shape<32, 64>();
+    if (e == cudaSuccess) e = init_shape<64, 32>();
+    if (e == cudaSuccess) e = init_shape<32, 32>();
     return e;
 }
 
