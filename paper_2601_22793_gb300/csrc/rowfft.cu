@@ -422,8 +422,12 @@ __host__ __device__ constexpr int ct_lg(int v) { return v <= 1 ? 0 : 1 + ct_lg<N
 template <int NX, int RP>
 __device__ __forceinline__ int row_of(int e) { return RP == 1 ? 0 : (int)((unsigned)e / NX); }
 
+// Shared memory: the thickness rows yb - 1 .. yb + 2 RP, staged for the
+// gradient, alias the FFT rows, which are written only after the last
+// thickness read (row_fwd_mono_smem).  256-thread monochromatic blocks run
+// five per SM (48 registers).
 template <int NX, int RP, bool POLY, bool GATHER>
-__global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
+__global__ void __launch_bounds__(NX * RP / kEPT, (NX * RP / kEPT == 256 && !POLY) ? 5 : (65536 / 64) / (NX * RP / kEPT))
 k_row_fwd_mono(const EprConsts C, const RowArgs A)
 {
     constexpr int T = NX * RP / kEPT;
@@ -438,7 +442,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     const size_t npix = (size_t)NX * ny;
     const size_t pb = (size_t)b * npix;
     const int yb = blockIdx.x * RP * 2;
-    float* Ts = reinterpret_cast<float*>(zs + ((PR::len(RP * SM) + 1) & ~1));
+    float* Ts = reinterpret_cast<float*>(zs);   // aliases the FFT rows (see above)
     if constexpr (GATHER) {   // T is not written by the predecessor: fetch it before the wait
         const float* Tb = A.T + pb;
         constexpr int Q4 = NX / 4;
@@ -467,6 +471,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     const float* Rb = POLY ? A.Ps + (pb * C.ns + (size_t)(A.line0 + sl) * npix) : A.P + pb;
     const float* Rt = A.P + pb;   // D - P, for |D - P|^2
     float ra = 0.f;
+    float2 vk[kEPT];   // the packed row pair values, stored once the thickness is dead
 #pragma unroll
     for (int k = 0; k < kEPT; ++k) {
         const int e = tid + k * T;
@@ -515,7 +520,14 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
                 ra += own * own;
             }
         }
-        zs[PR::idx(m * SM + x)] = make_float2(v[0], v[1]);
+        vk[k] = make_float2(v[0], v[1]);
+    }
+    if constexpr (GATHER) __syncthreads();   // every thickness read is done
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        const int e = tid + k * T;
+        const int m = row_of<NX, RP>(e), x = e - m * NX;
+        zs[PR::idx(m * SM + x)] = vk[k];
     }
     __syncthreads();
     eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
@@ -746,6 +758,15 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
     }
 }
 
+// dynamic shared memory of k_row_fwd_mono: FFT rows aliased with the
+// 2 RP + 2 staged thickness rows
+size_t row_fwd_mono_smem(int nx, int rp)
+{
+    const size_t fft = (size_t)((PR::len(rp * (nx + kPad)) + 1) & ~1) * sizeof(float2);
+    const size_t ts = (size_t)(2 * rp + 2) * nx * sizeof(float);
+    return fft > ts ? fft : ts;
+}
+
 // dynamic shared memory of k_row_inv_mono: FFT rows, T rows
 size_t row_inv_mono_smem(int nx, int rp)
 {
@@ -773,11 +794,11 @@ bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream,
         const dim3 blk(NXV * RPV / kEPT);                                                    \
         if (FWD && !poly) {                                                                  \
             err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, false, GATHER>, grid, blk, \
-                                    smem, stream, C, A);                                     \
+                                    row_fwd_mono_smem(NXV, RPV), stream, C, A);              \
         } else if (FWD) {                                                                    \
             const dim3 g3(grid.x, grid.y, A.nl);                                             \
-            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, true, GATHER>, g3, blk, smem, \
-                                    stream, C, A);                                           \
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, true, GATHER>, g3, blk, \
+                                    row_fwd_mono_smem(NXV, RPV), stream, C, A);              \
         } else if (!poly) {                                                                  \
             err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<NXV, RPV>, grid, blk,          \
                                     row_inv_mono_smem(NXV, RPV), stream, C, A);              \
