@@ -96,10 +96,11 @@ constexpr int kFarList = 256;
 constexpr int kQuad = 4;   // sources per scan work item
 
 // The tile shape is a compile-time parameter (64 x 64, 32 x 64, 64 x 32 or
-// 32 x 32, chosen on the host), so every tile-derived index and offset folds
-// into immediates.
-template <int NS, bool DET, bool RESID, int TH, int TW>
-__global__ void __launch_bounds__(kSplatThreads, (NS == 1 && RESID) ? 4 : 5)
+// 32 x 32, chosen on the host), and so is the reach RC of the float solves
+// for the reaches the tuner tries (3, 4, 6; RC = 0 takes C.smax), so every
+// tile- and reach-derived index, stride and offset folds into immediates.
+template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0>
+__global__ void __launch_bounds__(kSplatThreads, (NS == 1 && RESID && RC == 0) ? 4 : 5)
 k_splat(const EprConsts C, const SplatArgs A)
 {
     static_assert((TW & (TW - 1)) == 0 && TH * TW <= 4 * 4 * kSplatThreads, "tile shape");
@@ -111,7 +112,8 @@ k_splat(const EprConsts C, const SplatArgs A)
     const int nx = C.nx, ny = C.ny;
     const int ns = NS ? NS : C.ns;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-    const int R = C.smax + 1;
+    const int smax = RC > 0 ? RC : C.smax;
+    const int R = smax + 1;
     const int RH = TH + 2 * R, RW = TW + 2 * R;     // source region
     const int RHq = (RH + kQuad - 1) / kQuad;         // its rows in quads
     const int HX = (R + 1 + 3) & ~3;
@@ -176,7 +178,7 @@ k_splat(const EprConsts C, const SplatArgs A)
     }
     __syncthreads();
 
-    const float fsmax = (float)C.smax;
+    const float fsmax = (float)smax;
     // the accumulator scale 2^S is folded into the line weight: a power of two
     // scales exactly, so each contribution rounds to the same integer
     const float fxs = DET ? EPR_FX_SCALE : A.fxs;
@@ -506,12 +508,12 @@ __global__ void __launch_bounds__(256) k_bin_os(const EprConsts C, const SplatAr
     }
 }
 
-template <int NS, bool DET, bool RESID, int TH, int TW>
+template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0>
 cudaError_t launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
                      cudaStream_t stream)
 {
     const bool pdl = C.pdl != 0;
-    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID, TH, TW>, grid,
+    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID, TH, TW, RC>, grid,
                                             dim3(kSplatThreads), smem, stream, C, A);
     if (e != cudaSuccess) return e;
     return epr_launch_kernel(pdl, k_splat_overflow<DET, RESID>, dim3(128, batch), dim3(128), 0,
@@ -526,9 +528,21 @@ cudaError_t launch_shape(const EprConsts& C, const SplatArgs& A, int resid, dim3
     if (C.det)
         return mono ? launch_t<1, true, false, TH, TW>(C, A, grid, smem, batch, stream)
                     : launch_t<0, true, false, TH, TW>(C, A, grid, smem, batch, stream);
-    if (resid && mono) return launch_t<1, false, true, TH, TW>(C, A, grid, smem, batch, stream);
-    return mono ? launch_t<1, false, false, TH, TW>(C, A, grid, smem, batch, stream)
-                : launch_t<0, false, false, TH, TW>(C, A, grid, smem, batch, stream);
+    if (resid && mono) {
+        switch (C.smax) {
+        case 3: return launch_t<1, false, true, TH, TW, 3>(C, A, grid, smem, batch, stream);
+        case 4: return launch_t<1, false, true, TH, TW, 4>(C, A, grid, smem, batch, stream);
+        case 6: return launch_t<1, false, true, TH, TW, 6>(C, A, grid, smem, batch, stream);
+        default: return launch_t<1, false, true, TH, TW>(C, A, grid, smem, batch, stream);
+        }
+    }
+    if (mono) return launch_t<1, false, false, TH, TW>(C, A, grid, smem, batch, stream);
+    switch (C.smax) {
+    case 3: return launch_t<0, false, false, TH, TW, 3>(C, A, grid, smem, batch, stream);
+    case 4: return launch_t<0, false, false, TH, TW, 4>(C, A, grid, smem, batch, stream);
+    case 6: return launch_t<0, false, false, TH, TW, 6>(C, A, grid, smem, batch, stream);
+    default: return launch_t<0, false, false, TH, TW>(C, A, grid, smem, batch, stream);
+    }
 }
 
 template <int TH, int TW>
@@ -537,8 +551,14 @@ cudaError_t init_shape()
     cudaError_t e = epr_allow_max_smem(k_splat<1, true, false, TH, TW>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, true, false, TH, TW>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true, TH, TW>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true, TH, TW, 3>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true, TH, TW, 4>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true, TH, TW, 6>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, false, TH, TW>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 3>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 4>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 6>);
     return e;
 }
 
