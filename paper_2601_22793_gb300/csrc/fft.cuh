@@ -220,7 +220,8 @@ __device__ void fft(float2* buf, int N, int lgseq, int sj, int sm, const float2*
 // template parameters, so every stage is unrolled, strides fold into address
 // offsets, the first stage (Ns = 1) needs no twiddle, and a radix-R stage
 // loads one twiddle w = exp(DIR 2 pi i jm / (Ns R)) and forms w^2 .. w^(R-1)
-// by complex multiplication (a few ulp, well inside the transform's error).
+// by the Chebyshev three-term recurrence of cos and sin (a few ulp for
+// R <= 8, well inside the transform's error).
 // ---------------------------------------------------------------------------
 namespace eprfft {
 
@@ -292,13 +293,20 @@ __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const fl
                 for (int r = 0; r < R; ++r) v[k][r] = in[PADI::idx((j + r * NR) * SJ + base)];
             }
             if constexpr (NS > 1) {
+                // w^r = (cos r theta, sin r theta) by the three-term recurrence
+                // x_{r+1} = 2 cos(theta) x_r - x_{r-1} (two multiply-adds per power)
                 float2 w = __ldg(&tw[jm * TWSTEP]);
                 if (DIR > 0) w.y = -w.y;
-                float2 wr = w;
+                const float c2 = w.x + w.x;
+                float2 wp = make_float2(1.f, 0.f), wr = w;
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
                     v[k][r] = cmul(v[k][r], wr);
-                    if (r + 1 < R) wr = cmul(wr, w);
+                    if (r + 1 < R) {
+                        const float2 wn = make_float2(fmaf(c2, wr.x, -wp.x), fmaf(c2, wr.y, -wp.y));
+                        wp = wr;
+                        wr = wn;
+                    }
                 }
             }
             dst[k] = (jd * NS * R + jm) * SJ + base;

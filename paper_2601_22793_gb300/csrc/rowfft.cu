@@ -34,6 +34,12 @@ enum { FWD_SOLVE_NL = 0, FWD_SOLVE_LOCAL = 1, FWD_LOAD = 2 };
 enum { INV_UPDATE = 0, INV_STORE = 1 };
 
 constexpr int kEPT = 8;   // complex elements per thread in the row FFT
+
+// Projection of a row-pass block.  The row passes walk the batch from the
+// last projection to the first (grid y), the splat and the column pass from
+// the first to the last: each kernel starts on the projections its
+// predecessor touched last, whose data are still in L2.
+__device__ __forceinline__ int row_batch_index() { return (int)(gridDim.y - 1 - blockIdx.y); }
 using PR = eprfft::PadRow;  // shared layout of the packed rows
 constexpr int kPad = 4;   // float2 padding between packed rows in shared memory
 
@@ -123,7 +129,7 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
 {
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
-    const int b = blockIdx.y;
+    const int b = row_batch_index();
     const int nx = C.nx, ny = C.ny, half = C.half;
     const int T = blockDim.x, tid = threadIdx.x;
     const int RP = A.RP, sm = nx + kPad;
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const Row
 {
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
-    const int b = blockIdx.y;
+    const int b = row_batch_index();
     epr_grid_wait();
     if (A.check_done && A.st[b].done) return;
     epr_grid_release();
@@ -436,7 +442,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     constexpr int LGRP = ct_lg<NX>(RP);
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
-    const int b = blockIdx.y;
+    const int b = row_batch_index();
     const int sl = POLY ? (int)blockIdx.z : 0;   // line of this block (polychromatic)
     const int ny = C.ny, tid = threadIdx.x;
     const size_t npix = (size_t)NX * ny;
@@ -486,12 +492,18 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
             } else {
             const float* tr = Ts + (2 * m + r0 + 1) * NX;
             const float t = tr[x];
+            // edges (one-sided differences): with one row pair per block only
+            // the first and last element of a thread can be an edge column,
+            // and only the first (last) row of the pair the top (bottom) row
+            const bool xlo = (RP > 1 || k == 0) && x == 0;
+            const bool xhi = (RP > 1 || k == kEPT - 1) && x == NX - 1;
+            const bool ylo = r0 == 0 && y == 0, yhi = r0 == 1 && y == ny - 1;
             float gx, gy;
-            if (x == 0) gx = tr[1] - t;
-            else if (x == NX - 1) gx = t - tr[x - 1];
+            if (xlo) gx = tr[1] - t;
+            else if (xhi) gx = t - tr[x - 1];
             else gx = 0.5f * (tr[x + 1] - tr[x - 1]);
-            if (y == 0) gy = tr[NX + x] - t;
-            else if (y == ny - 1) gy = t - tr[x - NX];
+            if (ylo) gy = tr[NX + x] - t;
+            else if (yhi) gy = t - tr[x - NX];
             else gy = 0.5f * (tr[NX + x] - tr[x - NX]);
             const float lim = 2.f * (float)(NX > ny ? NX : ny);
             const float ux = fminf(fmaxf(cs * gx, -lim), lim);
@@ -580,7 +592,7 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
     constexpr int LGRP = ct_lg<NX>(RP);
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
-    const int b = blockIdx.y;
+    const int b = row_batch_index();
     const int ny = C.ny, tid = threadIdx.x;
     const size_t pb = (size_t)b * NX * ny;
     const int yb = blockIdx.x * RP * 2;
@@ -668,7 +680,7 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
     constexpr int LGRP = ct_lg<NX>(RP);
     extern __shared__ __align__(16) float2 zs[];
     __shared__ float red[64];
-    const int b = blockIdx.y;
+    const int b = row_batch_index();
     const int ny = C.ny, tid = threadIdx.x;
     const size_t pb = (size_t)b * NX * ny;
     const int yb = blockIdx.x * RP * 2;
