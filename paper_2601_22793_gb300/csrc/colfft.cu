@@ -32,38 +32,50 @@ struct ColArgs {
     int check_done;
 };
 
-// Filter value of frequency row y of the tile, in place in buf (two phases:
-// column 0 reads the mirrored frequency, so all reads precede all writes).
-template <int NY, int CW, int EPT, int T, int LGCW>
-__device__ __forceinline__ void col_filter(float2* buf, const EprConsts& C, int s, int kx0, int tid)
+// The Paganin filter H = inv_n / (1 + ha kx^2 + hb ky^2) of element e of a
+// [NY][CW] tile whose first column is kx0 > 0, as the output map of the last
+// forward FFT stage (a fast reciprocal: 2 ulp).
+template <int NY, int CW, int LGCW>
+struct ColPaganin {
+    float ha, hb, inv_n;
+    int kx0;
+    __device__ __forceinline__ float2 operator()(float2 v, int e) const
+    {
+        const int y = e >> LGCW, c = e & (CW - 1);
+        const float ky = (float)(y <= NY / 2 ? y : y - NY), kx = (float)(kx0 + c);
+        const float H = __fdividef(inv_n, fmaf(ha * kx, kx, fmaf(hb * ky, ky, 1.f)));
+        return make_float2(v.x * H, v.y * H);
+    }
+};
+
+// The filter of the tile holding column kx = 0, in place in buf.  That column
+// packs the DC and Nyquist columns of the real transform, so its output at y
+// mixes the values at y and NY - y: a thread takes both of a mirrored pair.
+// The other columns of the tile are filtered pointwise.  Ends with a barrier.
+template <int NY, int CW, int LGCW, int T>
+__device__ __forceinline__ void col_filter0(float2* buf, const EprConsts& C, int s, int tid)
 {
     const float ha = line_const(C.ha, s), hb = line_const(C.hb, s), inv_n = C.inv_n;
-    const int half = C.half;
-    float2 nv[EPT];
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-        const int e = tid + k * T;
-        const int y = e >> LGCW, c = e & (CW - 1);
-        const int kx = kx0 + c;
-        const float ky = (float)(y <= NY / 2 ? y : y - NY);
+    const float kn = (float)C.half;
+    for (int y = tid; y <= NY / 2; y += T) {
+        const int yn = y == 0 ? 0 : NY - y;   // 0 and NY / 2 are their own mirror
+        const float ky = (float)y;
         const float qy = hb * ky * ky;
-        const float2 v = buf[eprfft::PadCol::idx(e)];
-        if (kx != 0) {
-            const float H = inv_n / (1.f + ha * (float)kx * (float)kx + qy);
-            nv[k] = cscale(v, H);
-        } else {
-            const float kn = (float)half;
-            const float H0 = inv_n / (1.f + qy);
-            const float HN = inv_n / (1.f + ha * kn * kn + qy);
-            const int yneg = y == 0 ? 0 : NY - y;
-            const float2 w = cconj(buf[eprfft::PadCol::idx((yneg << LGCW) + c)]);
-            const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
-            nv[k] = make_float2(hp * v.x + hm * w.x, hp * v.y + hm * w.y);
-        }
+        const float H0 = inv_n / (1.f + qy);
+        const float HN = inv_n / (1.f + ha * kn * kn + qy);
+        const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
+        const float2 a = buf[eprfft::PadCol::idx(y << LGCW)];
+        const float2 b = buf[eprfft::PadCol::idx(yn << LGCW)];
+        buf[eprfft::PadCol::idx(y << LGCW)] = make_float2(hp * a.x + hm * b.x, hp * a.y - hm * b.y);
+        if (yn != y)
+            buf[eprfft::PadCol::idx(yn << LGCW)] = make_float2(hp * b.x + hm * a.x, hp * b.y - hm * a.y);
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) buf[eprfft::PadCol::idx(tid + k * T)] = nv[k];
+    const ColPaganin<NY, CW, LGCW> f{ha, hb, inv_n, 0};
+    for (int e = tid; e < NY * CW; e += T) {
+        if ((e & (CW - 1)) == 0) continue;
+        const int i = eprfft::PadCol::idx(e);
+        buf[i] = f(buf[i], e);
+    }
     __syncthreads();
 }
 
@@ -145,8 +157,13 @@ k_col_ct(const EprConsts C, const ColArgs A)
         buf[PC::idx(e)] = Sb[(size_t)y * half + kx0 + c];
     }
     __syncthreads();
-    eprfft::fft_ct<PC, -1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
-    col_filter<NY, CW, EPT, T, LGCW>(buf, C, s, kx0, tid);
+    if (kx0 != 0) {   // the filter as the output map of the forward transform
+        const ColPaganin<NY, CW, LGCW> f{line_const(C.ha, s), line_const(C.hb, s), C.inv_n, kx0};
+        eprfft::fft_ct<PC, -1, NY, EPT, LGCW, CW, 1, 0>(buf, A.tw, tid, f);
+    } else {
+        eprfft::fft_ct<PC, -1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
+        col_filter0<NY, CW, LGCW, T>(buf, C, s, tid);
+    }
     eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
     epr_grid_release();
 #pragma unroll
@@ -158,11 +175,14 @@ k_col_ct(const EprConsts C, const ColArgs A)
 }
 
 // The same pass with the [NY][CW] tile moved by the tensor memory
-// accelerator: BOXES bulk loads of [NY / BOXES][CW] into a dense staging tile
-// (no L1 traffic, one elected thread), the first FFT stage reading from it,
-// and the result copied back to the staging tile and stored in bulk.  The
-// tile's row pitch is CW * 8 bytes, which keeps the strided 16-byte row
-// segments of the column off the load/store unit.
+// accelerator: BOXES bulk loads of [NY / BOXES][CW] into a dense tile at the
+// start of the FFT buffer (no L1 traffic, one elected thread).  The first
+// FFT stage reads every operand from the dense tile before its barrier and
+// writes the padded layout over it; at the end the result is read out of the
+// padded layout, and after a barrier written back dense and stored in bulk.
+// So the block needs only the padded buffer.  The tile's row pitch is
+// CW * 8 bytes, which keeps the strided 16-byte row segments of the column
+// off the load/store unit.
 constexpr unsigned int kTmaWaitPolls = 1u << 22;
 
 template <int NY, int CW, int EPT>
@@ -176,10 +196,9 @@ k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMa
     constexpr unsigned int BYTES = NY * CW * sizeof(float2);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ alignas(8) uint64_t bar;
-    // 128-byte aligned staging tile, then the padded FFT buffer
+    // the 128-byte aligned FFT buffer; the dense tile occupies its start
     const size_t base = ((size_t)__cvta_generic_to_shared(smem_raw) + 127) & ~size_t(127);
-    float2* stg = reinterpret_cast<float2*>(smem_raw + (base - (size_t)__cvta_generic_to_shared(smem_raw)));
-    float2* buf = stg + NY * CW;
+    float2* buf = reinterpret_cast<float2*>(smem_raw + (base - (size_t)__cvta_generic_to_shared(smem_raw)));
     const int b = blockIdx.z, sl = blockIdx.y, tid = threadIdx.x;
     const int kx0 = blockIdx.x * CW;
     if (tid == 0) {
@@ -195,7 +214,7 @@ k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMa
         epr_tma::mbar_arrive_expect_tx(&bar, BYTES);
 #pragma unroll
         for (int i = 0; i < BOXES; ++i)
-            epr_tma::load_2d(stg + i * BOXY * CW, &map, 2 * kx0, row0 + i * BOXY, &bar);
+            epr_tma::load_2d(buf + i * BOXY * CW, &map, 2 * kx0, row0 + i * BOXY, &bar);
     }
     if (!epr_tma::mbar_wait(&bar, 0, kTmaWaitPolls)) {
         // the copy did not arrive: report, and wait once more (bounded) so
@@ -204,21 +223,34 @@ k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMa
         epr_tma::mbar_wait(&bar, 0, kTmaWaitPolls);
         return;
     }
-    eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1>(stg, buf, A.tw, tid);
-    col_filter<NY, CW, EPT, T, LGCW>(buf, C, A.line0 + sl, kx0, tid);
+    const int s = A.line0 + sl;
+    if (kx0 != 0) {   // the filter as the output map of the forward transform
+        const ColPaganin<NY, CW, LGCW> f{line_const(C.ha, s), line_const(C.hb, s), C.inv_n, kx0};
+        eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1>(buf, buf, A.tw, tid, f);
+    } else {
+        eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1>(buf, buf, A.tw, tid);
+        col_filter0<NY, CW, LGCW, T>(buf, C, s, tid);
+    }
     eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
     epr_grid_release();
+    // back to the dense layout in place, in two halves of the elements: the
+    // dense slot e holds the padded element e' <= e, so writing the first
+    // half destroys only first-half padded elements, already read
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-        const int e = tid + k * T;
-        stg[e] = buf[PC::idx(e)];
+    for (int h = 0; h < 2; ++h) {
+        float2 o[EPT / 2];
+#pragma unroll
+        for (int k = 0; k < EPT / 2; ++k) o[k] = buf[PC::idx(tid + (h * EPT / 2 + k) * T)];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < EPT / 2; ++k) buf[tid + (h * EPT / 2 + k) * T] = o[k];
     }
     epr_tma::fence_async_shared();
     __syncthreads();
     if (tid == 0) {
 #pragma unroll
         for (int i = 0; i < BOXES; ++i)
-            epr_tma::store_2d(&map, 2 * kx0, row0 + i * BOXY, stg + i * BOXY * CW);
+            epr_tma::store_2d(&map, 2 * kx0, row0 + i * BOXY, buf + i * BOXY * CW);
         epr_tma::bulk_commit();
         epr_tma::bulk_wait_all();
     }
@@ -259,9 +291,14 @@ static bool col_tma_case(const EprConsts& C, const EprColLaunch& L)
            (L.CW == 2 && (C.ny == 1536 || C.ny == 2048));
 }
 
+// elements per thread of the bulk-copy pass: 16 for 2048-point columns (256
+// threads and 37 KB per block, four blocks per SM, so the 512 blocks of a
+// 2048^2 projection are resident at once), 8 otherwise
+static int col_tma_ept(const EprConsts& C) { return C.ny == 2048 ? 16 : 8; }
+
 static size_t col_tma_smem(const EprConsts& C, const EprColLaunch& L)
 {
-    return 128 + (size_t)C.ny * L.CW * sizeof(float2) + (size_t)PC::len(C.ny * L.CW) * sizeof(float2);
+    return 128 + (size_t)PC::len(C.ny * L.CW) * sizeof(float2);
 }
 
 // Tensor map of S seen as `rows` rows of nx floats, with [ny or 256][2 CW]
@@ -314,17 +351,18 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     if (W.col_map && cw_hint == 0 && col_tma_case(C, L)) {
         const CUtensorMap& map = *static_cast<const CUtensorMap*>(W.col_map);
         const size_t smem = col_tma_smem(C, L);
-#define EPR_COL_TMA_CASE(NYV, CWV)                                                             \
-        if (!done && C.ny == NYV && L.CW == CWV) {                                            \
-            e = epr_launch_kernel(pdl, k_col_tma<NYV, CWV, 8>, grid, dim3(NYV * CWV / 8), smem, \
-                                  stream, C, A, map);                                         \
+        const int ept = col_tma_ept(C);
+#define EPR_COL_TMA_CASE(NYV, CWV, EPTV)                                                       \
+        if (!done && C.ny == NYV && L.CW == CWV && ept == EPTV) {                             \
+            e = epr_launch_kernel(pdl, k_col_tma<NYV, CWV, EPTV>, grid, dim3(NYV * CWV / EPTV), \
+                                  smem, stream, C, A, map);                                   \
             done = true;                                                                      \
         }
-        EPR_COL_TMA_CASE(256, 4)
-        EPR_COL_TMA_CASE(512, 4)
-        EPR_COL_TMA_CASE(1024, 4)
-        EPR_COL_TMA_CASE(1536, 2)
-        EPR_COL_TMA_CASE(2048, 2)
+        EPR_COL_TMA_CASE(256, 4, 8)
+        EPR_COL_TMA_CASE(512, 4, 8)
+        EPR_COL_TMA_CASE(1024, 4, 8)
+        EPR_COL_TMA_CASE(1536, 2, 8)
+        EPR_COL_TMA_CASE(2048, 2, 16)
 #undef EPR_COL_TMA_CASE
     }
 #define EPR_COL_CASE(NYV, CWV, EPTV)                                                           \
@@ -364,7 +402,7 @@ cudaError_t epr_col_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<512, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1024, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1536, 2, 8>);
-    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 16>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1536, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<3072, 1, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<4096, 1, 8>);

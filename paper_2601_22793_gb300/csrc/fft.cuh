@@ -260,11 +260,19 @@ __host__ __device__ constexpr int ct_ns(int n, int s)
     return v;
 }
 
-// Reads its operands from `in` (layout PADI) and writes to `buf` (layout
-// PAD); in == buf for every stage but a first one fed from another tile.
-template <class PADI, class PAD, int R, int DIR, int EPT, int N, int NS, int LGSEQ, int SJ, int SM>
+// Output map of a stage: out = post(value, e) with e = j * SJ + m * SM the
+// element's unpadded index; Identity leaves the value.
+struct Identity {
+    __device__ __forceinline__ float2 operator()(float2 v, int) const { return v; }
+};
+
+// Reads its operands from `in` (layout PADI) and writes post(result) to
+// `buf` (layout PAD).  Every operand is read before the stage's first
+// barrier, so in == buf works even when PADI != PAD.
+template <class PADI, class PAD, int R, int DIR, int EPT, int N, int NS, int LGSEQ, int SJ, int SM,
+          class POST = Identity>
 __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const float2* __restrict__ tw,
-                                         int tid)
+                                         int tid, const POST& post = POST())
 {
     constexpr int NSEQ = 1 << LGSEQ;
     constexpr int T = (N * NSEQ) / EPT;
@@ -320,33 +328,45 @@ __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const fl
             if constexpr ((NS * SJ) % PAD::kPeriod == 0) {
                 const int o0 = PAD::idx(dst[k]);
 #pragma unroll
-                for (int r = 0; r < R; ++r) buf[o0 + PAD::step(r * NS * SJ)] = v[k][r];
+                for (int r = 0; r < R; ++r)
+                    buf[o0 + PAD::step(r * NS * SJ)] = post(v[k][r], dst[k] + r * NS * SJ);
             } else {
 #pragma unroll
-                for (int r = 0; r < R; ++r) buf[PAD::idx(dst[k] + r * NS * SJ)] = v[k][r];
+                for (int r = 0; r < R; ++r)
+                    buf[PAD::idx(dst[k] + r * NS * SJ)] = post(v[k][r], dst[k] + r * NS * SJ);
             }
         }
     }
     __syncthreads();
 }
 
-template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int S = 0>
-__device__ __forceinline__ void fft_ct(float2* buf, const float2* __restrict__ tw, int tid)
+// Stages S.. of the transform; the last one maps its outputs through post.
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int S = 0, class POST = Identity>
+__device__ __forceinline__ void fft_ct(float2* buf, const float2* __restrict__ tw, int tid,
+                                       const POST& post = POST())
 {
-    if constexpr (S < ct_n_stages(N)) {
+    if constexpr (S + 1 < ct_n_stages(N)) {
         stage_ct<PAD, PAD, ct_radix(N, S), DIR, EPT, N, ct_ns(N, S), LGSEQ, SJ, SM>(buf, buf, tw, tid);
-        fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, S + 1>(buf, tw, tid);
+        fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, S + 1>(buf, tw, tid, post);
+    } else if constexpr (S + 1 == ct_n_stages(N)) {
+        stage_ct<PAD, PAD, ct_radix(N, S), DIR, EPT, N, ct_ns(N, S), LGSEQ, SJ, SM>(buf, buf, tw, tid,
+                                                                                     post);
     }
 }
 
-// The same transform with its input in a separate dense tile `in` (element
-// j of sequence m at in[j * SJ + m * SM]); the result is in buf.
-template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM>
+// The same transform with its input in a dense tile `in` (element j of
+// sequence m at in[j * SJ + m * SM]), which may be buf itself; the result is
+// in buf.
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, class POST = Identity>
 __device__ __forceinline__ void fft_ct_from(const float2* in, float2* buf, const float2* __restrict__ tw,
-                                            int tid)
+                                            int tid, const POST& post = POST())
 {
-    stage_ct<Dense, PAD, ct_radix(N, 0), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid);
-    fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, 1>(buf, tw, tid);
+    if constexpr (ct_n_stages(N) == 1) {
+        stage_ct<Dense, PAD, ct_radix(N, 0), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid, post);
+    } else {
+        stage_ct<Dense, PAD, ct_radix(N, 0), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid);
+        fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, 1>(buf, tw, tid, post);
+    }
 }
 
 }  // namespace eprfft
