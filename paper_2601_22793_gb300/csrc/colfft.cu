@@ -18,19 +18,34 @@
 #include "fft.cuh"
 #include "tma.cuh"
 
+int epr_row_blocks(const EprConsts& C);
+
 namespace {
 
 using PC = eprfft::PadCol;  // shared layout of the column tile
 
 struct ColArgs {
     float2* S;            // [B][nl][ny][nx/2]
-    const EprProjState* st;
+    EprProjState* st;
     const float2* tw;     // exp(-2 pi i t / ny)
     unsigned int* err;    // device error word
+    const double* part_c; // [B][max_blocks] forward row pass partials
+    double* rho_hist;     // [B][hist_len]
     int CW, lgCW;
     int line0, nl;
     int check_done;
+    int rho_it;           // >= 0: block 0 forms rho of this iteration
+    int nblk, max_blocks, hist_len;
 };
+
+// Block 0 of the column pass of a solve (line 0) turns the forward row
+// pass's partials into rho; the grid dependency wait has made them visible.
+__device__ __forceinline__ void col_finalize_rho(const ColArgs& A, int b, bool lead)
+{
+    if (A.rho_it >= 0 && lead)
+        finalize_rho(&A.st[b], A.part_c + (size_t)b * A.max_blocks, A.nblk,
+                     A.rho_hist ? A.rho_hist + (size_t)b * A.hist_len : nullptr, A.hist_len, A.rho_it);
+}
 
 // The Paganin filter H = inv_n / (1 + ha kx^2 + hb ky^2) of element e of a
 // [NY][CW] tile whose first column is kx0 > 0, as the output map of the last
@@ -87,6 +102,7 @@ __global__ void __launch_bounds__(512, 2) k_col(const EprConsts C, const ColArgs
     epr_grid_wait();
     if (A.check_done && A.st[b].done) return;
     epr_grid_release();
+    col_finalize_rho(A, b, blockIdx.x == 0 && sl == 0);
     const int s = A.line0 + sl;
     const int ny = C.ny, half = C.half, CW = A.CW, lgCW = A.lgCW;
     const int T = blockDim.x, tid = threadIdx.x;
@@ -146,6 +162,7 @@ k_col_ct(const EprConsts C, const ColArgs A)
     const int b = blockIdx.z, sl = blockIdx.y;
     epr_grid_wait();
     if (A.check_done && A.st[b].done) return;
+    col_finalize_rho(A, b, blockIdx.x == 0 && sl == 0);
     const int s = A.line0 + sl;
     const int half = C.half, tid = threadIdx.x;
     const int kx0 = blockIdx.x * CW;
@@ -216,6 +233,7 @@ k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMa
         for (int i = 0; i < BOXES; ++i)
             epr_tma::load_2d(buf + i * BOXY * CW, &map, 2 * kx0, row0 + i * BOXY, &bar);
     }
+    col_finalize_rho(A, b, blockIdx.x == 0 && sl == 0);   // while the tile is in flight
     if (!epr_tma::mbar_wait(&bar, 0, kTmaWaitPolls)) {
         // the copy did not arrive: report, and wait once more (bounded) so
         // that no copy lands after the block has left
@@ -330,8 +348,10 @@ bool epr_col_make_map(const EprConsts& C, const float2* S, long long rows, CUten
     return r == CUDA_SUCCESS;
 }
 
+// rho_it >= 0 (a solve): block 0 also forms rho of iteration rho_it from the
+// forward row pass's partials.
 cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int nl, int batch,
-                           int check_done, int cw_hint, cudaStream_t stream)
+                           int check_done, int cw_hint, int rho_it, cudaStream_t stream)
 {
     const EprColLaunch L = epr_col_config(C, cw_hint);
     ColArgs A;
@@ -339,6 +359,12 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     A.st = W.st;
     A.tw = W.tw_y;
     A.err = W.err;
+    A.part_c = W.part_c;
+    A.rho_hist = W.rho_hist;
+    A.rho_it = rho_it;
+    A.nblk = rho_it >= 0 ? epr_row_blocks(C) : 0;
+    A.max_blocks = W.max_blocks;
+    A.hist_len = W.hist_len;
     A.CW = L.CW;
     A.lgCW = L.lgCW;
     A.line0 = line0;

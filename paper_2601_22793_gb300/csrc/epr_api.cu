@@ -33,7 +33,7 @@ size_t epr_splat_smem(const EprConsts& C, int TH, int TW);
 cudaError_t epr_splat_init();
 cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
                                const float* D, const float* G, int line0, int nl, int it,
-                               int batch, int check_done, cudaStream_t stream);
+                               float tol, int batch, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* D, int batch,
                              int fixed_point, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* D, int batch,
@@ -48,7 +48,9 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
 cudaError_t epr_row_init();
 bool epr_col_make_map(const EprConsts& C, const float2* S, long long rows, CUtensorMap* out);
 cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int nl, int batch,
-                           int check_done, int cw_hint, cudaStream_t stream);
+                           int check_done, int cw_hint, int rho_it, cudaStream_t stream);
+cudaError_t epr_launch_finalize_kappa(const EprConsts& C, const EprWork& W, int it, float tol,
+                                      int batch, cudaStream_t stream);
 cudaError_t epr_col_init();
 cudaError_t epr_launch_gather(const EprConsts& C, const float* T, const float* r, float* g, int line,
                               int batch, cudaStream_t stream);
@@ -223,6 +225,7 @@ epr_status ensure_workspace(epr_plan_s* p, int batch, int hist)
     if (e == cudaSuccess) e = dalloc(p, &W.st, (size_t)nb);
     if (e == cudaSuccess) e = dalloc(p, &W.part_a, (size_t)nb * W.max_blocks);
     if (e == cudaSuccess) e = dalloc(p, &W.part_b, (size_t)nb * W.max_blocks);
+    if (e == cudaSuccess) e = dalloc(p, &W.part_c, (size_t)nb * W.max_blocks);
     if (e == cudaSuccess) e = dalloc(p, &W.rho_hist, (size_t)nb * nh);
     if (e == cudaSuccess) e = dalloc(p, &W.kappa_hist, (size_t)nb * nh);
     if (e == cudaSuccess) e = dalloc(p, &W.err, 1);
@@ -386,17 +389,22 @@ epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, cons
         }
         {
             ProfScope ps(p, EPR_KERNEL_ROW_FWD, s);
-            EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, T, D, nullptr, 0, C.ns, it, batch, 1, s));
+            EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, T, D, nullptr, 0, C.ns, it,
+                                       (float)o->tol, batch, 1, s));
         }
         {
             ProfScope ps(p, EPR_KERNEL_COL, s);
-            EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 1, 0, s));
+            EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 1, 0, it, s));
         }
         {
             ProfScope ps(p, EPR_KERNEL_ROW_INV, s);
             EPR_TRY(epr_launch_row_inv(C, p->W, 0, T, 0, C.ns, it, (float)o->omega, eps,
                                        (float)o->tol, batch, 1, s));
         }
+    }
+    if (o->n_iter > 0) {   // kappa of the last iteration (the others: each next forward pass)
+        ProfScope ps(p, EPR_KERNEL_OTHER, s);
+        EPR_TRY(epr_launch_finalize_kappa(C, p->W, o->n_iter - 1, (float)o->tol, batch, s));
     }
     return EPR_OK;
 }
@@ -848,8 +856,8 @@ epr_status epr_precondition(epr_plan_t p, float* g, int line, int batch, void* s
     bool sg;
     st = resolve(p, 0, g, n, true, s, &gd, &sg);
     if (st != EPR_OK) return st;
-    EPR_TRY(epr_launch_row_fwd(p->C, p->W, 2, nullptr, nullptr, gd, line, 1, 0, batch, 0, s));
-    EPR_TRY(epr_launch_col(p->C, p->W, line, 1, batch, 0, 0, s));
+    EPR_TRY(epr_launch_row_fwd(p->C, p->W, 2, nullptr, nullptr, gd, line, 1, 0, 0.f, batch, 0, s));
+    EPR_TRY(epr_launch_col(p->C, p->W, line, 1, batch, 0, 0, -1, s));
     EPR_TRY(epr_launch_row_inv(p->C, p->W, 1, gd, line, 1, 0, 1.f, 0.f, 0.f, batch, 0, s));
     if (sg) {
         EPR_TRY(cudaMemcpyAsync(g, gd, n * sizeof(float), cudaMemcpyDeviceToHost, s));

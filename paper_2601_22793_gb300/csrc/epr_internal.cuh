@@ -47,8 +47,6 @@ struct EprConsts {
 struct EprProjState {
     int done;        // 1 = converged, later iterations skip the projection
     int iters;       // iterations run
-    unsigned int cnt_fwd;     // arrival counters of the last-block pattern
-    unsigned int cnt_inv;
     int ovf_count[2];         // overflow list fill, by splat parity
     long long ovf_total;      // sources that took the overflow path, all iterations
     double dnorm2;            // |D|^2 of the projection (set once per solve)
@@ -66,15 +64,17 @@ struct EprWork {
     int* ovf_idx;        // [B][cap] source pixel index
     unsigned int* ovf_mask;   // [B][cap] lines that took the overflow path
     EprProjState* st;    // [B]
-    double* part_a;      // [B][max_blocks] block partial sums
-    double* part_b;      // [B][max_blocks]
+    double* part_a;      // [B][max_blocks] block partial sums of the inverse
+    double* part_b;      // [B][max_blocks]    row pass (kappa)
+    double* part_c;      // [B][max_blocks] block partial sums of the forward
+                         //    row pass (rho)
     double* rho_hist;    // [B][hist_len]
     double* kappa_hist;  // [B][hist_len]
     unsigned int* err;   // device error word
     const float2* tw_x;  // twiddles exp(-2 pi i t / nx), t < nx
     const float2* tw_y;  // twiddles exp(-2 pi i t / ny), t < ny
     int hist_len;        // columns of rho_hist / kappa_hist
-    int max_blocks;      // columns of part_a / part_b
+    int max_blocks;      // columns of part_a / part_b / part_c
     const void* col_map; // host: CUtensorMap of S for the column pass's bulk
                          // copies (NULL: the column pass uses plain loads)
 };
@@ -144,34 +144,66 @@ __device__ __forceinline__ double block_sum_d(double v, double* red)
     return t;
 }
 
-// Arrival counter of the last-block pattern: every block publishes (a, b)
-// in pa[blk], pb[blk]; the block that arrives last sums all of them in a
-// fixed order with all its threads and returns true (totals in A, B).
-__device__ __forceinline__ bool last_block_reduce(unsigned int* cnt, unsigned int nblk, double* pa,
-                                                  double* pb, int blk, float a, float b,
-                                                  double& A_out, double& B_out)
+// Reductions over a projection without inter-block synchronisation: each
+// block stores its pair of block sums in its slot of pa / pb (thread 0 holds
+// them after block_sum2), with no fence and no arrival counter.  One block of
+// a later kernel on the same stream, which sees every slot once its grid
+// dependency wait returns, adds the slots in a fixed order (a strided walk,
+// then a block tree: the same bits on every run for a given block size).
+__device__ __forceinline__ void store_partials(double* pa, double* pb, float a, float b)
 {
-    __shared__ int s_last;
-    __shared__ double s_red[32];
     if (threadIdx.x == 0) {
-        pa[blk] = (double)a;
-        pb[blk] = (double)b;
-        __threadfence();
-        const unsigned int prev = atomicAdd(cnt, 1u);
-        s_last = (prev == nblk - 1u);
+        pa[blockIdx.x] = (double)a;
+        if (pb) pb[blockIdx.x] = (double)b;
     }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
+}
+
+// Every thread of the block calls it; the totals reach every thread.
+__device__ __forceinline__ void sum_partials(const double* pa, const double* pb, int n, double& A_out,
+                                             double& B_out)
+{
+    __shared__ double s_red[32];
     double sa = 0.0, sb = 0.0;
-    for (unsigned int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
         sa += __ldcg(&pa[i]);
-        sb += __ldcg(&pb[i]);
+        if (pb) sb += __ldcg(&pb[i]);
     }
     A_out = block_sum_d(sa, s_red);
-    B_out = block_sum_d(sb, s_red);
-    if (threadIdx.x == 0) *cnt = 0u;
-    return true;
+    B_out = pb ? block_sum_d(sb, s_red) : 0.0;
+}
+
+// kappa of iteration `it` from the n partials of the inverse row pass: the
+// relative update |dT| / |T'|.  Records it, the iteration count and, at or
+// below tol, the projection's convergence flag.  Every thread of the block
+// calls it; the flag is visible to the whole block on return.
+__device__ __forceinline__ void finalize_kappa(EprProjState* st, const double* pa, const double* pb, int n,
+                                               double* hist, int hist_len, int it, float tol)
+{
+    double sa, sb;
+    sum_partials(pa, pb, n, sa, sb);
+    if (threadIdx.x == 0) {
+        const double kap = sb > 0.0 ? sqrt(sa / sb) : sqrt(sa);
+        st->kappa = (float)kap;
+        st->iters = it + 1;
+        if (hist && it < hist_len) hist[it] = kap;
+        if (tol > 0.f && kap <= (double)tol) st->done = 1;
+    }
+    __syncthreads();
+}
+
+// rho of iteration `it` from the n partials of the forward row pass:
+// |D - P| / |D|.  Every thread of the block calls it.
+__device__ __forceinline__ void finalize_rho(EprProjState* st, const double* pa, int n, double* hist,
+                                             int hist_len, int it)
+{
+    double sa, sb;
+    sum_partials(pa, nullptr, n, sa, sb);
+    if (threadIdx.x == 0) {
+        const double dn = st->dnorm2;
+        const double rho = dn > 0.0 ? sqrt(sa / dn) : sqrt(sa);
+        st->rho = (float)rho;
+        if (hist && it < hist_len) hist[it] = rho;
+    }
 }
 
 // Programmatic dependent launch.  A kernel launched with the programmatic

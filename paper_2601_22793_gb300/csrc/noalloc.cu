@@ -39,12 +39,12 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 // launchers of the preconditioner passes (rowfft.cu, colfft.cu)
 cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
                                const float* D, const float* G, int line0, int nl, int it,
-                               int batch, int check_done, cudaStream_t stream);
+                               float tol, int batch, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, float* Out,
                                int line0, int nl, int it, float omega, float eps, float tol,
                                int batch, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int nl, int batch,
-                           int check_done, int cw_hint, cudaStream_t stream);
+                           int check_done, int cw_hint, int rho_it, cudaStream_t stream);
 cudaError_t epr_row_init();
 cudaError_t epr_col_init();
 
@@ -144,8 +144,8 @@ extern "C" epr_status epr_precondition_noalloc(float* g, int nx, int ny, double 
     k_noalloc_twiddles<<<(ny + 255) / 256, 256, 0, s>>>(tw_y, ny);
     epr_count_launch(2);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = epr_launch_row_fwd(C, W, 2, nullptr, nullptr, g, 0, 1, 0, batch, 0, s);
-    if (e == cudaSuccess) e = epr_launch_col(C, W, 0, 1, batch, 0, 0, s);
+    if (e == cudaSuccess) e = epr_launch_row_fwd(C, W, 2, nullptr, nullptr, g, 0, 1, 0, 0.f, batch, 0, s);
+    if (e == cudaSuccess) e = epr_launch_col(C, W, 0, 1, batch, 0, 0, -1, s);
     if (e == cudaSuccess) e = epr_launch_row_inv(C, W, 1, g, 0, 1, 0, 1.f, 0.f, 0.f, batch, 0, s);
     return e == cudaSuccess ? EPR_OK : EPR_ERR_CUDA;
 }

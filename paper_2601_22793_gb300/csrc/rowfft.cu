@@ -14,8 +14,8 @@
 //   epilogue  unpack X0[k] = (Z[k] + conj Z[-k]) / 2, X1[k] = (Z[k] -
 //             conj Z[-k]) / 2i and store k < nx/2 with the real Nyquist
 //             value packed into the imaginary part of k = 0.
-// The block also adds its share of |D - P|^2; the last block of a projection
-// reduces the shares in a fixed order (deterministic) into rho.
+// The block also stores its share of |D - P|^2; block 0 of the column pass
+// that follows adds the shares in a fixed order (deterministic) into rho.
 //
 // Inverse row pass (C2R), the mirror image, fused with the update
 // ("Iterative inversion"): per line, I'_s = max(I_s + omega h_s, eps f_s),
@@ -23,8 +23,10 @@
 //   T' = - sum_s f_s mu_s ln(I'_s / f_s) / sum_s f_s mu_s^2,
 // evaluated as T' = T - sum_s w_s ln(1 + omega h_s / I_s) (w_s = f_s mu_s /
 // sum f mu^2), the same quantity without forming exp then log of values
-// near one.  The last block of a projection reduces |T' - T|^2 and |T'|^2
-// into kappa and retires the projection when kappa <= tol.
+// near one.  Each block stores its shares of |T' - T|^2 and |T'|^2; block 0
+// of the next forward row pass (or a one-block kernel after the last
+// iteration) adds them in a fixed order into kappa and retires the
+// projection when kappa <= tol.
 #include "epr_internal.cuh"
 #include "fft.cuh"
 
@@ -54,16 +56,33 @@ struct RowArgs {
     float* Out;              // [B][ny][nx] real output (INV_STORE) or T (INV_UPDATE)
     float2* S;               // [B][nl][ny][nx/2]
     EprProjState* st;
-    double* part_a;
+    double* part_a;          // [B][max_blocks] inverse pass partials (kappa)
     double* part_b;
-    double* hist;            // rho (forward) or kappa (inverse) history
+    double* part_c;          // [B][max_blocks] forward pass partials (rho)
+    double* hist;            // kappa history (finalised by the forward pass)
     const float2* tw;        // exp(-2 pi i t / nx)
     int RP, lgRP;            // row pairs per block
     int line0, nl;           // first physical line, number of lines handled
     int it, hist_len, max_blocks;
     int check_done;
+    int fin;                 // forward: block 0 finalises kappa of iteration it - 1
     float omega, eps, tol;
 };
+
+// Block 0 of a forward solve pass (line 0) turns the inverse pass's
+// partials of the previous iteration into kappa, the iteration count and
+// the convergence flag, unless the projection had already converged; the
+// grid dependency wait has made every partial visible.  The other blocks of
+// this pass may not see the flag: a projection that converges here runs this
+// pass and the splat before it once more, which changes nothing it keeps.
+__device__ __forceinline__ void fwd_finalize_kappa(const RowArgs& A, int b, bool lead)
+{
+    if (A.fin && lead && !A.st[b].done)
+        finalize_kappa(&A.st[b], A.part_a + (size_t)b * A.max_blocks,
+                       A.part_b + (size_t)b * A.max_blocks, (int)gridDim.x,
+                       A.hist ? A.hist + (size_t)b * A.hist_len : nullptr, A.hist_len, A.it - 1,
+                       A.tol);
+}
 
 __device__ __forceinline__ int fdiv(int i, float inv_d) { return (int)(((float)i + 0.5f) * inv_d); }
 
@@ -154,6 +173,7 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
         cp_async_commit();
     }
     epr_grid_wait();
+    if constexpr (MODE != FWD_LOAD) fwd_finalize_kappa(A, b, blockIdx.x == 0);
     if (A.check_done && A.st[b].done) {
         cp_async_wait_all();   // no copy may land after the block has left
         return;
@@ -235,19 +255,10 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
         __syncthreads();
     }
 
-    if constexpr (MODE != FWD_LOAD) {
+    if constexpr (MODE != FWD_LOAD) {   // |D - P|^2 partials; rho is formed by the column pass
         float rb = 0.f;
         block_sum2(ra, rb, red);
-        double sa, sb;
-        if (last_block_reduce(&A.st[b].cnt_fwd, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
-                              A.part_b + (size_t)b * A.max_blocks, blockIdx.x, ra, rb, sa, sb)) {
-            if (threadIdx.x == 0) {
-                const double dn = A.st[b].dnorm2;
-                const double rho = dn > 0.0 ? sqrt(sa / dn) : sqrt(sa);
-                A.st[b].rho = (float)rho;
-                if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = rho;
-            }
-        }
+        store_partials(A.part_c + (size_t)b * A.max_blocks, nullptr, ra, rb);
     }
 }
 
@@ -372,18 +383,9 @@ __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const Row
                 db += n0 * n0 + n1 * n1;
             }
         }
-        block_sum2(da, db, red);
-        double sa, sb;
-        if (last_block_reduce(&A.st[b].cnt_inv, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
-                              A.part_b + (size_t)b * A.max_blocks, blockIdx.x, da, db, sa, sb)) {
-            if (threadIdx.x == 0) {
-                const double kap = sb > 0.0 ? sqrt(sa / sb) : sqrt(sa);
-                A.st[b].kappa = (float)kap;
-                A.st[b].iters = A.it + 1;
-                if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = kap;
-                if (A.tol > 0.f && kap <= (double)A.tol) A.st[b].done = 1;
-            }
-        }
+        block_sum2(da, db, red);   // kappa partials, finalised by the next forward pass
+        store_partials(A.part_a + (size_t)b * A.max_blocks, A.part_b + (size_t)b * A.max_blocks, da,
+                       db);
     }
 }
 
@@ -466,6 +468,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
         cp_async_commit();
     }
     epr_grid_wait();
+    fwd_finalize_kappa(A, b, blockIdx.x == 0 && sl == 0);
     if (A.check_done && A.st[b].done) {
         cp_async_wait_all();   // no copy may land after the block has left
         return;
@@ -567,17 +570,8 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     }
     if (POLY && sl != 0) return;   // the residual norm is line 0's
     float rb = 0.f;
-    block_sum2(ra, rb, red);
-    double sa, sb;
-    if (last_block_reduce(&A.st[b].cnt_fwd, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
-                          A.part_b + (size_t)b * A.max_blocks, blockIdx.x, ra, rb, sa, sb)) {
-        if (threadIdx.x == 0) {
-            const double dn = A.st[b].dnorm2;
-            const double rho = dn > 0.0 ? sqrt(sa / dn) : sqrt(sa);
-            A.st[b].rho = (float)rho;
-            if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = rho;
-        }
-    }
+    block_sum2(ra, rb, red);   // |D - P|^2 partials; rho is formed by the column pass
+    store_partials(A.part_c + (size_t)b * A.max_blocks, nullptr, ra, rb);
 }
 
 // five 256-thread blocks per SM (51 registers): its shared memory is the FFT
@@ -652,18 +646,8 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
         da += l0 * l0 + l1 * l1;
         db += n0 * n0 + n1 * n1;
     }
-    block_sum2(da, db, red);
-    double sa, sb;
-    if (last_block_reduce(&A.st[b].cnt_inv, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
-                          A.part_b + (size_t)b * A.max_blocks, blockIdx.x, da, db, sa, sb)) {
-        if (threadIdx.x == 0) {
-            const double kap = sb > 0.0 ? sqrt(sa / sb) : sqrt(sa);
-            A.st[b].kappa = (float)kap;
-            A.st[b].iters = A.it + 1;
-            if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = kap;
-            if (A.tol > 0.f && kap <= (double)A.tol) A.st[b].done = 1;
-        }
-    }
+    block_sum2(da, db, red);   // kappa partials, finalised by the next forward pass
+    store_partials(A.part_a + (size_t)b * A.max_blocks, A.part_b + (size_t)b * A.max_blocks, da, db);
 }
 
 // Polychromatic update on the compile-time engine: for each line, the C2R
@@ -756,18 +740,8 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
         da += l0 * l0 + l1 * l1;
         db += n0 * n0 + n1 * n1;
     }
-    block_sum2(da, db, red);
-    double sa, sb;
-    if (last_block_reduce(&A.st[b].cnt_inv, gridDim.x, A.part_a + (size_t)b * A.max_blocks,
-                          A.part_b + (size_t)b * A.max_blocks, blockIdx.x, da, db, sa, sb)) {
-        if (threadIdx.x == 0) {
-            const double kap = sb > 0.0 ? sqrt(sa / sb) : sqrt(sa);
-            A.st[b].kappa = (float)kap;
-            A.st[b].iters = A.it + 1;
-            if (A.hist && A.it < A.hist_len) A.hist[(size_t)b * A.hist_len + A.it] = kap;
-            if (A.tol > 0.f && kap <= (double)A.tol) A.st[b].done = 1;
-        }
-    }
+    block_sum2(da, db, red);   // kappa partials, finalised by the next forward pass
+    store_partials(A.part_a + (size_t)b * A.max_blocks, A.part_b + (size_t)b * A.max_blocks, da, db);
 }
 
 // dynamic shared memory of k_row_fwd_mono: FFT rows aliased with the
@@ -882,18 +856,22 @@ EprRowLaunch epr_row_config(const EprConsts& C)
 
 // mode: 0 = non-local solve, 1 = local solve, 2 = load real map G.
 // FWD_SOLVE_NL reads the residual D - P from P and the split residuals from P_s.
+// In a solve (it > 0) block 0 also finalises kappa of iteration it - 1
+// against tol.
 cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
                                const float* D, const float* G, int line0, int nl, int it,
-                               int batch, int check_done, cudaStream_t stream)
+                               float tol, int batch, int check_done, cudaStream_t stream)
 {
     const EprRowLaunch L = epr_row_config(C);
     RowArgs A = {};
     A.T = T; A.D = D; A.G = G;
     A.P = W.P; A.Ps = W.Ps; A.Pq = W.Pq; A.Psq = W.Psq;
-    A.S = W.S; A.st = W.st; A.part_a = W.part_a; A.part_b = W.part_b;
-    A.hist = W.rho_hist; A.hist_len = W.hist_len; A.max_blocks = W.max_blocks;
+    A.S = W.S; A.st = W.st; A.part_a = W.part_a; A.part_b = W.part_b; A.part_c = W.part_c;
+    A.hist = W.kappa_hist; A.hist_len = W.hist_len; A.max_blocks = W.max_blocks;
     A.tw = W.tw_x; A.RP = L.RP; A.lgRP = L.lgRP; A.line0 = line0; A.nl = nl; A.it = it;
     A.check_done = check_done;
+    A.fin = mode != FWD_LOAD && it > 0;
+    A.tol = tol;
     const dim3 grid(C.ny / (2 * L.RP), batch), blk(L.threads);
     const bool mono = nl == 1, pdl = C.pdl != 0;
     cudaError_t e = cudaSuccess;
@@ -923,7 +901,7 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
     const EprRowLaunch L = epr_row_config(C);
     RowArgs A = {};
     A.Out = Out; A.S = W.S; A.st = W.st; A.part_a = W.part_a; A.part_b = W.part_b;
-    A.hist = W.kappa_hist; A.hist_len = W.hist_len; A.max_blocks = W.max_blocks;
+    A.hist_len = W.hist_len; A.max_blocks = W.max_blocks;
     A.tw = W.tw_x; A.RP = L.RP; A.lgRP = L.lgRP; A.line0 = line0; A.nl = nl; A.it = it;
     A.omega = omega; A.eps = eps; A.tol = tol; A.check_done = check_done;
     const dim3 grid(C.ny / (2 * L.RP), batch), blk(L.threads);
@@ -952,6 +930,38 @@ cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* 
     k_sumsq_final<<<batch, 32, 0, stream>>>(W.part_a, parts, W.max_blocks, scale, W.st);
     epr_count_launch(2);
     return cudaGetLastError();
+}
+
+// Blocks of a row pass (the number of partials a reduction adds up).
+int epr_row_blocks(const EprConsts& C) { return C.ny / (2 * epr_row_config(C).RP); }
+
+namespace {
+
+// kappa of the last iteration of a solve (the forward pass of a following
+// iteration finalises the others): one block per projection.
+__global__ void __launch_bounds__(256) k_finalize_kappa(EprProjState* st, const double* part_a,
+                                                        const double* part_b, int max_blocks,
+                                                        int nblk, double* hist, int hist_len,
+                                                        int it, float tol)
+{
+    const int b = blockIdx.x;
+    epr_grid_wait();
+    if (st[b].done) return;   // converged earlier: the partials are stale
+    finalize_kappa(&st[b], part_a + (size_t)b * max_blocks, part_b + (size_t)b * max_blocks, nblk,
+                   hist ? hist + (size_t)b * hist_len : nullptr, hist_len, it, tol);
+}
+
+}  // namespace
+
+cudaError_t epr_launch_finalize_kappa(const EprConsts& C, const EprWork& W, int it, float tol,
+                                      int batch, cudaStream_t stream)
+{
+    const cudaError_t e =
+        epr_launch_kernel(C.pdl != 0, k_finalize_kappa, dim3(batch), dim3(256), 0, stream, W.st,
+                          (const double*)W.part_a, (const double*)W.part_b, W.max_blocks,
+                          epr_row_blocks(C), W.kappa_hist, W.hist_len, it, tol);
+    epr_count_launch(1);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t epr_row_init()
