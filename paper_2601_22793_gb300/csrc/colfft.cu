@@ -270,7 +270,7 @@ k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMa
         for (int i = 0; i < BOXES; ++i)
             epr_tma::store_2d(&map, 2 * kx0, row0 + i * BOXY, buf + i * BOXY * CW);
         epr_tma::bulk_commit();
-        epr_tma::bulk_wait_all();
+        epr_tma::bulk_wait_read_all();   // the tile must outlive the copy's reads
     }
 }
 

@@ -84,7 +84,12 @@ __device__ __forceinline__ void store_2d(const CUtensorMap* map, int x, int y, c
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
-// wait until every committed bulk group of this thread has completed
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// wait until every committed bulk group of this thread has finished reading
+// its shared-memory source (the writes complete on their own; the end of the
+// grid makes them visible to later grids)
+__device__ __forceinline__ void bulk_wait_read_all()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
 
 }  // namespace epr_tma
