@@ -47,7 +47,7 @@ typedef enum {
     EPR_ERR_UNSUPPORTED_SIZE = 2, /* nx or ny not 2^a 3^b in [16, 4096]  */
     EPR_ERR_OOM = 3,              /* device allocation failed           */
     EPR_ERR_CUDA = 4,             /* a CUDA runtime or launch error     */
-    EPR_ERR_NONFINITE = 5,        /* NaN or Inf in an input map         */
+    EPR_ERR_NONFINITE = 5,        /* NaN or Inf in the data D of a solve */
     EPR_ERR_TIMEOUT = 6,          /* a bounded device wait on a bulk copy ran out */
     EPR_ERR_NOT_CONVERGED = 7,    /* reserved                           */
     EPR_ERR_SHIFT_OVERFLOW = 8    /* more large-shift sources than the overflow list holds */
@@ -178,7 +178,10 @@ epr_status epr_precondition(epr_plan_t plan, float* g, int line, int batch, void
  * preconditioner, relaxed update floored at eps_I f_s and least-squares
  * projection onto one thickness (Eq. 7).  T is the initial thickness when
  * opts->init = 1 and receives the result.  info may be NULL; when it is not,
- * the call synchronises the stream and fills it. */
+ * the call synchronises the stream and fills it, and returns
+ * EPR_ERR_NONFINITE when D holds a NaN or an infinity (the result is then
+ * meaningless) and EPR_ERR_SHIFT_OVERFLOW when an overflow list overfilled.
+ * Without info the same conditions are read by epr_check_device_status. */
 epr_status epr_solve_nonlocal(epr_plan_t plan, const float* D, float* T, int batch,
                               const epr_solve_opts* opts, epr_solve_info* info, void* stream);
 
@@ -188,8 +191,10 @@ epr_status epr_solve_local(epr_plan_t plan, const float* D, float* T, int batch,
                            const epr_solve_opts* opts, epr_solve_info* info, void* stream);
 
 /* Synchronise `stream`, read and clear the plan's device error word:
- * EPR_ERR_SHIFT_OVERFLOW if a splat since the last check overfilled its
- * overflow list (its prediction then lacks those sources), else EPR_OK. */
+ * EPR_ERR_NONFINITE if the data of a solve since the last check held a NaN or
+ * an infinity, EPR_ERR_TIMEOUT if a bounded device wait on a bulk copy ran
+ * out, EPR_ERR_SHIFT_OVERFLOW if a splat overfilled its overflow list (its
+ * prediction then lacks those sources), else EPR_OK (first match wins). */
 epr_status epr_check_device_status(epr_plan_t plan, void* stream);
 
 /* Paganin-type preconditioner of one line without a plan and without any

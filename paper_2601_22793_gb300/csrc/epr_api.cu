@@ -444,6 +444,7 @@ epr_status collect_info(epr_plan_s* p, int batch, int n_iter, epr_solve_info* in
     }
     if (first == 0) info->overflow_sources = 0;
     info->overflow_sources += ovf;
+    if (herr & EPR_DEVERR_NONFINITE) return EPR_ERR_NONFINITE;
     if (herr & EPR_DEVERR_TIMEOUT) return EPR_ERR_TIMEOUT;
     if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
     return EPR_OK;
@@ -955,6 +956,7 @@ epr_status epr_check_device_status(epr_plan_t p, void* stream)
     EPR_TRY(cudaMemcpyAsync(&herr, p->W.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     EPR_TRY(cudaMemsetAsync(p->W.err, 0, sizeof(unsigned int), s));
     EPR_TRY(cudaStreamSynchronize(s));
+    if (herr & EPR_DEVERR_NONFINITE) return EPR_ERR_NONFINITE;
     if (herr & EPR_DEVERR_TIMEOUT) return EPR_ERR_TIMEOUT;
     if (herr & EPR_DEVERR_OVERFLOW) return EPR_ERR_SHIFT_OVERFLOW;
     return EPR_OK;

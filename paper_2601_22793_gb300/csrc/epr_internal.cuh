@@ -15,6 +15,7 @@
 // Device-side error bits (OR-ed into the plan's error word).
 #define EPR_DEVERR_OVERFLOW 1u
 #define EPR_DEVERR_TIMEOUT 2u    // a bounded wait on a bulk copy gave up
+#define EPR_DEVERR_NONFINITE 4u  // NaN or Inf in the data of a solve
 
 // Fixed-point scale of the deterministic splat: value * 2^40.
 #define EPR_FX_SCALE 1099511627776.0f

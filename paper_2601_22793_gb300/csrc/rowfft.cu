@@ -407,14 +407,17 @@ __global__ void __launch_bounds__(256) k_sumsq_part(const float* __restrict__ D,
     if (threadIdx.x == 0) part[(size_t)b * max_blocks + blockIdx.x] = (double)a;
 }
 
+// A NaN or an infinity anywhere in D makes the sum non-finite (finite float
+// squares cannot overflow a double sum): flagged in the device error word.
 __global__ void k_sumsq_final(const double* part, int nparts, int max_blocks, double scale,
-                              EprProjState* st)
+                              EprProjState* st, unsigned int* err)
 {
     const int b = blockIdx.x;
     if (threadIdx.x != 0) return;
     double s = 0.0;
     for (int i = 0; i < nparts; ++i) s += part[(size_t)b * max_blocks + i];
     st[b].dnorm2 = s * scale;
+    if (!isfinite(s)) atomicOr(err, EPR_DEVERR_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -927,7 +930,7 @@ cudaError_t epr_launch_dnorm(const EprConsts& C, const EprWork& W, const float* 
 {
     const int parts = W.max_blocks < 64 ? W.max_blocks : 64;
     k_sumsq_part<<<dim3(parts, batch), 256, 0, stream>>>(D, npix, W.part_a, W.max_blocks);
-    k_sumsq_final<<<batch, 32, 0, stream>>>(W.part_a, parts, W.max_blocks, scale, W.st);
+    k_sumsq_final<<<batch, 32, 0, stream>>>(W.part_a, parts, W.max_blocks, scale, W.st, W.err);
     epr_count_launch(2);
     return cudaGetLastError();
 }

@@ -342,6 +342,31 @@ def test_solve_tolerance_stops_like_the_oracle(torch, E, oracle):
     assert rel(host(T), Tr) < 1e-4
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_nonfinite_data_is_reported(torch, E, oracle, bad):
+    """A NaN or an infinity in D is reported as EPR_ERR_NONFINITE: by the solve
+    when it fills info, else by the device status check, which then clears."""
+    wl, ln, D = _spheres_data(oracle)
+    Dbad = D.copy()
+    Dbad[100, 37] = bad
+    with plan_of(E, wl) as p:
+        T = torch.empty(D.shape, device="cuda")
+        with pytest.raises(E.EprError) as ex:
+            E.epr_solve_nonlocal(p.handle, cuda(torch, Dbad), T, n_iter=3, omega=wl.omega)
+        assert ex.value.status == 5
+        with pytest.raises(E.EprError) as ex:        # the word still holds it: read and clear
+            E.epr_check_device_status(p.handle)
+        assert ex.value.status == 5
+        E.epr_check_device_status(p.handle)          # cleared
+        E.epr_solve_nonlocal(p.handle, cuda(torch, Dbad), T, n_iter=3, omega=wl.omega,
+                             want_info=False)
+        with pytest.raises(E.EprError) as ex:
+            E.epr_check_device_status(p.handle)
+        assert ex.value.status == 5
+        info = E.epr_solve_nonlocal(p.handle, cuda(torch, D), T, n_iter=3, omega=wl.omega)
+        assert info["iters"][0] == 3 and np.isfinite(host(T)).all()
+
+
 def test_batch_equals_single_projections(torch, E, oracle):
     wl, T32 = small_poly(seed=11)
     ln = lines_of(oracle, wl)
