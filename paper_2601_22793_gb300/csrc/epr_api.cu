@@ -222,6 +222,7 @@ epr_status ensure_workspace(epr_plan_s* p, int batch, int hist)
     if (e == cudaSuccess) e = dalloc(p, &W.S, (size_t)nb * C.ns * C.ny * C.half);
     if (e == cudaSuccess) e = dalloc(p, &W.ovf_idx, (size_t)nb * C.ovf_cap);
     if (e == cudaSuccess) e = dalloc(p, &W.ovf_mask, (size_t)nb * C.ovf_cap);
+    if (e == cudaSuccess) e = dalloc(p, &W.ovf_tg, (size_t)nb * C.ovf_cap);
     if (e == cudaSuccess) e = dalloc(p, &W.st, (size_t)nb);
     if (e == cudaSuccess) e = dalloc(p, &W.part_a, (size_t)nb * W.max_blocks);
     if (e == cudaSuccess) e = dalloc(p, &W.part_b, (size_t)nb * W.max_blocks);

@@ -64,6 +64,7 @@ struct EprWork {
     float2* S;           // [B][ns][ny][nx/2] packed half spectrum
     int* ovf_idx;        // [B][cap] source pixel index
     unsigned int* ovf_mask;   // [B][cap] lines that took the overflow path
+    float4* ovf_tg;      // [B][cap] T and twice its gradient (x, y) at the source
     EprProjState* st;    // [B]
     double* part_a;      // [B][max_blocks] block partial sums of the inverse
     double* part_b;      // [B][max_blocks]    row pass (kappa)

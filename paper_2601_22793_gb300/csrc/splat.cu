@@ -58,6 +58,7 @@ struct SplatArgs {
     unsigned long long* Psq;
     int* ovf_idx;
     unsigned int* ovf_mask;
+    float4* ovf_tg;          // (T, twice the gradient x, y, 0) of each entry
     EprProjState* st;
     unsigned int* err;
     int parity;
@@ -222,6 +223,7 @@ k_splat(const EprConsts C, const SplatArgs A)
                 if (gpos < C.ovf_cap) {
                     A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = sy * nx + sx;
                     A.ovf_mask[(size_t)b * C.ovf_cap + gpos] = far;
+                    A.ovf_tg[(size_t)b * C.ovf_cap + gpos] = make_float4(t, gx2, gy2, 0.f);
                 } else {
                     atomicOr(A.err, EPR_DEVERR_OVERFLOW);
                 }
@@ -269,7 +271,9 @@ k_splat(const EprConsts C, const SplatArgs A)
     __syncthreads();
     epr_grid_release();
 
-    // far sources of this block: one reservation in the global list
+    // far sources of this block: one reservation in the global list.  Each
+    // entry carries T and twice the gradient, formed from the staged window
+    // as in the scan (the same bits), so the overflow kernel reads no T.
     const int nfar = s_far_n < kFarList ? s_far_n : kFarList;
     if (nfar > 0) {
         if (tid == 0) s_far_base = atomicAdd(&A.st[b].ovf_count[A.parity], nfar);
@@ -277,8 +281,22 @@ k_splat(const EprConsts C, const SplatArgs A)
         for (int e = tid; e < nfar; e += kSplatThreads) {
             const int gpos = s_far_base + e;
             if (gpos < C.ovf_cap) {
-                A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = s_far_idx[e];
+                const int pix = s_far_idx[e];
+                const int sy = pix / nx, sx = pix - sy * nx;
+                const int ly = sy - ty0 + R, lx = sx - tx0 + R;   // in the source region
+                const float* tp = Ts + (ly + 1) * SWa + (lx + 1 + coff);
+                const float t = tp[0];
+                float gx2, gy2;
+                if (interior) {
+                    gx2 = tp[1] - tp[-1];
+                    gy2 = tp[SWa] - tp[-SWa];
+                } else {
+                    gx2 = 2.f * grad1(tp[-1], t, tp[1], sx, nx);
+                    gy2 = 2.f * grad1(tp[-SWa], t, tp[SWa], sy, ny);
+                }
+                A.ovf_idx[(size_t)b * C.ovf_cap + gpos] = pix;
                 A.ovf_mask[(size_t)b * C.ovf_cap + gpos] = s_far_mask[e];
+                A.ovf_tg[(size_t)b * C.ovf_cap + gpos] = make_float4(t, gx2, gy2, 0.f);
             } else {
                 atomicOr(A.err, EPR_DEVERR_OVERFLOW);
             }
@@ -349,18 +367,30 @@ __global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const
         A.st[b].ovf_count[A.parity ^ 1] = 0;   // the next splat's slot
         if (cnt > 0) A.st[b].ovf_total += cnt;
     }
-    const float* Tb = A.T + (size_t)b * npix;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
-        const int pix = A.ovf_idx[(size_t)b * C.ovf_cap + e];
-        const unsigned int mask = A.ovf_mask[(size_t)b * C.ovf_cap + e];
+    // entries come with T and twice the gradient; the first round's entry is
+    // loaded together with the count (every slot below the capacity exists)
+    const int stride = gridDim.x * blockDim.x;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int pix = 0;
+    unsigned int mask = 0u;
+    float4 tg = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < C.ovf_cap) {
+        pix = A.ovf_idx[(size_t)b * C.ovf_cap + e];
+        mask = A.ovf_mask[(size_t)b * C.ovf_cap + e];
+        tg = A.ovf_tg[(size_t)b * C.ovf_cap + e];
+    }
+    for (; e < cnt; e += stride) {
+        if (e >= stride) {   // later rounds
+            pix = A.ovf_idx[(size_t)b * C.ovf_cap + e];
+            mask = A.ovf_mask[(size_t)b * C.ovf_cap + e];
+            tg = A.ovf_tg[(size_t)b * C.ovf_cap + e];
+        }
         const int sy = pix / nx, sx = pix - sy * nx;
-        const float* tp = Tb + pix;
-        const float t = tp[0];
-        const float gx = grad1(sx > 0 ? tp[-1] : t, t, sx < nx - 1 ? tp[1] : t, sx, nx);
-        const float gy = grad1(sy > 0 ? tp[-nx] : t, t, sy < ny - 1 ? tp[nx] : t, sy, ny);
+        const float t = tg.x;
         for (int s = 0; s < ns; ++s) {
             if (!((mask >> s) & 1u)) continue;
-            const float ux = C.c[s] * gx, uy = C.c[s] * gy;
+            const float ch = 0.5f * C.c[s];
+            const float ux = ch * tg.y, uy = ch * tg.z;
             const float fx = floorf(ux), fy = floorf(uy);
             const float dx = ux - fx, dy = uy - fy;
             const float m = C.f[s] * __expf(-C.mu[s] * t);
@@ -589,6 +619,7 @@ cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* 
     A.Psq = W.Psq;
     A.ovf_idx = W.ovf_idx;
     A.ovf_mask = W.ovf_mask;
+    A.ovf_tg = W.ovf_tg;
     A.st = W.st;
     A.err = W.err;
     A.parity = parity & 1;
