@@ -577,7 +577,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     store_partials(A.part_c + (size_t)b * A.max_blocks, nullptr, ra, rb);
 }
 
-// five 256-thread blocks per SM (51 registers): its shared memory is the FFT
+// five 256-thread blocks per SM (48 registers): its shared memory is the FFT
 // rows and 2 RP thickness rows only (row_inv_mono_smem)
 template <int NX, int RP>
 __global__ void __launch_bounds__(NX * RP / kEPT, NX * RP / kEPT == 256 ? 5 : (65536 / 64) / (NX * RP / kEPT))

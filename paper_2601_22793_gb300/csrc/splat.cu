@@ -33,8 +33,9 @@
 //    monochromatic float solve the flush stores the residual D - P instead
 //    of P (the adjoint gather then reads one value per corner).
 //  * A source-line with |u| > reach in either axis (or T below the bound
-//    above) is never splatted by the scan; the block that owns the source pixel appends it (with a bit mask
-//    of its long lines) to a per-projection overflow list, and a second
+//    above) is never splatted by the scan; the block that owns the source
+//    pixel appends it (with a bit mask of its long lines, its thickness and
+//    twice its gradient) to a per-projection overflow list, and a second
 //    kernel adds those contributions with global atomics.  No mass is lost,
 //    whatever the shift.  The list fill counter alternates between two slots
 //    by iteration parity, so the overflow kernel can clear the next slot.
@@ -100,6 +101,9 @@ constexpr int kQuad = 4;   // sources per scan work item
 // 32 x 32, chosen on the host), and so is the reach RC of the float solves
 // for the reaches the tuner tries (3, 4, 6; RC = 0 takes C.smax), so every
 // tile- and reach-derived index, stride and offset folds into immediates.
+// Five blocks per SM (48 registers; a 64 x 64 tile at reach 4 takes 44 KB of
+// shared memory); the mono residual kernel with a runtime reach needs more
+// registers and runs four.
 template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0>
 __global__ void __launch_bounds__(kSplatThreads, (NS == 1 && RESID && RC == 0) ? 4 : 5)
 k_splat(const EprConsts C, const SplatArgs A)
