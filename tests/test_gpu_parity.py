@@ -342,6 +342,38 @@ def test_solve_tolerance_stops_like_the_oracle(torch, E, oracle):
     assert rel(host(T), Tr) < 1e-4
 
 
+def test_single_iteration_reports_rho_and_kappa(torch, E, oracle):
+    """One iteration: rho comes from the column pass and kappa from the kernel
+    after the loop (no later forward pass forms it); from T = 0, kappa = 1."""
+    wl, ln, D = _spheres_data(oracle)
+    Tr, info_r = oracle.solve(ln, D.astype(np.float64), n_iter=1, omega=wl.omega)
+    with plan_of(E, wl) as p:
+        T = torch.empty(D.shape, device="cuda")
+        info = E.epr_solve_nonlocal(p.handle, cuda(torch, D), T, n_iter=1, omega=wl.omega)
+    assert info["iters"][0] == 1
+    assert rel(host(T), Tr) < 1e-4
+    assert np.isclose(info["rho"][0], info_r["rho"][0], rtol=1e-4)
+    assert np.isclose(info["kappa"][0], 1.0, rtol=1e-6) and np.isclose(info_r["kappa"][0], 1.0)
+
+
+def test_convergence_on_the_last_iteration(torch, E, oracle):
+    """A solve whose tolerance is met exactly at its last allowed iteration: the
+    kernel after the loop forms that kappa and the iteration count."""
+    wl, ln, D = _spheres_data(oracle)
+    tol = 0.01
+    _, info_r = oracle.solve(ln, D.astype(np.float64), n_iter=20, omega=1.0, tol=tol)
+    k = info_r["iters"]
+    assert 2 <= k < 20
+    Tr, _ = oracle.solve(ln, D.astype(np.float64), n_iter=k, omega=1.0, tol=tol)
+    with plan_of(E, wl) as p:
+        T = torch.empty(D.shape, device="cuda")
+        info = E.epr_solve_nonlocal(p.handle, cuda(torch, D), T, n_iter=k, omega=1.0, tol=tol)
+    assert info["iters"][0] == k
+    assert info["kappa"][0] <= tol
+    assert np.isclose(info["kappa"][0], info_r["kappa"][k - 1], rtol=1e-2)
+    assert rel(host(T), Tr) < 1e-4
+
+
 @pytest.mark.parametrize("bad", [np.nan, np.inf])
 def test_nonfinite_data_is_reported(torch, E, oracle, bad):
     """A NaN or an infinity in D is reported as EPR_ERR_NONFINITE: by the solve
