@@ -594,9 +594,10 @@ def run_reference(a):
     per_solve = per_iter * wl.n_iter
     value = (rows * wl.nx / REF_PIX) / per_solve
     sample = (f"each step = 1 iteration on rows {y0}..{y0 + rows - 1} ({rows}x{wl.nx}) of the "
-              f"2048x2048 workload, scaled by pixel count and by 50 iterations")
+              f"2048x2048 workload (ms_per_step is that step), value scaled by pixel count and "
+              f"by 50 iterations")
     out = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
-           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(per_solve * 1e3, 2),
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(per_iter * 1e3, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic: seeded ellipsoid phantom, D = oracle forward + Poisson(1e4)",
            "config": {"workload": WORKLOAD, "parallelism": "host, 1 thread"},
