@@ -42,6 +42,11 @@
  *       back-transport, the preconditioner (fine grid) and the update.
  *       o = 1 is the plain solve.
  *
+ * Beyond the paper: orc_vjp (the transpose of the non-local forward model)
+ * and orc_solve_vjp (reverse mode through a fixed number of iterations of
+ * the non-local solve, for calibrating L, delta_s and beta_s) are pinned by
+ * finite differences of the oracle's own forward and solve.
+ *
  * Parity unpinned: the residual split of R5.  The paper only says the
  * weights are "positivity-weighted"; P_s / P and f_s agree at the flat-field
  * start and at every fixed point, so no fact the paper fixes tells them
@@ -812,4 +817,299 @@ void orc_bin(int nyd, int nxd, int os, const double* fine, double* det)
                 for (int b = 0; b < os; ++b) m += fine[IDX(yd * os + a, xd * os + b)];
             det[(size_t)yd * nxd + xd] = m / ((double)os * (double)os);
         }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vector-Jacobian product of the unrolled non-local solve (not in the      */
+/* paper: calibration of L, delta_s and beta_s by gradient descent through  */
+/* a fixed number of iterations of "Iteration structure", with the readings */
+/* R1-R7 of the forward solve).                                             */
+/* ------------------------------------------------------------------------ */
+
+/* out = Re F^-1[K F[in]] with the preconditioner's symbol (kind 0:
+ * K = H = mu / (mu + Ld |q|^2)) or one of its partial derivatives (kind 1:
+ * dH/dmu = Ld |q|^2 / (mu + Ld |q|^2)^2; kind 2: dH/dLd = -mu |q|^2 /
+ * (mu + Ld |q|^2)^2), periodic and normalised as orc_paganin (reading R4).
+ * K is real and even in q, so each of these operators is self-adjoint. */
+static int filter_kind(int ny, int nx, double p, double mu, double Ld, int kind,
+                       const double* in, double* out)
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    double* im = calloc(n, sizeof(double));
+    if (!im) return ORC_ENOMEM;
+    memcpy(out, in, sizeof(double) * n);
+    int st = orc_fft2(ny, nx, out, im, -1);
+    if (st == ORC_OK) {
+        for (int y = 0; y < ny; ++y) {
+            double fy = fftfreq(ny, p, y);
+            for (int x = 0; x < nx; ++x) {
+                double fx = fftfreq(nx, p, x);
+                double q2 = 4.0 * ORC_PI * ORC_PI * (fx * fx + fy * fy);
+                double d = mu + Ld * q2;
+                double K = kind == 0 ? mu / d : kind == 1 ? Ld * q2 / (d * d) : -mu * q2 / (d * d);
+                out[IDX(y, x)] *= K;
+                im[IDX(y, x)] *= K;
+            }
+        }
+        st = orc_fft2(ny, nx, out, im, +1);
+        for (size_t i = 0; i < n; ++i) out[i] /= (double)n;
+    }
+    free(im);
+    return st;
+}
+
+/* Bilinear interpolation of e at the mapped point of pixel (y, x) (the
+ * weights of orc_splat / orc_gather; corners outside the grid read 0) and
+ * its derivatives with respect to the shift components u_x, u_y (the right
+ * derivative where the point crosses an integer). */
+static void interp_du(int ny, int nx, const double* e, int y, int x, double uy, double ux,
+                      double* val, double* dux, double* duy)
+{
+    double xt = (double)x + ux, yt = (double)y + uy;
+    double fx0 = floor(xt), fy0 = floor(yt);
+    double dx = xt - fx0, dy = yt - fy0;
+    double g[4];
+    int ox[4] = {0, 1, 0, 1}, oy[4] = {0, 0, 1, 1};
+    for (int c = 0; c < 4; ++c) {
+        double cx = fx0 + ox[c], cy = fy0 + oy[c];
+        g[c] = (cx >= 0.0 && cx < (double)nx && cy >= 0.0 && cy < (double)ny)
+                   ? e[IDX((int)cy, (int)cx)]
+                   : 0.0;
+    }
+    *val = (1.0 - dx) * (1.0 - dy) * g[0] + dx * (1.0 - dy) * g[1] + (1.0 - dx) * dy * g[2] +
+           dx * dy * g[3];
+    *dux = (1.0 - dy) * (g[1] - g[0]) + dy * (g[3] - g[2]);
+    *duy = (1.0 - dx) * (g[2] - g[0]) + dx * (g[3] - g[1]);
+}
+
+/* Given Tbar = dF/dtau_N for tau_N, the thickness after n_iter iterations of
+ * the non-local solve from T0 (zeros when NULL) with data D, relaxation omega
+ * and floor eps_I (no early stop), returns dF/dT0, dF/dD, dF/ddelta_s,
+ * dF/dbeta_s and dF/dL (each output may be NULL).  The iterates are stored
+ * and every iteration is undone in reverse order, step by step against its
+ * forward (the solver above, with the split of R5, the floor of R7 and the
+ * projection of R6):
+ *   tau' = -num / den, num = sum_s f_s mu_s ln(I'_s / f_s), den = sum_s f_s mu_s^2;
+ *   I'_s = max(I_s + omega h_s, eps_I f_s) (no gradient through the floor);
+ *   h_s = F^-1 H_s F g_s (self-adjoint; H_s depends on mu_s and L delta_s);
+ *   g_s = M_s^* r_s: r_s receives the splat of the adjoint of g_s, the shift
+ *     the derivative of the bilinear interpolation of r_s;
+ *   r_s = r P_s / P (P > 1e-30, else r f_s), r = D - P, P = sum_s P_s;
+ *   P_s = M_s[I_s]: I_s receives the gather, the shift I_s times the
+ *     derivative of the interpolation of the adjoint of P_s;
+ *   I_s = f_s exp(-mu_s tau), u_s = c_s G[tau], c_s = -L delta_s / p^2,
+ *   mu_s = 2 k_s beta_s. */
+int orc_solve_vjp(int ny, int nx, double p, double L, int n_lines, const double* E_keV,
+                  const double* delta, const double* beta, const double* weights,
+                  const double* D, const double* T0, int n_iter, double omega, double eps_I,
+                  const double* Tbar_N, double* T0_bar, double* D_bar, double* delta_bar,
+                  double* beta_bar, double* L_bar)
+{
+    if (ny < 3 || nx < 3 || n_iter < 0) return ORC_EINVAL;
+    orc_lines ln;
+    int st = lines_init(&ln, n_lines, E_keV, delta, beta, weights, L, p);
+    const size_t n = (size_t)nx * (size_t)ny;
+    const int ns = n_lines;
+    const size_t nsn = (size_t)(ns > 0 ? ns : 1) * n;
+    double* Ts = alloc_n((size_t)(n_iter + 1) * n);
+    double *gy = alloc_n(n), *gx = alloc_n(n), *uy = alloc_n(n), *ux = alloc_n(n),
+           *Iw = alloc_n(n), *Pl = alloc_n(n), *P = alloc_n(n), *r = alloc_n(n),
+           *num = alloc_n(n), *tb = alloc_n(n), *tn = alloc_n(n), *Pbar = alloc_n(n),
+           *rbar = alloc_n(n), *vx = alloc_n(n), *vy = alloc_n(n), *hb = alloc_n(n),
+           *gb = alloc_n(n), *tmp = alloc_n(n), *Db = alloc_n(n);
+    double *Ps = alloc_n(nsn), *Is = alloc_n(nsn), *rs = alloc_n(nsn), *ga = alloc_n(nsn),
+           *In = alloc_n(nsn), *rsb = alloc_n(nsn), *uxb = alloc_n(nsn), *uyb = alloc_n(nsn),
+           *Isb = alloc_n(nsn), *Psb = alloc_n(nsn);
+    double *mub = calloc((size_t)(ns > 0 ? ns : 1), sizeof(double)),
+           *Ldb = calloc((size_t)(ns > 0 ? ns : 1), sizeof(double)),
+           *cb = calloc((size_t)(ns > 0 ? ns : 1), sizeof(double));
+    if (st == ORC_OK &&
+        (!Ts || !gy || !gx || !uy || !ux || !Iw || !Pl || !P || !r || !num || !tb || !tn ||
+         !Pbar || !rbar || !vx || !vy || !hb || !gb || !tmp || !Db || !Ps || !Is || !rs ||
+         !ga || !In || !rsb || !uxb || !uyb || !Isb || !Psb || !mub || !Ldb || !cb))
+        st = ORC_ENOMEM;
+    double den = 0.0;
+    for (int s = 0; st == ORC_OK && s < ns; ++s) den += ln.f[s] * ln.mu[s] * ln.mu[s];
+    if (st == ORC_OK && !(den > 0.0)) st = ORC_EINVAL;
+
+    /* forward: every iterate, by the solver itself (one iteration per call) */
+    for (size_t i = 0; st == ORC_OK && i < n; ++i) Ts[i] = T0 ? T0[i] : 0.0;
+    for (int it = 0; st == ORC_OK && it < n_iter; ++it) {
+        memcpy(Ts + (size_t)(it + 1) * n, Ts + (size_t)it * n, sizeof(double) * n);
+        st = solve_impl(ny, nx, 1, p, L, n_lines, E_keV, delta, beta, weights,
+                        ORC_MODEL_NONLOCAL, D, Ts + (size_t)(it + 1) * n, 1, omega, -1.0,
+                        eps_I, NULL, NULL, NULL);
+    }
+
+    /* reverse */
+    for (size_t i = 0; st == ORC_OK && i < n; ++i) {
+        tb[i] = Tbar_N[i];
+        Db[i] = 0.0;
+    }
+    for (int it = n_iter - 1; st == ORC_OK && it >= 0; --it) {
+        const double* T = Ts + (size_t)it * n;
+        /* the forward of this iteration, recomputed */
+        st = forward_impl(ny, nx, &ln, ORC_MODEL_NONLOCAL, T, P, Ps, NULL, gy, gx, uy, ux, Iw,
+                          Pl);
+        if (st != ORC_OK) break;
+        for (size_t i = 0; i < n; ++i) {
+            r[i] = D[i] - P[i];
+            num[i] = 0.0;
+        }
+        for (int s = 0; s < ns; ++s) {
+            double *I_s = Is + (size_t)s * n, *rs_s = rs + (size_t)s * n,
+                   *ga_s = ga + (size_t)s * n, *In_s = In + (size_t)s * n;
+            const double* P_s = Ps + (size_t)s * n;
+            for (size_t i = 0; i < n; ++i) I_s[i] = ln.f[s] * exp(-ln.mu[s] * T[i]);
+            if (ln.f[s] == 0.0) continue; /* a line without weight carries nothing */
+            for (size_t i = 0; i < n; ++i) {
+                rs_s[i] = (P[i] > 1e-30) ? r[i] * P_s[i] / P[i] : r[i] * ln.f[s];
+                uy[i] = ln.c[s] * gy[i];
+                ux[i] = ln.c[s] * gx[i];
+            }
+            orc_gather(ny, nx, rs_s, uy, ux, ga_s);
+            st = filter_kind(ny, nx, p, ln.mu[s], L * ln.delta[s], 0, ga_s, tmp);
+            if (st != ORC_OK) break;
+            for (size_t i = 0; i < n; ++i) {
+                In_s[i] = I_s[i] + omega * tmp[i];
+                double fl = eps_I * ln.f[s];
+                double Ic = In_s[i] < fl ? fl : In_s[i];
+                num[i] += ln.f[s] * ln.mu[s] * log(Ic / ln.f[s]);
+            }
+        }
+        if (st != ORC_OK) break;
+
+        /* tau' = -num / den */
+        double denb = 0.0;
+        for (size_t i = 0; i < n; ++i) {
+            denb += tb[i] * num[i] / (den * den);
+            tn[i] = 0.0;
+            Pbar[i] = 0.0;
+            rbar[i] = 0.0;
+            vx[i] = 0.0;
+            vy[i] = 0.0;
+        }
+        for (int s = 0; s < ns; ++s) mub[s] += denb * 2.0 * ln.f[s] * ln.mu[s];
+        for (int s = 0; s < ns; ++s) {
+            double *rsb_s = rsb + (size_t)s * n, *uxb_s = uxb + (size_t)s * n,
+                   *uyb_s = uyb + (size_t)s * n, *Isb_s = Isb + (size_t)s * n;
+            for (size_t i = 0; i < n; ++i) {
+                rsb_s[i] = 0.0;
+                uxb_s[i] = 0.0;
+                uyb_s[i] = 0.0;
+                Isb_s[i] = 0.0;
+            }
+            if (ln.f[s] == 0.0) continue;
+            const double *In_s = In + (size_t)s * n, *ga_s = ga + (size_t)s * n,
+                         *rs_s = rs + (size_t)s * n;
+            const double fl = eps_I * ln.f[s];
+            /* num = sum_s f_s mu_s ln(I'_s / f_s), I'_s = max(I_s + omega h_s, fl) */
+            for (size_t i = 0; i < n; ++i) {
+                const double numb = -tb[i] / den;
+                const double Ic = In_s[i] < fl ? fl : In_s[i];
+                mub[s] += numb * ln.f[s] * log(Ic / ln.f[s]);
+                const double Inb = In_s[i] < fl ? 0.0 : numb * ln.f[s] * ln.mu[s] / Ic;
+                Isb_s[i] += Inb;
+                hb[i] = omega * Inb;
+            }
+            /* h_s = F^-1 H_s F g_s */
+            st = filter_kind(ny, nx, p, ln.mu[s], L * ln.delta[s], 0, hb, gb);
+            if (st == ORC_OK) st = filter_kind(ny, nx, p, ln.mu[s], L * ln.delta[s], 1, ga_s, tmp);
+            if (st != ORC_OK) break;
+            for (size_t i = 0; i < n; ++i) mub[s] += hb[i] * tmp[i];
+            st = filter_kind(ny, nx, p, ln.mu[s], L * ln.delta[s], 2, ga_s, tmp);
+            if (st != ORC_OK) break;
+            for (size_t i = 0; i < n; ++i) Ldb[s] += hb[i] * tmp[i];
+            /* g_s = M_s^* r_s at the shift u_s */
+            for (size_t i = 0; i < n; ++i) {
+                uy[i] = ln.c[s] * gy[i];
+                ux[i] = ln.c[s] * gx[i];
+            }
+            orc_splat(ny, nx, gb, uy, ux, rsb_s, NULL);
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t i = IDX(y, x);
+                    double val, dux, duy;
+                    interp_du(ny, nx, rs_s, y, x, uy[i], ux[i], &val, &dux, &duy);
+                    uxb_s[i] += gb[i] * dux;
+                    uyb_s[i] += gb[i] * duy;
+                }
+        }
+        if (st != ORC_OK) break;
+        /* r_s = r P_s / P (P > 1e-30), else r f_s */
+        for (int s = 0; s < ns; ++s) {
+            if (ln.f[s] == 0.0) continue;
+            const double *rsb_s = rsb + (size_t)s * n, *P_s = Ps + (size_t)s * n;
+            double* Psb_s = Psb + (size_t)s * n;
+            for (size_t i = 0; i < n; ++i) {
+                Psb_s[i] = 0.0;
+                if (P[i] > 1e-30) {
+                    rbar[i] += rsb_s[i] * P_s[i] / P[i];
+                    Psb_s[i] += rsb_s[i] * r[i] / P[i];
+                    Pbar[i] -= rsb_s[i] * r[i] * P_s[i] / (P[i] * P[i]);
+                } else {
+                    rbar[i] += rsb_s[i] * ln.f[s];
+                }
+            }
+        }
+        /* r = D - P, P = sum_s P_s */
+        for (size_t i = 0; i < n; ++i) {
+            Db[i] += rbar[i];
+            Pbar[i] -= rbar[i];
+        }
+        for (int s = 0; s < ns; ++s) {
+            if (ln.f[s] == 0.0) continue;
+            double *Psb_s = Psb + (size_t)s * n, *Isb_s = Isb + (size_t)s * n,
+                   *uxb_s = uxb + (size_t)s * n, *uyb_s = uyb + (size_t)s * n;
+            const double* I_s = Is + (size_t)s * n;
+            for (size_t i = 0; i < n; ++i) {
+                Psb_s[i] += Pbar[i];
+                uy[i] = ln.c[s] * gy[i];
+                ux[i] = ln.c[s] * gx[i];
+            }
+            /* P_s = M_s[I_s] at the shift u_s */
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t i = IDX(y, x);
+                    double val, dux, duy;
+                    interp_du(ny, nx, Psb_s, y, x, uy[i], ux[i], &val, &dux, &duy);
+                    Isb_s[i] += val;
+                    uxb_s[i] += I_s[i] * dux;
+                    uyb_s[i] += I_s[i] * duy;
+                }
+            /* I_s = f_s exp(-mu_s tau), u_s = c_s G[tau] */
+            for (size_t i = 0; i < n; ++i) {
+                tn[i] += -ln.mu[s] * I_s[i] * Isb_s[i];
+                mub[s] += -T[i] * I_s[i] * Isb_s[i];
+                vx[i] += ln.c[s] * uxb_s[i];
+                vy[i] += ln.c[s] * uyb_s[i];
+                cb[s] += uxb_s[i] * gx[i] + uyb_s[i] * gy[i];
+            }
+        }
+        /* G^T */
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                tn[IDX(y, x)] += gT(vx + IDX(y, 0), 1, nx, x);
+                tn[IDX(y, x)] += gT(vy + x, (size_t)nx, ny, y);
+            }
+        memcpy(tb, tn, sizeof(double) * n);
+    }
+    if (st == ORC_OK) {
+        if (T0_bar) memcpy(T0_bar, tb, sizeof(double) * n);
+        if (D_bar) memcpy(D_bar, Db, sizeof(double) * n);
+        double lbar = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            /* c_s = -L delta_s / p^2; the filter's L delta_s; mu_s = 2 k_s beta_s */
+            if (delta_bar) delta_bar[s] = -L / (p * p) * cb[s] + L * Ldb[s];
+            if (beta_bar) beta_bar[s] = 2.0 * ln.k[s] * mub[s];
+            lbar += -ln.delta[s] / (p * p) * cb[s] + ln.delta[s] * Ldb[s];
+        }
+        if (L_bar) *L_bar = lbar;
+    }
+    free(Ts); free(gy); free(gx); free(uy); free(ux); free(Iw); free(Pl); free(P); free(r);
+    free(num); free(tb); free(tn); free(Pbar); free(rbar); free(vx); free(vy); free(hb);
+    free(gb); free(tmp); free(Db); free(Ps); free(Is); free(rs); free(ga); free(In);
+    free(rsb); free(uxb); free(uyb); free(Isb); free(Psb); free(mub); free(Ldb); free(cb);
+    lines_free(&ln);
+    return st;
 }

@@ -73,6 +73,8 @@ def _load():
                                          d, d, ip]
             lib.orc_bin.argtypes = [i, i, i, d, d]
             lib.orc_bin.restype = None
+            lib.orc_solve_vjp.argtypes = [i, i, f, f, i, d, d, d, d, d, d, i, f, f, d, d, d, d,
+                                          d, d]
             _lib = lib
     return _lib
 
@@ -217,6 +219,24 @@ def vjp(lines: Lines, T, gbar):
                          _p(db), _p(bb), _p(lb))
     _check(st, "vjp")
     return Tbar, db, bb, float(lb[0])
+
+
+def solve_vjp(lines: Lines, D, Tbar, n_iter, omega=1.0, T0=None, eps_I=1e-8):
+    """Gradients of F = <Tbar, tau_N>, tau_N the thickness after n_iter
+    non-local iterations from T0 (zeros when None), without early stop:
+    returns (T0_bar, D_bar, delta_bar[n], beta_bar[n], L_bar)."""
+    D, Tbar = _c(D), _c(Tbar)
+    T0 = np.zeros_like(D) if T0 is None else _c(T0)
+    t0b = np.empty_like(D)
+    dbar = np.empty_like(D)
+    db = np.zeros(lines.n)
+    bb = np.zeros(lines.n)
+    lb = np.zeros(1)
+    st = _load().orc_solve_vjp(D.shape[0], D.shape[1], *lines._args(), _p(D), _p(T0),
+                               int(n_iter), float(omega), float(eps_I), _p(Tbar), _p(t0b),
+                               _p(dbar), _p(db), _p(bb), _p(lb))
+    _check(st, "solve_vjp")
+    return t0b, dbar, db, bb, float(lb[0])
 
 
 def solve(lines: Lines, D, T0=None, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8,
