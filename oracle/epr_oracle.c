@@ -47,10 +47,14 @@
  * the non-local solve, for calibrating L, delta_s and beta_s) are pinned by
  * finite differences of the oracle's own forward and solve.
  *
- * Parity unpinned: the residual split of R5.  The paper only says the
- * weights are "positivity-weighted"; P_s / P and f_s agree at the flat-field
- * start and at every fixed point, so no fact the paper fixes tells them
- * apart.  Every other step is pinned by the CPU tests.
+ * The residual split of R5 is pinned through the paper's word for it,
+ * "positivity-weighted": without transport and preconditioning (L = 0) and
+ * with omega = 1 the update of line s is I_s + w_s (D - P), and the only
+ * weights that sum to one and keep every line positive for every D >= 0 are
+ * w_s = P_s / P (each line is then scaled by D / P).  The floor of R7 is
+ * pinned by data with a dark block, where the first update from the flat
+ * field falls to eps_I f_s in closed form.  Every step is pinned by the CPU
+ * tests.
  */
 #include <complex.h>
 #undef I /* the object intensity is called I below; the imaginary unit is _Complex_I */
