@@ -207,11 +207,14 @@ epr_status epr_check_device_status(epr_plan_t plan, void* stream);
  * not acceptable).  Scratch lives in a static device array of 16 MiB + 64 KiB
  * that every GPU loading the library holds until the process exits; it
  * bounds batch * nx * ny to 4 Mi pixels (e.g. one 2048 x 2048 map), and a
- * larger request returns EPR_ERR_UNSUPPORTED_SIZE.  The first call on each
- * device performs a one-time set-up (the array's device address and kernel
- * attributes); make that first call before any stream capture.  All calls
- * share the array: calls whose work overlaps on the GPU race.  g is device
- * memory, 16-byte aligned. */
+ * larger request returns EPR_ERR_UNSUPPORTED_SIZE.  Every call looks up the
+ * array's device address with the current device (cudaGetSymbolAddress,
+ * which allocates nothing); the first call on each device also sets the
+ * kernels' shared-memory attributes once, so make that first call before any
+ * stream capture (and, as for plans, not across a cudaDeviceReset, which
+ * drops those attributes).  All calls share the array and nothing in it has
+ * to start at zero (each call writes what it reads); calls whose work
+ * overlaps on the GPU race.  g is device memory, 16-byte aligned. */
 epr_status epr_precondition_noalloc(float* g, int nx, int ny, double pixel_m, double L_m,
                                     double energy_keV, double delta, double beta, int batch,
                                     void* stream);

@@ -61,28 +61,28 @@ __global__ void k_noalloc_twiddles(float2* tw, int n)
     tw[t] = make_float2((float)c, (float)s);
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current.  In host code the array's name is only a host-side stand-in.
+// Device address of the scratch array.  In host code the array's name is
+// only a host-side stand-in, so the address is looked up with the device
+// current, on every call (cudaGetSymbolAddress allocates nothing and is
+// cheap).  The kernels' shared-memory attributes are set once per device.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char* g_addr[kMaxDevices];
-bool g_ready[kMaxDevices];
+bool g_attr_ready[kMaxDevices];
 
 cudaError_t setup(int dev, unsigned char** out)
 {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ready[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
+    if (!g_attr_ready[dev]) {
         e = epr_row_init();
         if (e != cudaSuccess) return e;
         e = epr_col_init();
         if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<unsigned char*>(p);
-        g_ready[dev] = true;
+        g_attr_ready[dev] = true;
     }
-    *out = g_addr[dev];
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 

@@ -1,0 +1,119 @@
+"""GPU parity on branches of the update that the workloads do not reach,
+against the FP64 oracle through the C ABI.
+
+* The positivity floor of the update, I'_s = max(I_s + omega h_s, eps_I f_s)
+  ("Iterative inversion", Eq. 7): data with a dark block drive the first
+  update of every line below the floor inside the block.  eps_I = 1e-3 keeps
+  the floor far above the float32 rounding of the filtered data, so both
+  sides take the same branch except where the value is within rounding of
+  the floor, where max() is continuous.
+* A solve that starts from the caller's thickness (init = 1).
+* The residual split without transport (L = 0): with omega = 1 every line is
+  scaled by D / P (the positivity-preserving split), on data far from the
+  model.
+
+Tolerance: relative L2 <= 1e-4 on the thickness."""
+import numpy as np
+import pytest
+
+from paper_2601_22793_gb300 import phantoms as ph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_22793_gb300 import build
+    build.build()
+    from paper_2601_22793_gb300 import epr
+    epr.load()
+    return torch
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _gpu_solve(torch, E, nx, ny, p, L, Es, d, b, w, D, n_iter, omega, eps_I=1e-8, T0=None,
+               **kw):
+    with E.Plan(nx, ny, p, L, Es, d, b, w, **kw) as plan:
+        Dd = torch.from_numpy(np.ascontiguousarray(D, np.float32)).cuda()
+        T = torch.zeros_like(Dd) if T0 is None else torch.from_numpy(
+            np.ascontiguousarray(T0, np.float32)).cuda()
+        info = E.epr_solve_nonlocal(plan.handle, Dd, T, n_iter=n_iter, omega=omega,
+                                    eps_I=eps_I, init=0 if T0 is None else 1)
+        return T.cpu().numpy().astype(np.float64), info
+
+
+def _dark_block(ny, nx, seed=21):
+    g = np.random.default_rng(seed)
+    D = 1.0 + 0.02 * g.normal(size=(ny, nx))
+    D[ny // 5:ny - ny // 5, nx // 5:nx - nx // 5] = 0.0
+    return D.astype(np.float32)
+
+
+@pytest.mark.parametrize("n_lines", [1, 2])
+@pytest.mark.parametrize("ny,nx", [(64, 72), (256, 256)])
+def test_update_floor_branch(torch, oracle, n_lines, ny, nx):
+    from paper_2601_22793_gb300 import epr as E
+    p, L, eps_I = 1.0e-6, 5e-4, 1e-3
+    Es, d, b, w = [55.0, 95.0], [2.4e-7, 8.0e-8], [2.0e-10, 2.6e-11], [0.35, 0.65]
+    Es, d, b, w = Es[:n_lines], d[:n_lines], b[:n_lines], w[:n_lines]
+    D = _dark_block(ny, nx)
+    ln = oracle.Lines(Es, d, b, w, L=L, pixel=p)
+    Tr, _ = oracle.solve(ln, D.astype(np.float64), n_iter=1, omega=1.0, eps_I=eps_I)
+    Tg, info = _gpu_solve(torch, E, nx, ny, p, L, Es, d, b, w, D, 1, 1.0, eps_I=eps_I)
+    assert rel(Tg, Tr) < 1e-4
+    # the floor is active on a good share of the block
+    _, mu, *_ = ln.params()
+    if n_lines == 1:
+        floored = np.isclose(Tr, -np.log(eps_I) / mu[0], rtol=1e-12, atol=0)
+        assert floored.sum() > 0.1 * (0.6 * ny) * (0.6 * nx)
+        assert np.allclose(Tg[floored], Tr[floored], rtol=1e-6)
+
+
+def test_solve_from_the_callers_thickness(torch, oracle):
+    """init = 1: the solve starts from the caller's T (here half the true
+    thickness), 8 iterations, mono and two lines."""
+    from paper_2601_22793_gb300 import epr as E
+    wl, tau = ph.spheres_mono_256()
+    ln = oracle.Lines(wl.energy_keV, wl.delta, wl.beta, wl.weights, wl.L, wl.pixel)
+    D = ph.poisson(oracle.forward(ln, tau), wl.photons, 3).astype(np.float32)
+    T0 = (0.5 * tau).astype(np.float32)
+    Tr, ir = oracle.solve(ln, D.astype(np.float64), T0=T0.astype(np.float64), n_iter=8,
+                          omega=wl.omega)
+    Tg, ig = _gpu_solve(torch, E, wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta,
+                        wl.beta, wl.weights, D, 8, wl.omega, T0=T0)
+    assert rel(Tg, Tr) < 1e-4
+    assert np.allclose(ig["rho_hist"][0], ir["rho"], rtol=1e-3)
+    # two lines, fixed-point splat
+    Es, d, b, w = ph.spectrum(2, 60.0, 100.0, 80.0, 30.0, ph.BONE[0], ph.BONE[1], 80.0, 4)
+    l2 = oracle.Lines(Es, d, b, w, L=wl.L, pixel=wl.pixel)
+    D2 = ph.poisson(oracle.forward(l2, tau), wl.photons, 4).astype(np.float32)
+    Tr2, _ = oracle.solve(l2, D2.astype(np.float64), T0=T0.astype(np.float64), n_iter=8,
+                          omega=wl.omega)
+    Tg2, _ = _gpu_solve(torch, E, wl.nx, wl.ny, wl.pixel, wl.L, Es, d, b, w, D2, 8, wl.omega,
+                        T0=T0, deterministic=True)
+    assert rel(Tg2, Tr2) < 1e-4
+
+
+def test_split_without_transport_scales_every_line(torch, oracle):
+    from paper_2601_22793_gb300 import epr as E
+    p = 1.0e-6
+    Es, d, b, w = [50.0, 80.0, 140.0], [3e-7, 1.2e-7, 4e-8], [4e-10, 1e-10, 1.5e-11], [0.2, 0.5, 0.3]
+    ln = oracle.Lines(Es, d, b, w, L=0.0, pixel=p)
+    f, mu, *_ = ln.params()
+    g = np.random.default_rng(31)
+    ny, nx = 48, 64
+    tau = (1e-3 * (1.0 + g.random((ny, nx)))).astype(np.float32)
+    I = f[:, None, None] * np.exp(-mu[:, None, None] * tau.astype(np.float64)[None])
+    D = (I.sum(0) * np.exp(g.normal(scale=1.5, size=(ny, nx)))).astype(np.float32)
+    Tr, _ = oracle.solve(ln, D.astype(np.float64), T0=tau.astype(np.float64), n_iter=1,
+                         omega=1.0)
+    Tg, _ = _gpu_solve(torch, E, nx, ny, p, 0.0, Es, d, b, w, D, 1, 1.0, T0=tau)
+    assert rel(Tg, Tr) < 1e-5

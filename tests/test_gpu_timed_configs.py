@@ -1,0 +1,130 @@
+"""GPU parity on the configurations bench.py times, against the FP64 oracle.
+
+* The monochromatic 2048 x 2048 workload itself: 200 ellipsoids, E = 80 keV,
+  L = 30 m, p = 20 um, Poisson(1e4) data from the oracle forward, 50
+  non-local iterations at omega = 0.4, one projection per call (the headline
+  line of bench.py).
+* Two members of the batched call of 32 such projections (8 phantoms, 4
+  noise draws each), solved in one call as bench.py's batched comparison
+  does.
+* An 8-line polychromatic solve (60-160 keV) on a 1024 x 2048 crop of the
+  rotated ellipsoid phantom, 20 iterations.
+
+Tolerance: relative L2 <= 1e-4 on the thickness (the converged-thickness
+bound), 1e-3 relative on the residual history.  The oracle references run in
+a pool of worker processes started before the GPU work of this module."""
+import numpy as np
+import pytest
+
+from paper_2601_22793_gb300 import phantoms as ph
+
+import oracle_jobs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _spec(wl):
+    return (wl.energy_keV, wl.delta, wl.beta, wl.weights, wl.L, wl.pixel)
+
+
+@pytest.fixture(scope="module")
+def jobs(oracle):
+    """Data and oracle references, computed before any CUDA call of this
+    module; the solves run in spawn workers while the GPU tests run."""
+    pool = oracle_jobs.Pool(4)
+    out = {}
+    # the headline workload (bench.py: seed 2000, noise seed 7)
+    wl, tau = ph.ellipsoids_mono(seed=2000)
+    spec = _spec(wl)
+    D = ph.poisson(oracle.forward(oracle.Lines(*spec[:4], L=wl.L, pixel=wl.pixel), tau),
+                   wl.photons, 7).astype(np.float32)
+    out["mono"] = (wl, D, pool.submit(oracle_jobs.solve_job, spec, D, wl.n_iter, wl.omega))
+    # the batched call: 8 phantoms x 4 noise draws; members 0 and 21 checked
+    ln = oracle.Lines(*spec[:4], L=wl.L, pixel=wl.pixel)
+    Ds = []
+    for j in range(8):
+        _, tk = ph.ellipsoids_mono(seed=3000 + j)
+        Pj = oracle.forward(ln, tk)
+        for r in range(4):
+            Ds.append(ph.poisson(Pj, wl.photons, 50 + 4 * j + r).astype(np.float32))
+    members = (0, 21)
+    out["batch"] = (wl, np.stack(Ds), members,
+                    [pool.submit(oracle_jobs.solve_job, spec, Ds[m], wl.n_iter, wl.omega)
+                     for m in members])
+    # polychromatic crop: 8 lines, rows 512..1535 of the projection at angle 21 pi / 64
+    wp, ells, angles = ph.ellipsoids_poly()
+    tp = ph.project_ellipsoids(ells, wp.ny, wp.nx, wp.pixel, angles[21])[512:1536]
+    sp = _spec(wp)
+    lp = oracle.Lines(*sp[:4], L=wp.L, pixel=wp.pixel)
+    Dp = ph.poisson(oracle.forward(lp, tp), wp.photons, 9).astype(np.float32)
+    out["poly"] = (wp, Dp, pool.submit(oracle_jobs.solve_job, sp, Dp, 20, wp.omega))
+    yield out
+    pool.close()
+
+
+@pytest.fixture(scope="module")
+def torch(jobs):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_22793_gb300 import build
+    build.build()
+    from paper_2601_22793_gb300 import epr
+    epr.load()
+    return torch
+
+
+def _plan(E, wl):
+    return E.Plan(wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights)
+
+
+def test_headline_workload_50_iterations(torch, jobs):
+    from paper_2601_22793_gb300 import epr as E
+    wl, D, fut = jobs["mono"]
+    with _plan(E, wl) as p:
+        Dd = torch.from_numpy(D).cuda()
+        T = torch.empty_like(Dd)
+        info = E.epr_solve_nonlocal(p.handle, Dd, T, n_iter=wl.n_iter, omega=wl.omega)
+        Tg = T.cpu().numpy()
+    Tr, rho_r, kappa_r, it_r = fut.get()
+    assert info["iters"][0] == it_r == wl.n_iter
+    assert rel(Tg, Tr) < 1e-4
+    assert np.allclose(info["rho_hist"][0], rho_r, rtol=1e-3)
+    assert np.allclose(info["kappa_hist"][0][1:], kappa_r[1:], rtol=1e-2)
+
+
+def test_batched_call_of_32_members_vs_oracle(torch, jobs):
+    from paper_2601_22793_gb300 import epr as E
+    wl, Ds, members, futs = jobs["batch"]
+    nb = Ds.shape[0]
+    with _plan(E, wl) as p:
+        Db = torch.from_numpy(Ds).cuda()
+        Tb = torch.empty_like(Db)
+        info = E.epr_solve_nonlocal(p.handle, Db, Tb, batch=nb, n_iter=wl.n_iter,
+                                    omega=wl.omega)
+        Tg = Tb.cpu().numpy()
+    assert all(int(k) == wl.n_iter for k in info["iters"])
+    for m, fut in zip(members, futs):
+        Tr, rho_r, _, _ = fut.get()
+        assert rel(Tg[m], Tr) < 1e-4, m
+        assert np.allclose(info["rho_hist"][m], rho_r, rtol=1e-3), m
+
+
+def test_polychromatic_8_lines_1024x2048(torch, jobs):
+    from paper_2601_22793_gb300 import epr as E
+    wp, Dp, fut = jobs["poly"]
+    ny, nx = Dp.shape
+    with E.Plan(nx, ny, wp.pixel, wp.L, wp.energy_keV, wp.delta, wp.beta, wp.weights) as p:
+        Dd = torch.from_numpy(Dp).cuda()
+        T = torch.empty_like(Dd)
+        info = E.epr_solve_nonlocal(p.handle, Dd, T, n_iter=20, omega=wp.omega)
+        Tg = T.cpu().numpy()
+    Tr, rho_r, _, _ = fut.get()
+    assert rel(Tg, Tr) < 1e-4
+    assert np.allclose(info["rho_hist"][0], rho_r, rtol=1e-3)
