@@ -41,6 +41,14 @@
  *       to the o x o fine pixels of its block before the split, the
  *       back-transport, the preconditioner (fine grid) and the update.
  *       o = 1 is the plain solve.
+ *   R12 non-local model to second order (the caption of the non-local grid
+ *       figure calls the non-local model second order, while the Methods
+ *       define the transport M_s as pure WKB0): P_s = M_s[I_s] minus the
+ *       diffraction-pressure (WKB1) term of Eq. 1, eps^2/(4 p^4)
+ *       D_i(I_s D_i Q_s), evaluated on the detector grid with the object
+ *       intensity as in the local closure of order 2; the back-transport
+ *       stays the transport's adjoint.  At zero shift it is the local
+ *       closure of order 2.
  *
  * Beyond the paper: orc_vjp (the transpose of the non-local forward model)
  * and orc_solve_vjp (reverse mode through a fixed number of iterations of
@@ -66,7 +74,8 @@
 #define ORC_PI 3.14159265358979323846
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 3 };
-enum { ORC_MODEL_NONLOCAL = 0, ORC_MODEL_LOCAL1 = 1, ORC_MODEL_LOCAL2 = 2 };
+enum { ORC_MODEL_NONLOCAL = 0, ORC_MODEL_LOCAL1 = 1, ORC_MODEL_LOCAL2 = 2,
+       ORC_MODEL_NONLOCAL_WKB1 = 3 };
 
 #define IDX(y, x) ((size_t)(y) * (size_t)nx + (size_t)(x))
 
@@ -412,6 +421,37 @@ static void lines_free(orc_lines* ln)
     free(ln->c); free(ln->eps); free(ln->delta);
 }
 
+/* The diffraction-pressure (WKB1) term of Eq. 1 in pixel units, subtracted
+ * from P: P -= eps^2/(4 p^4) [D_x(I D_x Q) + D_y(I D_y Q)] with
+ * Q = (D_xx + D_yy) sqrt(I) / sqrt(I) (reading R10 for the stencils). */
+static int wkb1_term(int ny, int nx, const double* I, double eps, double p, double* P)
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    double* a = malloc(sizeof(double) * n);
+    double* b = malloc(sizeof(double) * n);
+    double* t = malloc(sizeof(double) * n);
+    double* q = malloc(sizeof(double) * n);
+    if (!a || !b || !t || !q) {
+        free(a); free(b); free(t); free(q);
+        return ORC_ENOMEM;
+    }
+    for (size_t i = 0; i < n; ++i) a[i] = sqrt(I[i]);
+    d_xx(ny, nx, a, b);
+    d_yy(ny, nx, a, t);
+    for (size_t i = 0; i < n; ++i) q[i] = (a[i] > 0.0) ? (b[i] + t[i]) / a[i] : 0.0;
+    double coef = eps * eps / (4.0 * p * p * p * p);
+    d_x(ny, nx, q, a);
+    for (size_t i = 0; i < n; ++i) a[i] *= I[i];
+    d_x(ny, nx, a, b);
+    for (size_t i = 0; i < n; ++i) P[i] -= coef * b[i];
+    d_y(ny, nx, q, a);
+    for (size_t i = 0; i < n; ++i) a[i] *= I[i];
+    d_y(ny, nx, a, b);
+    for (size_t i = 0; i < n; ++i) P[i] -= coef * b[i];
+    free(a); free(b); free(t); free(q);
+    return ORC_OK;
+}
+
 /* Local O(L^2) closure of one line (Eq. 1 in pixel units, reading R10):
  *   P = I - D_i(I u_i)                                             (m = 1)
  *       + 1/2 D_i D_j (I u_i u_j) - eps^2/(4 p^4) D_i(I D_i Q)    (m = 2)
@@ -453,19 +493,8 @@ static int local_line(int ny, int nx, int order, const double* I,
         d_x(ny, nx, t, b);
         for (size_t i = 0; i < n; ++i) P[i] += b[i];
         /* - eps^2/(4 p^4) [ D_x(I D_x Q) + D_y(I D_y Q) ] */
-        for (size_t i = 0; i < n; ++i) a[i] = sqrt(I[i]);
-        d_xx(ny, nx, a, b);
-        d_yy(ny, nx, a, t);
-        for (size_t i = 0; i < n; ++i) q[i] = (a[i] > 0.0) ? (b[i] + t[i]) / a[i] : 0.0;
-        double coef = eps * eps / (4.0 * p * p * p * p);
-        d_x(ny, nx, q, a);
-        for (size_t i = 0; i < n; ++i) a[i] *= I[i];
-        d_x(ny, nx, a, b);
-        for (size_t i = 0; i < n; ++i) P[i] -= coef * b[i];
-        d_y(ny, nx, q, a);
-        for (size_t i = 0; i < n; ++i) a[i] *= I[i];
-        d_y(ny, nx, a, b);
-        for (size_t i = 0; i < n; ++i) P[i] -= coef * b[i];
+        free(a); free(b); free(t); free(q);
+        return wkb1_term(ny, nx, I, eps, p, P);
     }
     free(a); free(b); free(t); free(q);
     return ORC_OK;
@@ -474,6 +503,10 @@ static int local_line(int ny, int nx, int order, const double* I,
 /* Polychromatic forward (Eq. 5): P = sum_s F_s[I_s] with I_s = f_s exp(-mu_s
  * tau) (Eq. 7) and u_s = c_s G[tau] (reading R2).  F_s is the bilinear
  * redistribution for model 0 and the local closure of order m for models 1, 2.
+ * Model 3 (reading R12) is the non-local model to second order: the bilinear
+ * redistribution (WKB0 transport, all orders of the shift) minus the
+ * diffraction-pressure term of Eq. 1, evaluated on the detector grid with the
+ * line's object intensity, as the local closure of order 2 evaluates it.
  * Ps (n_lines maps, may be NULL) and dropped (n_lines values, may be NULL)
  * receive the per-line predictions and the per-line mass that left the grid. */
 static int forward_impl(int ny, int nx, const orc_lines* ln, int model,
@@ -492,8 +525,12 @@ static int forward_impl(int ny, int nx, const orc_lines* ln, int model,
             Pl[i] = 0.0;
         }
         double lost = 0.0;
-        if (model == ORC_MODEL_NONLOCAL) {
+        if (model == ORC_MODEL_NONLOCAL || model == ORC_MODEL_NONLOCAL_WKB1) {
             orc_splat(ny, nx, I, uy, ux, Pl, &lost);
+            if (model == ORC_MODEL_NONLOCAL_WKB1) {
+                int st = wkb1_term(ny, nx, I, ln->eps[s], ln->p, Pl);
+                if (st != ORC_OK) return st;
+            }
         } else {
             int st = local_line(ny, nx, model, I, uy, ux, ln->eps[s], ln->p, Pl);
             if (st != ORC_OK) return st;
@@ -512,7 +549,7 @@ int orc_forward(int ny, int nx, double p, double L, int n_lines,
                 const double* weights, int model, const double* T, double* P,
                 double* Ps, double* dropped)
 {
-    if (ny < 2 || nx < 2 || model < 0 || model > 2) return ORC_EINVAL;
+    if (ny < 2 || nx < 2 || model < 0 || model > 3) return ORC_EINVAL;
     orc_lines ln;
     int st = lines_init(&ln, n_lines, E_keV, delta, beta, weights, L, p);
     size_t n = (size_t)nx * (size_t)ny;
@@ -692,7 +729,7 @@ static int solve_impl(int ny, int nx, int os, double p, double L, int n_lines,
                       int n_iter, double omega, double tol, double eps_I, double* rho,
                       double* kappa, int* iters)
 {
-    if (ny < 2 || nx < 2 || model < 0 || model > 2 || n_iter < 0 || os < 1 ||
+    if (ny < 2 || nx < 2 || model < 0 || model > 3 || n_iter < 0 || os < 1 ||
         ny % os != 0 || nx % os != 0)
         return ORC_EINVAL;
     const int nyd = ny / os, nxd = nx / os;
@@ -742,8 +779,10 @@ static int solve_impl(int ny, int nx, int os, double p, double L, int n_lines,
             /* 3. split */
             for (size_t i = 0; i < n; ++i)
                 rs[i] = (P[i] > 1e-30) ? r[i] * P_s[i] / P[i] : r[i] * ln.f[s];
-            /* 4. back-transport (shift of this line recomputed from tau) */
-            if (model == ORC_MODEL_NONLOCAL) {
+            /* 4. back-transport (shift of this line recomputed from tau); the
+             * non-local models take the transport's adjoint (Eq. 4), the
+             * local closures the identity */
+            if (model == ORC_MODEL_NONLOCAL || model == ORC_MODEL_NONLOCAL_WKB1) {
                 for (size_t i = 0; i < n; ++i) {
                     uy[i] = ln.c[s] * gy[i];
                     ux[i] = ln.c[s] * gx[i];

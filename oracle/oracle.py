@@ -27,6 +27,7 @@ _lib = None
 MODEL_NONLOCAL = 0
 MODEL_LOCAL1 = 1
 MODEL_LOCAL2 = 2
+MODEL_NONLOCAL_WKB1 = 3
 
 
 def build(force: bool = False) -> str:
