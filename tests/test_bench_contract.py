@@ -33,3 +33,27 @@ def test_reference_arm_prints_the_contract_line():
     rows = int(cb["sample"].split("(")[1].split("x")[0])
     expect = (rows * 2048 / 2048 ** 2) / (50 * line["ms_per_step"] / 1e3)
     assert abs(line["value"] / expect - 1.0) < 1e-2
+
+
+def test_reference_arm_config_is_the_gpu_arms():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2601_22793_gb300 import phantoms as ph
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    wl, _ = ph.ellipsoids_mono(seed=bench.PHANTOM_SEED)
+    assert line["config"] == json.loads(json.dumps(bench.bench_config(wl, 1)))
+
+
+def test_cpu_baseline_leg_times_one_and_all_cores_and_returns_the_data():
+    sys.path.insert(0, ROOT)
+    import bench
+    rec, D = bench.cpu_baseline(1)
+    assert rec["kind"] == "oracle" and rec["cores"] == (os.cpu_count() or 1)
+    assert rec["value"] > 0 and rec["single_thread"]["value"] > 0 and rec["cpu_model"]
+    assert D.shape == (2048, 2048) and D.dtype.name == "float32"
+    # the reference arm solves the same data
+    _, _, _, D2 = bench._oracle_workload()
+    assert (D == D2).all()
