@@ -49,6 +49,17 @@
  *       intensity as in the local closure of order 2; the back-transport
  *       stays the transport's adjoint.  At zero shift it is the local
  *       closure of order 2.
+ *   R13 x-dependent effective spectrum ("Remark on spatially varying
+ *       spectra", whose file format and blockwise interpolation are in a
+ *       supplement that is not available): x is the detector column; a table
+ *       of knot columns gives each line's weight, delta and beta, linearly
+ *       interpolated in x and constant beyond the end knots; f_s(x) is the
+ *       weight normalised per column, mu_s(x) = 2 k_s beta_s(x), the shift
+ *       u_s = -(L delta_s(x) / p^2) G[tau] holds the table constant under the
+ *       derivative (slow variation), the update floors at eps_I f_s(x) and the
+ *       projection weighs by f_s(x) mu_s(x) per column; the preconditioner,
+ *       which must be FFT-diagonal, takes each line's column means of mu_s and
+ *       L delta_s.
  *
  * Beyond the paper: orc_vjp (the transpose of the non-local forward model)
  * and orc_solve_vjp (reverse mode through a fixed number of iterations of
@@ -1154,5 +1165,195 @@ int orc_solve_vjp(int ny, int nx, double p, double L, int n_lines, const double*
     free(gb); free(tmp); free(Db); free(Ps); free(Is); free(rs); free(ga); free(In);
     free(rsb); free(uxb); free(uyb); free(Isb); free(Psb); free(mub); free(Ldb); free(cb);
     lines_free(&ln);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* x-dependent effective spectrum ("Remark on spatially varying spectra";   */
+/* Eq. 6 with db_s(x), Eq. 7 with f_s(x) and gamma_s(x); reading R13).       */
+/* ------------------------------------------------------------------------ */
+
+/* Per-column line constants from a knot table: K knot columns X_0 < ... <
+ * X_{K-1} (pixel units) with, per line s and knot k, the weight w[s][k], the
+ * decrement delta[s][k] and the absorption index beta[s][k].  Each is
+ * interpolated linearly in the column x between knots and held constant
+ * beyond the end knots.  Then, per column,
+ *   f_s(x) = w_s(x) / sum_s w_s(x)            (local spectral fraction),
+ *   mu_s(x) = 2 k_s beta_s(x)                 (gamma_s(x) of Eq. 7),
+ *   c_s(x) = -L delta_s(x) / p^2              (shift per thickness step;
+ *                                              delta_s = db_s beta_s),
+ * and the preconditioner of each line takes the column means
+ * mu_h[s] = mean_x mu_s(x), Ld_h[s] = L mean_x delta_s(x) (an FFT-diagonal
+ * symbol needs constants).  f, mu, c are [n_lines][nx]. */
+static double knot_interp(int K, const double* X, const double* v, double x)
+{
+    if (x <= X[0]) return v[0];
+    if (x >= X[K - 1]) return v[K - 1];
+    int k = 0;
+    while (k + 1 < K && X[k + 1] < x) ++k;
+    double t = (x - X[k]) / (X[k + 1] - X[k]);
+    return v[k] + t * (v[k + 1] - v[k]);
+}
+
+int orc_xspec_params(int nx, int n_lines, const double* E_keV, int K, const double* X,
+                     const double* w, const double* delta, const double* beta, double L,
+                     double p, double* f, double* mu, double* c, double* mu_h, double* Ld_h)
+{
+    if (nx < 1 || n_lines < 1 || K < 1 || !(p > 0.0) || L < 0.0) return ORC_EINVAL;
+    for (int k = 0; k + 1 < K; ++k)
+        if (!(X[k + 1] > X[k])) return ORC_EINVAL;
+    for (int s = 0; s < n_lines; ++s) {
+        mu_h[s] = 0.0;
+        Ld_h[s] = 0.0;
+    }
+    for (int x = 0; x < nx; ++x) {
+        double wsum = 0.0;
+        for (int s = 0; s < n_lines; ++s) {
+            double ws = knot_interp(K, X, w + (size_t)s * K, (double)x);
+            if (!(ws > 0.0)) return ORC_EINVAL;
+            f[(size_t)s * nx + x] = ws;
+            wsum += ws;
+        }
+        for (int s = 0; s < n_lines; ++s) {
+            double lam = ORC_HC_EV_M / (E_keV[s] * 1e3);
+            double k = 2.0 * ORC_PI / lam;
+            double bs = knot_interp(K, X, beta + (size_t)s * K, (double)x);
+            double ds = knot_interp(K, X, delta + (size_t)s * K, (double)x);
+            f[(size_t)s * nx + x] /= wsum;
+            mu[(size_t)s * nx + x] = 2.0 * k * bs;
+            c[(size_t)s * nx + x] = -L * ds / (p * p);
+            mu_h[s] += 2.0 * k * bs / nx;
+            Ld_h[s] += L * ds / nx;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Non-local forward with per-column constants: I_s = f_s(x) exp(-mu_s(x) tau),
+ * u_s = c_s(x) G[tau] (the table held constant under the derivative: the
+ * spectrum varies slowly on the scale of the shift), P = sum_s M_s[I_s]. */
+static void forward_x_impl(int ny, int nx, int ns, const double* f, const double* mu,
+                           const double* c, const double* T, double* P, double* Ps,
+                           double* dropped, const double* gy, const double* gx, double* uy,
+                           double* ux, double* I, double* Pl)
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    for (size_t i = 0; i < n; ++i) P[i] = 0.0;
+    for (int s = 0; s < ns; ++s) {
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t i = IDX(y, x), j = (size_t)s * nx + x;
+                uy[i] = c[j] * gy[i];
+                ux[i] = c[j] * gx[i];
+                I[i] = f[j] * exp(-mu[j] * T[i]);
+                Pl[i] = 0.0;
+            }
+        double lost = 0.0;
+        orc_splat(ny, nx, I, uy, ux, Pl, &lost);
+        for (size_t i = 0; i < n; ++i) P[i] += Pl[i];
+        if (Ps) memcpy(Ps + (size_t)s * n, Pl, sizeof(double) * n);
+        if (dropped) dropped[s] = lost;
+    }
+}
+
+int orc_forward_x(int ny, int nx, int ns, const double* f, const double* mu, const double* c,
+                  const double* T, double* P, double* Ps, double* dropped)
+{
+    if (ny < 2 || nx < 2 || ns < 1) return ORC_EINVAL;
+    size_t n = (size_t)nx * (size_t)ny;
+    double *gy = alloc_n(n), *gx = alloc_n(n), *uy = alloc_n(n), *ux = alloc_n(n),
+           *I = alloc_n(n), *Pl = alloc_n(n);
+    int st = (!gy || !gx || !uy || !ux || !I || !Pl) ? ORC_ENOMEM : ORC_OK;
+    if (st == ORC_OK) {
+        orc_gradient(ny, nx, T, gy, gx);
+        forward_x_impl(ny, nx, ns, f, mu, c, T, P, Ps, dropped, gy, gx, uy, ux, I, Pl);
+    }
+    free(gy); free(gx); free(uy); free(ux); free(I); free(Pl);
+    return st;
+}
+
+/* The non-local solve of "Iteration structure" with per-column constants:
+ * split r_s = r P_s / P (P > 1e-30, else r f_s(x)), back-transport by the
+ * gather at u_s = c_s(x) G[tau], preconditioner with the column means
+ * (mu_h[s], Ld_h[s]), update I'_s = max(I_s + omega h_s, eps_I f_s(x)) and
+ * the projection of Eq. 7 with per-column weights,
+ *   tau' = -sum_s f_s(x) mu_s(x) ln(I'_s / f_s(x)) / sum_s f_s(x) mu_s(x)^2. */
+int orc_solve_x(int ny, int nx, double p, int ns, const double* f, const double* mu,
+                const double* c, const double* mu_h, const double* Ld_h, const double* D,
+                double* T, int n_iter, double omega, double tol, double eps_I, double* rho,
+                double* kappa, int* iters)
+{
+    if (ny < 2 || nx < 2 || ns < 1 || n_iter < 0) return ORC_EINVAL;
+    size_t n = (size_t)nx * (size_t)ny;
+    double *gy = alloc_n(n), *gx = alloc_n(n), *uy = alloc_n(n), *ux = alloc_n(n),
+           *I = alloc_n(n), *Pl = alloc_n(n), *P = alloc_n(n), *r = alloc_n(n),
+           *rs = alloc_n(n), *g = alloc_n(n), *num = alloc_n(n), *den = alloc_n(nx),
+           *Ps = alloc_n(n * (size_t)ns);
+    int st = (!gy || !gx || !uy || !ux || !I || !Pl || !P || !r || !rs || !g || !num || !den ||
+              !Ps) ? ORC_ENOMEM : ORC_OK;
+    for (int x = 0; st == ORC_OK && x < nx; ++x) {
+        den[x] = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            size_t j = (size_t)s * nx + x;
+            den[x] += f[j] * mu[j] * mu[j];
+        }
+        if (!(den[x] > 0.0)) st = ORC_EINVAL;
+    }
+    double dnorm = 0.0;
+    for (size_t i = 0; st == ORC_OK && i < n; ++i) dnorm += D[i] * D[i];
+    dnorm = sqrt(dnorm);
+    int it = 0;
+    for (; st == ORC_OK && it < n_iter; ++it) {
+        orc_gradient(ny, nx, T, gy, gx);
+        forward_x_impl(ny, nx, ns, f, mu, c, T, P, Ps, NULL, gy, gx, uy, ux, I, Pl);
+        double rr = 0.0;
+        for (size_t i = 0; i < n; ++i) {
+            r[i] = D[i] - P[i];
+            rr += r[i] * r[i];
+            num[i] = 0.0;
+        }
+        if (rho) rho[it] = dnorm > 0.0 ? sqrt(rr) / dnorm : sqrt(rr);
+        for (int s = 0; s < ns; ++s) {
+            const double* P_s = Ps + (size_t)s * n;
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t i = IDX(y, x), j = (size_t)s * nx + x;
+                    rs[i] = (P[i] > 1e-30) ? r[i] * P_s[i] / P[i] : r[i] * f[j];
+                    uy[i] = c[j] * gy[i];
+                    ux[i] = c[j] * gx[i];
+                }
+            orc_gather(ny, nx, rs, uy, ux, g);
+            st = orc_paganin(ny, nx, p, mu_h[s], Ld_h[s], g);
+            if (st != ORC_OK) break;
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t i = IDX(y, x), j = (size_t)s * nx + x;
+                    double Is = f[j] * exp(-mu[j] * T[i]);
+                    double In = Is + omega * g[i];
+                    double fl = eps_I * f[j];
+                    if (In < fl) In = fl;
+                    num[i] += f[j] * mu[j] * log(In / f[j]);
+                }
+        }
+        if (st != ORC_OK) break;
+        double dd = 0.0, tt = 0.0;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t i = IDX(y, x);
+                double tn = -num[i] / den[x];
+                dd += (tn - T[i]) * (tn - T[i]);
+                tt += tn * tn;
+                T[i] = tn;
+            }
+        double kap = tt > 0.0 ? sqrt(dd / tt) : sqrt(dd);
+        if (kappa) kappa[it] = kap;
+        if (kap <= tol) {
+            ++it;
+            break;
+        }
+    }
+    if (iters) *iters = it;
+    free(gy); free(gx); free(uy); free(ux); free(I); free(Pl); free(P); free(r); free(rs);
+    free(g); free(num); free(den); free(Ps);
     return st;
 }

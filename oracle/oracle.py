@@ -76,6 +76,9 @@ def _load():
             lib.orc_bin.restype = None
             lib.orc_solve_vjp.argtypes = [i, i, f, f, i, d, d, d, d, d, d, i, f, f, d, d, d, d,
                                           d, d]
+            lib.orc_xspec_params.argtypes = [i, i, d, i, d, d, d, d, f, f, d, d, d, d, d]
+            lib.orc_forward_x.argtypes = [i, i, i, d, d, d, d, d, d, d]
+            lib.orc_solve_x.argtypes = [i, i, f, i, d, d, d, d, d, d, d, i, f, f, f, d, d, ip]
             _lib = lib
     return _lib
 
@@ -279,5 +282,61 @@ def solve_os(lines: Lines, D, os_, T0=None, n_iter=20, omega=1.0, tol=0.0, eps_I
                               int(n_iter), float(omega), float(tol), float(eps_I),
                               _p(rho), _p(kappa), ctypes.byref(iters))
     _check(st, "solve_os")
+    k = iters.value
+    return T, {"rho": rho[:k], "kappa": kappa[:k], "iters": k}
+
+
+class XSpec:
+    """x-dependent spectrum (reading R13): energies E (keV) per line, knot
+    columns X (ascending, pixel units) and per-line, per-knot weights, delta
+    and beta ([n_lines][K] each); L and p in metres; nx columns."""
+
+    def __init__(self, energy_keV, X, weights, delta, beta, L, pixel, nx):
+        self.E = _c(np.atleast_1d(energy_keV))
+        self.X = _c(np.atleast_1d(X))
+        K = self.X.size
+        self.w = _c(np.reshape(weights, (self.E.size, K)))
+        self.delta = _c(np.reshape(delta, (self.E.size, K)))
+        self.beta = _c(np.reshape(beta, (self.E.size, K)))
+        self.L, self.p, self.nx = float(L), float(pixel), int(nx)
+        n = self.E.size
+        self.f = np.zeros((n, nx))
+        self.mu = np.zeros((n, nx))
+        self.c = np.zeros((n, nx))
+        self.mu_h = np.zeros(n)
+        self.Ld_h = np.zeros(n)
+        st = _load().orc_xspec_params(nx, n, _p(self.E), K, _p(self.X), _p(self.w),
+                                      _p(self.delta), _p(self.beta), self.L, self.p,
+                                      _p(self.f), _p(self.mu), _p(self.c), _p(self.mu_h),
+                                      _p(self.Ld_h))
+        _check(st, "xspec_params")
+
+    @property
+    def n(self):
+        return int(self.E.size)
+
+
+def forward_x(xs: XSpec, T, per_line=False):
+    T = _c(T)
+    ny, nx = T.shape
+    P = np.empty_like(T)
+    Ps = np.empty((xs.n, ny, nx)) if per_line else None
+    dropped = np.zeros(xs.n) if per_line else None
+    st = _load().orc_forward_x(ny, nx, xs.n, _p(xs.f), _p(xs.mu), _p(xs.c), _p(T), _p(P),
+                               _p(Ps), _p(dropped))
+    _check(st, "forward_x")
+    return (P, Ps, dropped) if per_line else P
+
+
+def solve_x(xs: XSpec, D, T0=None, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8):
+    D = _c(D)
+    T = np.zeros_like(D) if T0 is None else _c(T0).copy()
+    rho = np.zeros(max(n_iter, 1))
+    kappa = np.zeros(max(n_iter, 1))
+    iters = ctypes.c_int(0)
+    st = _load().orc_solve_x(D.shape[0], D.shape[1], xs.p, xs.n, _p(xs.f), _p(xs.mu), _p(xs.c),
+                             _p(xs.mu_h), _p(xs.Ld_h), _p(D), _p(T), int(n_iter), float(omega),
+                             float(tol), float(eps_I), _p(rho), _p(kappa), ctypes.byref(iters))
+    _check(st, "solve_x")
     k = iters.value
     return T, {"rho": rho[:k], "kappa": kappa[:k], "iters": k}
