@@ -54,11 +54,17 @@ typedef enum {
 } epr_status;
 
 /* Forward models (Eq. 5: F_s is M_s for the non-local model, P_{m,s} for the
- * local closure of order m). */
+ * local closure of order m).  EPR_MODEL_NONLOCAL_WKB1 is the non-local model
+ * to second order (the caption of the paper's non-local grid figure calls the
+ * non-local model second order; the Methods define M_s as WKB0 transport):
+ * P_s = M_s[I_s] - eps_s^2/(4 p^4) D_i(I_s D_i Q_s), the diffraction-pressure
+ * term of Eq. 1 evaluated on the detector grid with the object intensity, as
+ * the local closure of order 2 evaluates it. */
 typedef enum {
     EPR_MODEL_NONLOCAL = 0,
     EPR_MODEL_LOCAL1 = 1,
-    EPR_MODEL_LOCAL2 = 2
+    EPR_MODEL_LOCAL2 = 2,
+    EPR_MODEL_NONLOCAL_WKB1 = 3
 } epr_model;
 
 /* Plan options (NULL = defaults). */
@@ -141,13 +147,45 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
                            int n_lines, const double* energy_keV, const double* delta,
                            const double* beta, const double* weights, const epr_options* opt);
 
+/* x-dependent effective spectrum (the paper's "Remark on spatially varying
+ * spectra", with db_s(x) of Eq. 6 and f_s(x), gamma_s(x) of Eq. 7; the
+ * paper's table format is in a supplement that is not available, so this
+ * one is the library's own).  x is the detector column.  A table gives K
+ * knot columns (pixel units, strictly ascending) and, per line s and knot k,
+ * row-major [n_lines][K] host arrays of the spectral weight (> 0), delta and
+ * beta (>= 0).  Each is interpolated linearly in x between knots and held
+ * constant beyond the end knots; per column the weights are normalised to
+ * sum 1 (f_s(x)), mu_s(x) = 2 k_s beta_s(x) with the plan's line energies,
+ * and the shift is u_s = -(L delta_s(x) / p^2) G[T] (the table is held
+ * constant under the derivative: slow variation).  The residual split falls
+ * back to f_s(x), the update floors at eps_I f_s(x) and the projection weighs
+ * each column by f_s(x) mu_s(x).  The preconditioner, which must be
+ * FFT-diagonal, uses each line's column means of mu_s(x) and L delta_s(x).
+ * K = 1 is a uniform spectrum. */
+typedef struct {
+    int n_knots;            /* K >= 1 */
+    const double* x_knots;  /* [K] */
+    const double* weights;  /* [n_lines][K] */
+    const double* delta;    /* [n_lines][K] */
+    const double* beta;     /* [n_lines][K] */
+} epr_xspec;
+
+/* Give the plan an x-dependent spectrum (table != NULL; host arrays, copied)
+ * or return it to the uniform spectrum it was created with (NULL).  While a
+ * table is set, epr_forward (model EPR_MODEL_NONLOCAL), epr_adjoint,
+ * epr_precondition and epr_solve_nonlocal use it; the local solves, the
+ * second-order model, epr_vjp and oversampled plans return
+ * EPR_ERR_INVALID_ARG.  Synchronises the device.  EPR_ERR_INVALID_ARG for a
+ * malformed table or a column without an absorbing line. */
+epr_status epr_plan_set_xspec(epr_plan_t plan, const epr_xspec* table);
+
 /* Release the plan and its device workspace (synchronises the device). */
 void epr_plan_destroy(epr_plan_t plan);
 
 /* Forward model: P = sum_s F_s[f_s exp(-mu_s T)] for `batch` projections
  * (Eq. 5).  Ps (may be NULL) receives the per-line predictions
- * [batch][n_lines][ny][nx].  model is an epr_model.  Splat targets outside the
- * grid are dropped. */
+ * [batch][n_lines][ny][nx].  model is an epr_model (0..3).  Splat targets
+ * outside the grid are dropped. */
 epr_status epr_forward(epr_plan_t plan, const float* T, float* P, float* Ps, int batch,
                        int model, void* stream);
 
@@ -184,6 +222,14 @@ epr_status epr_precondition(epr_plan_t plan, float* g, int line, int batch, void
  * Without info the same conditions are read by epr_check_device_status. */
 epr_status epr_solve_nonlocal(epr_plan_t plan, const float* D, float* T, int batch,
                               const epr_solve_opts* opts, epr_solve_info* info, void* stream);
+
+/* Non-local solve with the second-order model EPR_MODEL_NONLOCAL_WKB1 as
+ * forward model: the iteration of epr_solve_nonlocal (same back-transport,
+ * the transport's adjoint of Eq. 4), with the diffraction-pressure term of
+ * Eq. 1 added to every line's prediction before the residual is formed.
+ * Arguments, synchronisation and status codes as epr_solve_nonlocal. */
+epr_status epr_solve_nonlocal_wkb1(epr_plan_t plan, const float* D, float* T, int batch,
+                                   const epr_solve_opts* opts, epr_solve_info* info, void* stream);
 
 /* Local solve: the same iteration with the local closure of order 1 or 2
  * (Eq. 1) as forward model and the identity as back-transport. */

@@ -58,6 +58,8 @@ cudaError_t epr_launch_fx_to_float(const unsigned long long* q, float* out, size
 cudaError_t epr_launch_local(const EprConsts& C, const EprWork& W, const float* T, float* P, float* Ps,
                              int order, int batch, int check_done, cudaStream_t stream);
 cudaError_t epr_local_init();
+cudaError_t epr_launch_wkb1(const EprConsts& C, const EprWork& W, const float* T, int fixed_point,
+                            int batch, int check_done, cudaStream_t stream);
 cudaError_t epr_launch_vjp(const EprConsts& C, const float* T, const float* gbar, float* Tbar,
                            float* vx, float* vy, double* part, int nblk, int batch,
                            cudaStream_t stream);
@@ -132,6 +134,10 @@ struct epr_plan_s {
     double* vjp_part;
     double* h_vjp_part;
     int vjp_cap;
+    // x-dependent spectrum: per-column constants on the device (C.xt points
+    // here while a table is set) and the uniform preconditioner constants
+    float* xt_dev;
+    float ha_uniform[EPR_MAX_LINES], hb_uniform[EPR_MAX_LINES];
 };
 
 namespace {
@@ -344,10 +350,16 @@ struct ProfScope {
 epr_status launch_forward(epr_plan_s* p, const float* T, const float* D, int parity, int batch,
                           int model, int check_done, cudaStream_t s)
 {
-    if (model == EPR_MODEL_NONLOCAL) {
-        ProfScope ps(p, EPR_KERNEL_SPLAT, s);
-        EPR_TRY(epr_launch_splat(p->C, p->W, T, D, D != nullptr, parity, batch, p->splat_TH,
-                                 p->splat_TW, check_done, s));
+    if (model == EPR_MODEL_NONLOCAL || model == EPR_MODEL_NONLOCAL_WKB1) {
+        {
+            ProfScope ps(p, EPR_KERNEL_SPLAT, s);
+            EPR_TRY(epr_launch_splat(p->C, p->W, T, D, D != nullptr, parity, batch, p->splat_TH,
+                                     p->splat_TW, check_done, s));
+        }
+        if (model == EPR_MODEL_NONLOCAL_WKB1) {   // second-order term: float P, P_s after it
+            ProfScope ps(p, EPR_KERNEL_LOCAL, s);
+            EPR_TRY(epr_launch_wkb1(p->C, p->W, T, p->C.det, batch, check_done, s));
+        }
     } else {
         ProfScope ps(p, EPR_KERNEL_LOCAL, s);
         EPR_TRY(epr_launch_local(p->C, p->W, T, p->W.P, p->W.Ps, model, batch, check_done, s));
@@ -371,12 +383,16 @@ epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, cons
         const size_t npd = npix / ((size_t)C.os * C.os);
         EPR_TRY(epr_launch_dnorm(C, p->W, D, batch, npd, (double)C.os * C.os, s));
     }
-    const int fwd_mode = model == EPR_MODEL_NONLOCAL ? 0 : 1;
+    // the non-local models back-transport with the gather, the local closures
+    // with the identity
+    const bool nonlocal = model == EPR_MODEL_NONLOCAL || model == EPR_MODEL_NONLOCAL_WKB1;
+    const int fwd_mode = nonlocal ? 0 : 1;
     // the residual D - P (and its split over the lines) is stored by the
-    // splat flush (non-local, one line, float accumulation) or by the split
-    // kernel after the forward (several lines, fixed point, local closure)
-    const bool nl = model == EPR_MODEL_NONLOCAL;
-    const bool resid_in_splat = nl && C.ns == 1 && !C.det && C.os == 1;
+    // splat flush (plain non-local model, one line, float accumulation) or by
+    // the split kernel after the forward (several lines, fixed point, local
+    // closure, second-order non-local model)
+    const bool nl = model == EPR_MODEL_NONLOCAL;   // P still in the splat's own format
+    const bool resid_in_splat = nl && C.ns == 1 && !C.det && C.os == 1 && !C.xt;
     const float eps = (float)(o->eps_I > 0 ? o->eps_I : 1e-8);
     for (int it = 0; it < o->n_iter; ++it) {
         epr_status st = launch_forward(p, T, resid_in_splat ? D : nullptr, it & 1, batch, model, 1, s);
@@ -457,7 +473,7 @@ epr_status collect_info(epr_plan_s* p, int batch, int n_iter, epr_solve_info* in
 epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int batch, cudaStream_t s)
 {
     p->tuned = true;
-    const bool resid = p->C.ns == 1 && !p->C.det && p->C.os == 1;
+    const bool resid = p->C.ns == 1 && !p->C.det && p->C.os == 1 && !p->C.xt;
     const int tiles[4][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}};
     const int reaches[3] = {3, 4, 6};
     const EprConsts saved = p->C;
@@ -514,6 +530,7 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
 {
     if (!p || !D || !T || !o || batch <= 0 || o->n_iter < 0 || !(o->omega > 0.0) || o->tol < 0.0)
         return EPR_ERR_INVALID_ARG;
+    if (p->C.xt && model != EPR_MODEL_NONLOCAL) return EPR_ERR_INVALID_ARG;
     if (!aligned16(D) || !aligned16(T)) return EPR_ERR_INVALID_ARG;
     EPR_TRY(cudaSetDevice(p->device));
     const size_t n = (size_t)batch * p->C.nx * p->C.ny;
@@ -717,6 +734,10 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
         return EPR_ERR_INVALID_ARG;  // no line both weighted and absorbing
     }
     for (int s = 0; s < n_lines; ++s) C.wproj[s] = (float)(f[s] * mu[s] / den);
+    for (int s = 0; s < n_lines; ++s) {
+        p->ha_uniform[s] = C.ha[s];
+        p->hb_uniform[s] = C.hb[s];
+    }
 
     epr_status st = init_kernels(p->device);
     if (st != EPR_OK) {
@@ -768,6 +789,7 @@ void epr_plan_destroy(epr_plan_t p)
     if (p->vjp_vy) cudaFree(p->vjp_vy);
     if (p->vjp_part) cudaFree(p->vjp_part);
     if (p->h_vjp_part) cudaFreeHost(p->h_vjp_part);
+    if (p->xt_dev) cudaFree(p->xt_dev);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto& r : p->recs) {
         cudaEventDestroy(r.a);
@@ -780,7 +802,8 @@ void epr_plan_destroy(epr_plan_t p)
 epr_status epr_forward(epr_plan_t p, const float* T, float* P, float* Ps, int batch, int model,
                        void* stream)
 {
-    if (!p || !T || !P || batch <= 0 || model < 0 || model > 2) return EPR_ERR_INVALID_ARG;
+    if (!p || !T || !P || batch <= 0 || model < 0 || model > 3) return EPR_ERR_INVALID_ARG;
+    if (p->C.xt && model != EPR_MODEL_NONLOCAL) return EPR_ERR_INVALID_ARG;
     if (!aligned16(T) || !aligned16(P) || (Ps && !aligned16(Ps))) return EPR_ERR_INVALID_ARG;
     EPR_TRY(cudaSetDevice(p->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -874,6 +897,12 @@ epr_status epr_solve_nonlocal(epr_plan_t p, const float* D, float* T, int batch,
     return solve_common(p, D, T, batch, EPR_MODEL_NONLOCAL, opts, info, (cudaStream_t)stream);
 }
 
+epr_status epr_solve_nonlocal_wkb1(epr_plan_t p, const float* D, float* T, int batch,
+                                   const epr_solve_opts* opts, epr_solve_info* info, void* stream)
+{
+    return solve_common(p, D, T, batch, EPR_MODEL_NONLOCAL_WKB1, opts, info, (cudaStream_t)stream);
+}
+
 epr_status epr_solve_local(epr_plan_t p, const float* D, float* T, int batch, int order,
                            const epr_solve_opts* opts, epr_solve_info* info, void* stream)
 {
@@ -885,7 +914,7 @@ epr_status epr_vjp(epr_plan_t p, const float* T, const float* gbar, float* Tbar,
                    double* delta_bar, double* beta_bar, double* L_bar, int batch, void* stream)
 {
     if (!p || !T || !gbar || !Tbar || batch <= 0) return EPR_ERR_INVALID_ARG;
-    if (p->C.nx < 3 || p->C.ny < 3 || p->C.os > 1) return EPR_ERR_INVALID_ARG;
+    if (p->C.nx < 3 || p->C.ny < 3 || p->C.os > 1 || p->C.xt) return EPR_ERR_INVALID_ARG;
     EPR_TRY(cudaSetDevice(p->device));
     cudaStream_t s = (cudaStream_t)stream;
     const EprConsts& C = p->C;
@@ -943,6 +972,97 @@ epr_status epr_vjp(epr_plan_t p, const float* T, const float* gbar, float* Tbar,
             }
             if (L_bar) L_bar[b] = lbar;
         }
+    }
+    return EPR_OK;
+}
+
+epr_status epr_plan_set_xspec(epr_plan_t p, const epr_xspec* tab)
+{
+    if (!p) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    EprConsts& C = p->C;
+    const int ns = C.ns, nx = C.nx;
+    if (!tab) {   // back to the uniform spectrum of the plan
+        EPR_TRY(cudaDeviceSynchronize());
+        if (p->xt_dev) cudaFree(p->xt_dev);
+        p->xt_dev = nullptr;
+        C.xt = nullptr;
+        for (int s = 0; s < ns; ++s) {
+            C.ha[s] = p->ha_uniform[s];
+            C.hb[s] = p->hb_uniform[s];
+        }
+    } else {
+        const int K = tab->n_knots;
+        if (K < 1 || !tab->x_knots || !tab->weights || !tab->delta || !tab->beta || C.os > 1)
+            return EPR_ERR_INVALID_ARG;
+        for (int k = 0; k < K; ++k)
+            if (!isfinite(tab->x_knots[k]) || (k > 0 && !(tab->x_knots[k] > tab->x_knots[k - 1])))
+                return EPR_ERR_INVALID_ARG;
+        for (int i = 0; i < ns * K; ++i)
+            if (!(tab->weights[i] > 0.0) || !isfinite(tab->weights[i]) || !(tab->beta[i] >= 0.0) ||
+                !isfinite(tab->beta[i]) || !isfinite(tab->delta[i]))
+                return EPR_ERR_INVALID_ARG;
+        // each knot value at column x: linear between the knots around x,
+        // constant beyond the first and the last
+        auto at = [&](const double* v, double x) {
+            const double* X = tab->x_knots;
+            if (x <= X[0]) return v[0];
+            if (x >= X[K - 1]) return v[K - 1];
+            int k = 1;
+            while (X[k] < x) ++k;   // X[k - 1] < x <= X[k]
+            const double t = (x - X[k - 1]) / (X[k] - X[k - 1]);
+            return v[k - 1] + t * (v[k] - v[k - 1]);
+        };
+        const double kPi = 3.14159265358979323846;
+        std::vector<float> h((size_t)EPR_XT_KINDS * ns * nx);
+        std::vector<double> f(ns), mu(ns), dl(ns), mu_mean(ns, 0.0), ld_mean(ns, 0.0);
+        auto put = [&](int kind, int s, int x, double v) {
+            h[((size_t)kind * ns + s) * nx + x] = (float)v;
+        };
+        for (int x = 0; x < nx; ++x) {
+            double wsum = 0.0, den = 0.0;
+            for (int s = 0; s < ns; ++s) {
+                f[s] = at(tab->weights + (size_t)s * K, (double)x);
+                wsum += f[s];
+            }
+            for (int s = 0; s < ns; ++s) {
+                const double lam = kHcEvM / (p->E[s] * 1e3);
+                const double k = 2.0 * kPi / lam;
+                f[s] /= wsum;
+                mu[s] = 2.0 * k * at(tab->beta + (size_t)s * K, (double)x);
+                dl[s] = at(tab->delta + (size_t)s * K, (double)x);
+                den += f[s] * mu[s] * mu[s];
+                mu_mean[s] += mu[s] / nx;
+                ld_mean[s] += p->L * dl[s] / nx;
+            }
+            if (!(den > 0.0)) return EPR_ERR_INVALID_ARG;   // no absorbing line in column x
+            for (int s = 0; s < ns; ++s) {
+                put(EPR_XT_F, s, x, f[s]);
+                put(EPR_XT_MU, s, x, mu[s]);
+                put(EPR_XT_C, s, x, -p->L * dl[s] / (p->pixel * p->pixel));
+                put(EPR_XT_WPROJ, s, x, f[s] * mu[s] / den);
+                put(EPR_XT_TNEG, s, x, mu[s] > 0.0 ? -0.6931471805599453 / mu[s] : -3.0e38);
+            }
+        }
+        EPR_TRY(cudaDeviceSynchronize());
+        if (!p->xt_dev) EPR_TRY(cudaMalloc((void**)&p->xt_dev, h.size() * sizeof(float)));
+        EPR_TRY(cudaMemcpy(p->xt_dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+        C.xt = p->xt_dev;
+        // the preconditioner must be FFT-diagonal: each line's column means
+        const double fx1 = 1.0 / (nx * p->pixel), fy1 = 1.0 / (C.ny * p->pixel);
+        for (int s = 0; s < ns; ++s) {
+            C.ha[s] = mu_mean[s] > 0.0 ? (float)(ld_mean[s] * 4.0 * kPi * kPi * fx1 * fx1 / mu_mean[s]) : 0.f;
+            C.hb[s] = mu_mean[s] > 0.0 ? (float)(ld_mean[s] * 4.0 * kPi * kPi * fy1 * fy1 / mu_mean[s]) : 0.f;
+        }
+    }
+    // kernels take the constants by value: cached graphs are stale
+    if (p->has_graph) {
+        cudaGraphExecDestroy(p->gexec);
+        p->has_graph = false;
+    }
+    if (p->prof_exec) {
+        cudaGraphExecDestroy(p->prof_exec);
+        p->prof_exec = nullptr;
     }
     return EPR_OK;
 }

@@ -42,7 +42,21 @@ struct EprConsts {
     float hb[EPR_MAX_LINES];    // Paganin: L delta 4 pi^2 / (mu (ny p)^2)
     float qc[EPR_MAX_LINES];    // local closure: eps^2 / (4 p^4), eps = L / k
     float tneg[EPR_MAX_LINES];  // -ln 2 / mu: below it f exp(-mu T) > 2 f (splat bound)
+    const float* xt;     // x-dependent spectrum: per-column constants
+                         // [EPR_XT_KINDS][ns][nx] in device memory, or NULL
+                         // (the uniform constants above)
 };
+
+// Kinds of the per-column table of an x-dependent spectrum.  f, mu, c, wproj
+// and tneg as above, per line and detector column; the preconditioner's ha,
+// hb stay per line (from the column means).
+enum { EPR_XT_F = 0, EPR_XT_MU = 1, EPR_XT_C = 2, EPR_XT_WPROJ = 3, EPR_XT_TNEG = 4,
+       EPR_XT_KINDS = 5 };
+
+__device__ __forceinline__ float xt_get(const EprConsts& C, int kind, int s, int x)
+{
+    return __ldg(&C.xt[((size_t)kind * C.ns + s) * C.nx + x]);
+}
 
 // Per-projection solver state in device memory.
 struct EprProjState {

@@ -34,7 +34,7 @@ __global__ void k_gather(const EprConsts C, const float* __restrict__ T, const f
     const size_t pb = (size_t)b * nx * ny;
     const float* Tb = T + pb;
     const float* rb = r + pb;
-    const float cs = C.c[line];
+    const float cs = C.xt ? xt_get(C, EPR_XT_C, line, x) : C.c[line];
     const float lim = 2.f * (float)(nx > ny ? nx : ny);
     const float ux = fminf(fmaxf(cs * grad_g(Tb, y, x, ny, nx, true), -lim), lim);
     const float uy = fminf(fmaxf(cs * grad_g(Tb, y, x, ny, nx, false), -lim), lim);

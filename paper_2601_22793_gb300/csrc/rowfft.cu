@@ -143,7 +143,8 @@ __device__ __forceinline__ float gather_px(const EprConsts& C, const RowArgs& A,
     return (1.f - dy) * top + dy * bot;
 }
 
-template <int MODE, bool DET, bool RESID, int NS>
+// XT: an x-dependent spectrum, the shift constant read per object column.
+template <int MODE, bool DET, bool RESID, int NS, bool XT = false>
 __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const RowArgs A)
 {
     extern __shared__ __align__(16) float2 zs[];
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(512, 2) k_row_fwd(const EprConsts C, const Row
                     if (y == 0) gy = tr[nx + x] - t;
                     else if (y == ny - 1) gy = t - tr[x - nx];
                     else gy = 0.5f * (tr[nx + x] - tr[x - nx]);
-                    const float cs = line_const(C.c, s);
+                    const float cs = XT ? xt_get(C, EPR_XT_C, s, x) : line_const(C.c, s);
                     v[r0] = gather_px<DET, RESID>(C, A, pb, y, x, cs * gy, cs * gx, s);
                 } else if constexpr (MODE == FWD_SOLVE_LOCAL) {
                     v[r0] = resid<DET, RESID>(C, A, pb, (size_t)y * nx + x, s);
@@ -290,7 +291,8 @@ __device__ __forceinline__ float log_ratio(float t, float h, float om_f, float m
     return logf(eps) + mus * t;
 }
 
-template <int MODE, int NS>
+// XT: an x-dependent spectrum, the update's constants read per column.
+template <int MODE, int NS, bool XT = false>
 __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const RowArgs A)
 {
     extern __shared__ __align__(16) float2 zs[];
@@ -339,8 +341,10 @@ __global__ void __launch_bounds__(512, 2) k_row_inv(const EprConsts C, const Row
             const float2 h = zs[PR::idx(m * sm + x)];
             const size_t q0 = pb + (size_t)(yb + 2 * m) * nx + x;
             if constexpr (MODE == INV_UPDATE) {
-                const float fs = line_const(C.f, s), mus = line_const(C.mu, s),
-                            w = line_const(C.wproj, s), om_f = A.omega / fs;
+                const float fs = XT ? xt_get(C, EPR_XT_F, s, x) : line_const(C.f, s);
+                const float mus = XT ? xt_get(C, EPR_XT_MU, s, x) : line_const(C.mu, s);
+                const float w = XT ? xt_get(C, EPR_XT_WPROJ, s, x) : line_const(C.wproj, s);
+                const float om_f = A.omega / fs;
                 const float t0 = A.Out[q0], t1 = A.Out[q0 + nx];
                 const float l0 = w * log_ratio(t0, h.x, om_f, mus, A.eps);
                 const float l1 = w * log_ratio(t1, h.y, om_f, mus, A.eps);
@@ -879,7 +883,9 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, c
     const bool mono = nl == 1, pdl = C.pdl != 0;
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kernel) { e = epr_launch_kernel(pdl, kernel, grid, blk, L.smem, stream, C, A); };
-    if (mode == FWD_SOLVE_NL) {
+    if (mode == FWD_SOLVE_NL && C.xt) {
+        go(k_row_fwd<FWD_SOLVE_NL, false, true, 0, true>);   // per-column shift constants
+    } else if (mode == FWD_SOLVE_NL) {
         // the residual D - P is in P and, with several lines, the split
         // residuals in P_s (written by the splat flush or the split kernel)
         if (!launch_mono_ct<true>(C.nx, L.RP, grid, L.smem, stream, C, A, e)) {
@@ -911,7 +917,9 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
     const bool pdl = C.pdl != 0;
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kernel) { e = epr_launch_kernel(pdl, kernel, grid, blk, L.smem, stream, C, A); };
-    if (mode == INV_UPDATE) {
+    if (mode == INV_UPDATE && C.xt) {
+        go(k_row_inv<INV_UPDATE, 0, true>);   // per-column update constants
+    } else if (mode == INV_UPDATE) {
         if (launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A, e)) {
         } else if (nl == 1) go(k_row_inv<INV_UPDATE, 1>);
         else go(k_row_inv<INV_UPDATE, 0>);
@@ -979,6 +987,8 @@ cudaError_t epr_row_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 1>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 0>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_STORE, 1>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_fwd<FWD_SOLVE_NL, false, true, 0, true>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_row_inv<INV_UPDATE, 0, true>);
     if (e == cudaSuccess) e = init_mono_ct();
     return e;
 }

@@ -104,7 +104,9 @@ constexpr int kQuad = 4;   // sources per scan work item
 // Five blocks per SM (48 registers; a 64 x 64 tile at reach 4 takes 44 KB of
 // shared memory); the mono residual kernel with a runtime reach needs more
 // registers and runs four.
-template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0>
+// XT: an x-dependent spectrum, the line constants read per source column
+// from the plan's table (runtime line count and reach only).
+template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0, bool XT = false>
 __global__ void __launch_bounds__(kSplatThreads, (NS == 1 && RESID && RC == 0) ? 4 : 5)
 k_splat(const EprConsts C, const SplatArgs A)
 {
@@ -193,17 +195,21 @@ k_splat(const EprConsts C, const SplatArgs A)
     // them: 0.5 scales exactly, so u is the same float.
     auto source = [&](int ly, int lx, float t, float gx2, float gy2) {
         unsigned int far = 0u;
+        const int sxc = XT ? tx0 - R + lx : 0;   // source column (inside the grid)
 #pragma unroll(NS ? NS : 1)
         for (int s = 0; s < ns; ++s) {
-            const float ch = 0.5f * C.c[s];
+            const float ch = 0.5f * (XT ? xt_get(C, EPR_XT_C, s, sxc) : C.c[s]);
             const float ux = ch * gx2, uy = ch * gy2;
-            if (fabsf(ux) <= fsmax && fabsf(uy) <= fsmax && t >= C.tneg[s]) {
+            const float tneg = XT ? xt_get(C, EPR_XT_TNEG, s, sxc) : C.tneg[s];
+            if (fabsf(ux) <= fsmax && fabsf(uy) <= fsmax && t >= tneg) {
                 const float fx = floorf(ux), fy = floorf(uy);
                 const int cx = lx - R + (int)fx, cy = ly - R + (int)fy;  // corner 00, tile-local
                 // all four corners have a slot (apron) when one is in the tile
                 if ((unsigned)(cx + 1) <= (unsigned)TW && (unsigned)(cy + 1) <= (unsigned)TH) {
                     const float dx = ux - fx, dy = uy - fy;
-                    const float m = (C.f[s] * fxs) * __expf(-C.mu[s] * t);   // 2^S f e^(-mu t)
+                    const float fs = XT ? xt_get(C, EPR_XT_F, s, sxc) : C.f[s];
+                    const float mus = XT ? xt_get(C, EPR_XT_MU, s, sxc) : C.mu[s];
+                    const float m = (fs * fxs) * __expf(-mus * t);   // 2^S f e^(-mu t)
                     const float mx1 = m * dx, mx0 = m - mx1;          // m (1 - dx), m dx
                     const float w = 1.f - dy;
                     const int idx = s * ACC + (cy + 1) * AP + (cx + 1);
@@ -356,7 +362,7 @@ k_splat(const EprConsts C, const SplatArgs A)
 }
 
 // The long-shift sources of the overflow list, added with global atomics.
-template <bool DET, bool RESID>
+template <bool DET, bool RESID, bool XT = false>
 __global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const SplatArgs A)
 {
     const int b = blockIdx.y;
@@ -393,11 +399,13 @@ __global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const
         const float t = tg.x;
         for (int s = 0; s < ns; ++s) {
             if (!((mask >> s) & 1u)) continue;
-            const float ch = 0.5f * C.c[s];
+            const float ch = 0.5f * (XT ? xt_get(C, EPR_XT_C, s, sx) : C.c[s]);
             const float ux = ch * tg.y, uy = ch * tg.z;
             const float fx = floorf(ux), fy = floorf(uy);
             const float dx = ux - fx, dy = uy - fy;
-            const float m = C.f[s] * __expf(-C.mu[s] * t);
+            const float fs = XT ? xt_get(C, EPR_XT_F, s, sx) : C.f[s];
+            const float mus = XT ? xt_get(C, EPR_XT_MU, s, sx) : C.mu[s];
+            const float m = fs * __expf(-mus * t);
             const float w[4] = {(1.f - dx) * (1.f - dy), dx * (1.f - dy), (1.f - dx) * dy, dx * dy};
             // corner coordinates in float first: a huge shift must not wrap an int
             const float cxf = (float)sx + fx, cyf = (float)sy + fy;
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const
 // overflow sources are in: P <- D - P and P_s <- (D - P) P_s / P as float
 // maps, so that the adjoint gather reads one value per corner and line.  In
 // fixed-point mode the sums are read from the integer maps.
-template <bool DET>
+template <bool DET, bool XT = false>
 __global__ void __launch_bounds__(256) k_split(const EprConsts C, const SplatArgs A)
 {
     const int b = blockIdx.y;
@@ -443,7 +451,8 @@ __global__ void __launch_bounds__(256) k_split(const EprConsts C, const SplatArg
         for (int s = 0; ns > 1 && s < ns; ++s) {   // one line: r itself
             const size_t o = (pb * ns) + (size_t)s * npix + q;
             const float pl = DET ? (float)A.Psq[o] * EPR_FX_INV : A.Ps[o];
-            A.Ps[o] = (p > 1e-30f) ? r * (pl / p) : r * line_const(C.f, s);
+            const float fs = XT ? xt_get(C, EPR_XT_F, s, (int)(q % (size_t)C.nx)) : line_const(C.f, s);
+            A.Ps[o] = (p > 1e-30f) ? r * (pl / p) : r * fs;
         }
         A.P[pb + q] = r;
     }
@@ -542,15 +551,15 @@ __global__ void __launch_bounds__(256) k_bin_os(const EprConsts C, const SplatAr
     }
 }
 
-template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0>
+template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0, bool XT = false>
 cudaError_t launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
                      cudaStream_t stream)
 {
     const bool pdl = C.pdl != 0;
-    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID, TH, TW, RC>, grid,
+    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID, TH, TW, RC, XT>, grid,
                                             dim3(kSplatThreads), smem, stream, C, A);
     if (e != cudaSuccess) return e;
-    return epr_launch_kernel(pdl, k_splat_overflow<DET, RESID>, dim3(128, batch), dim3(128), 0,
+    return epr_launch_kernel(pdl, k_splat_overflow<DET, RESID, XT>, dim3(128, batch), dim3(128), 0,
                              stream, C, A);
 }
 
@@ -559,6 +568,9 @@ cudaError_t launch_shape(const EprConsts& C, const SplatArgs& A, int resid, dim3
                          int batch, cudaStream_t stream)
 {
     const bool mono = C.ns == 1;
+    if (C.xt)   // x-dependent spectrum: the generic kernels with per-column constants
+        return C.det ? launch_t<0, true, false, TH, TW, 0, true>(C, A, grid, smem, batch, stream)
+                     : launch_t<0, false, false, TH, TW, 0, true>(C, A, grid, smem, batch, stream);
     if (C.det)
         return mono ? launch_t<1, true, false, TH, TW>(C, A, grid, smem, batch, stream)
                     : launch_t<0, true, false, TH, TW>(C, A, grid, smem, batch, stream);
@@ -593,6 +605,8 @@ cudaError_t init_shape()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 3>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 4>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 6>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, true, false, TH, TW, 0, true>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 0, true>);
     return e;
 }
 
@@ -674,9 +688,13 @@ cudaError_t epr_launch_split(const EprConsts& C, const EprWork& W, const float* 
     size_t blocks = (npix + 255) / 256;
     if (blocks > 1216) blocks = 1216;   // 8 per SM on 152 SMs, grid-stride beyond
     const dim3 grid((unsigned)blocks, batch);
-    const cudaError_t e =
-        fixed_point ? epr_launch_kernel(C.pdl != 0, k_split<true>, grid, dim3(256), 0, stream, C, A)
-                    : epr_launch_kernel(C.pdl != 0, k_split<false>, grid, dim3(256), 0, stream, C, A);
+    cudaError_t e;
+    if (C.xt)
+        e = fixed_point ? epr_launch_kernel(C.pdl != 0, k_split<true, true>, grid, dim3(256), 0, stream, C, A)
+                        : epr_launch_kernel(C.pdl != 0, k_split<false, true>, grid, dim3(256), 0, stream, C, A);
+    else
+        e = fixed_point ? epr_launch_kernel(C.pdl != 0, k_split<true>, grid, dim3(256), 0, stream, C, A)
+                        : epr_launch_kernel(C.pdl != 0, k_split<false>, grid, dim3(256), 0, stream, C, A);
     epr_count_launch(1);
     return e != cudaSuccess ? e : cudaGetLastError();
 }

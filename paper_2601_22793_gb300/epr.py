@@ -34,12 +34,14 @@ EPR_ERR_SHIFT_OVERFLOW = 8
 EPR_MODEL_NONLOCAL = 0
 EPR_MODEL_LOCAL1 = 1
 EPR_MODEL_LOCAL2 = 2
+EPR_MODEL_NONLOCAL_WKB1 = 3
 
 SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
-           "epr_precondition", "epr_solve_nonlocal", "epr_solve_local",
+           "epr_precondition", "epr_solve_nonlocal", "epr_solve_nonlocal_wkb1", "epr_solve_local",
            "epr_check_device_status", "epr_status_string", "epr_launch_count",
            "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc", "epr_vjp",
-           "epr_batch_create", "epr_batch_destroy", "epr_solve_nonlocal_batched")
+           "epr_batch_create", "epr_batch_destroy", "epr_solve_nonlocal_batched",
+           "epr_plan_set_xspec")
 
 KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 
@@ -54,6 +56,13 @@ class epr_options(ctypes.Structure):
 class epr_batch_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("D", ctypes.c_void_p),
                 ("T", ctypes.c_void_p)]
+
+
+class epr_xspec(ctypes.Structure):
+    _fields_ = [("n_knots", ctypes.c_int), ("x_knots", ctypes.POINTER(ctypes.c_double)),
+                ("weights", ctypes.POINTER(ctypes.c_double)),
+                ("delta", ctypes.POINTER(ctypes.c_double)),
+                ("beta", ctypes.POINTER(ctypes.c_double))]
 
 
 class epr_solve_opts(ctypes.Structure):
@@ -103,6 +112,9 @@ def load(path: str | None = None):
         lib.epr_solve_nonlocal.argtypes = [vp, vp, vp, i, ctypes.POINTER(epr_solve_opts),
                                            ctypes.POINTER(epr_solve_info), vp]
         lib.epr_solve_nonlocal.restype = i
+        lib.epr_solve_nonlocal_wkb1.argtypes = [vp, vp, vp, i, ctypes.POINTER(epr_solve_opts),
+                                                ctypes.POINTER(epr_solve_info), vp]
+        lib.epr_solve_nonlocal_wkb1.restype = i
         lib.epr_solve_local.argtypes = [vp, vp, vp, i, i, ctypes.POINTER(epr_solve_opts),
                                         ctypes.POINTER(epr_solve_info), vp]
         lib.epr_solve_local.restype = i
@@ -127,6 +139,8 @@ def load(path: str | None = None):
                                                    ctypes.POINTER(epr_solve_opts),
                                                    ctypes.POINTER(epr_solve_info), vp]
         lib.epr_solve_nonlocal_batched.restype = i
+        lib.epr_plan_set_xspec.argtypes = [vp, ctypes.POINTER(epr_xspec)]
+        lib.epr_plan_set_xspec.restype = i
         lib.epr_launch_count.argtypes = []
         lib.epr_launch_count.restype = ctypes.c_longlong
         _lib = lib
@@ -205,6 +219,21 @@ def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
     return h.value
 
 
+def epr_plan_set_xspec(plan, x_knots=None, weights=None, delta=None, beta=None):
+    """x-dependent spectrum: knot columns [K] and per-line tables [n_lines][K]
+    of weights, delta, beta (see the C header).  x_knots None returns the plan
+    to its uniform spectrum."""
+    if x_knots is None:
+        _check(load().epr_plan_set_xspec(plan, None), "epr_plan_set_xspec")
+        return
+    X, Xp = _darr(x_knots)
+    w, wp = _darr(np.ravel(weights))
+    d, dp_ = _darr(np.ravel(delta))
+    b, bp = _darr(np.ravel(beta))
+    tab = epr_xspec(int(X.size), Xp, wp, dp_, bp)
+    _check(load().epr_plan_set_xspec(plan, ctypes.byref(tab)), "epr_plan_set_xspec")
+
+
 def epr_plan_destroy(plan):
     load().epr_plan_destroy(plan)
 
@@ -276,6 +305,20 @@ def epr_solve_nonlocal(plan, D, T, batch=1, n_iter=20, omega=1.0, tol=0.0, eps_I
                                    ctypes.byref(info) if info is not None else None,
                                    _stream(stream))
     _check(st, "epr_solve_nonlocal")
+    if arrs is not None:
+        arrs["overflow_sources"] = int(info.overflow_sources)
+    return arrs
+
+
+def epr_solve_nonlocal_wkb1(plan, D, T, batch=1, n_iter=20, omega=1.0, tol=0.0, eps_I=1e-8,
+                            init=0, want_info=True, stream=None):
+    """The non-local solve with the second-order forward model (see the C header)."""
+    opts = _solve_opts(n_iter, omega, tol, eps_I, init)
+    info, arrs = _info(batch, n_iter) if want_info else (None, None)
+    st = load().epr_solve_nonlocal_wkb1(plan, _ptr(D), _ptr(T), int(batch), ctypes.byref(opts),
+                                        ctypes.byref(info) if info is not None else None,
+                                        _stream(stream))
+    _check(st, "epr_solve_nonlocal_wkb1")
     if arrs is not None:
         arrs["overflow_sources"] = int(info.overflow_sources)
     return arrs

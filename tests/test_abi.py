@@ -13,7 +13,7 @@ def _declared():
     with open(os.path.join(ROOT, "include", "epr.h")) as f:
         src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(epr_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(epr_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
