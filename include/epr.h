@@ -179,6 +179,15 @@ typedef struct {
  * malformed table or a column without an absorbing line. */
 epr_status epr_plan_set_xspec(epr_plan_t plan, const epr_xspec* table);
 
+/* New L, delta_s and beta_s for an existing plan (host arrays of n_lines),
+ * keeping its grid, energies, weights, options and workspace: the per-line
+ * constants are derived again and nothing is allocated, so a calibration
+ * loop can change them every step.  Cached solve graphs are dropped (work
+ * already queued keeps the old constants).  EPR_ERR_INVALID_ARG for invalid
+ * values, for values that leave no line both weighted and absorbing, or
+ * while an x-dependent spectrum is set. */
+epr_status epr_plan_set_params(epr_plan_t plan, double L_m, const double* delta, const double* beta);
+
 /* Release the plan and its device workspace (synchronises the device). */
 void epr_plan_destroy(epr_plan_t plan);
 
@@ -206,6 +215,33 @@ epr_status epr_adjoint(epr_plan_t plan, const float* T, const float* r, float* g
  * buffers are requested. */
 epr_status epr_vjp(epr_plan_t plan, const float* T, const float* gbar, float* Tbar,
                    double* delta_bar, double* beta_bar, double* L_bar, int batch, void* stream);
+
+/* Reverse mode through the unrolled non-local solve (not in the paper: the
+ * calibration of L, delta_s and beta_s by gradient descent through a fixed
+ * number of iterations of "Iteration structure").  Runs n_iter iterations of
+ * epr_solve_nonlocal from T0 (NULL = the flat field, T := 0) on the data D,
+ * without early stop, with relaxation omega and floor eps_I, and for
+ * F = <Tbar, tau_N> returns dF/dT0, dF/dD and, per projection and line,
+ * dF/ddelta_s, dF/dbeta_s and dF/dL.  Each iteration is recomputed from its
+ * iterate and undone step by step: the projection and the floor of the
+ * update (no gradient at the floor), the preconditioner (self-adjoint, and
+ * its symbol's dependence on mu_s and L delta_s), the adjoint transport, the
+ * residual split, the transport and the intensity and shift of each line.
+ * The iterates are kept every checkpoint_every iterations (0 or 1 = every
+ * one; m > 1 keeps n_iter / m + 1 of them and recomputes the others one
+ * segment at a time, for less memory).  Where a mapped point sits exactly on
+ * a pixel boundary the right derivative is taken.
+ * D, T0, Tbar [batch][ny][nx] and the outputs T_out (tau_N), T0_bar, D_bar
+ * (each may be NULL) are device memory; delta_bar, beta_bar [batch][n_lines]
+ * and L_bar [batch] are host arrays (may be NULL; when any is given the call
+ * synchronises the stream).  Needs mu_s > 0 and L delta_s > 0 for every line,
+ * and a plan without oversampling or x-dependent spectrum
+ * (EPR_ERR_INVALID_ARG otherwise).  The plan holds the iterates and about
+ * 6 n_lines + 8 maps per projection of workspace, allocated on first use. */
+epr_status epr_solve_vjp(epr_plan_t plan, const float* D, const float* T0, int batch, int n_iter,
+                         double omega, double eps_I, int checkpoint_every, const float* Tbar,
+                         float* T_out, float* T0_bar, float* D_bar, double* delta_bar,
+                         double* beta_bar, double* L_bar, void* stream);
 
 /* Paganin-type preconditioner of line `line`, in place: g <- Re F^-1[H_s F[g]],
  * periodic, no padding. */

@@ -36,7 +36,22 @@ struct ColArgs {
     int check_done;
     int rho_it;           // >= 0: block 0 forms rho of this iteration
     int nblk, max_blocks, hist_len;
+    int kind;             // symbol of the generic pass: 0 = H = 1 / (1 + a),
+                          // 1, 2 = kscale a / (1 + a)^2 (the derivatives of
+                          // H by mu and by L delta), a = (L delta / mu) |q|^2
+    float kscale;         // 1 / mu (kind 1) or -1 / (L delta) (kind 2)
 };
+
+// Symbol of the generic column pass at a = (L delta / mu) |q|^2, times the
+// 1 / (nx ny) of the two inverse transforms.  With H = mu / (mu + L delta
+// |q|^2) = 1 / (1 + a): dH/dmu = (a / mu) / (1 + a)^2 and dH/d(L delta) =
+// -(a / (L delta)) / (1 + a)^2.
+__device__ __forceinline__ float col_symbol(const ColArgs& A, float inv_n, float a)
+{
+    if (A.kind == 0) return inv_n / (1.f + a);
+    const float d = 1.f + a;
+    return A.kscale * inv_n * a / (d * d);
+}
 
 // Block 0 of the column pass of a solve (line 0) turns the forward row
 // pass's partials into rho; the grid dependency wait has made them visible.
@@ -128,12 +143,12 @@ __global__ void __launch_bounds__(512, 2) k_col(const EprConsts C, const ColArgs
         const float qy = hb * ky * ky;
         const float2 v = buf[PC::idx(e)];
         if (kx != 0) {
-            const float H = inv_n / (1.f + ha * (float)kx * (float)kx + qy);
+            const float H = col_symbol(A, inv_n, ha * (float)kx * (float)kx + qy);
             nv[k] = cscale(v, H);
         } else {
             const float kn = (float)half;
-            const float H0 = inv_n / (1.f + qy);
-            const float HN = inv_n / (1.f + ha * kn * kn + qy);
+            const float H0 = col_symbol(A, inv_n, qy);
+            const float HN = col_symbol(A, inv_n, ha * kn * kn + qy);
             const int yneg = (y == 0) ? 0 : ny - y;
             const float2 w = cconj(buf[PC::idx((yneg << lgCW) + c)]);
             const float hp = 0.5f * (H0 + HN), hm = 0.5f * (H0 - HN);
@@ -370,6 +385,8 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     A.line0 = line0;
     A.nl = nl;
     A.check_done = check_done;
+    A.kind = 0;
+    A.kscale = 0.f;
     const dim3 grid(C.half / L.CW, nl, batch);
     const bool pdl = C.pdl != 0;
     cudaError_t e = cudaSuccess;
@@ -412,6 +429,36 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
         else
             e = epr_launch_kernel(pdl, k_col<16>, grid, dim3(L.threads), L.smem, stream, C, A);
     }
+    epr_count_launch(1);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// The generic column pass with symbol `kind` (col_symbol) for one line of a
+// batch of spectra (line slot 0 of S, the constants of line `line`): the
+// filter derivatives of the reverse pass through the solve.
+cudaError_t epr_launch_col_kind(const EprConsts& C, const EprWork& W, int line, int batch,
+                                int kind, float kscale, cudaStream_t stream)
+{
+    const EprColLaunch L = epr_col_config(C, 0);
+    ColArgs A = {};
+    A.S = W.S;
+    A.st = W.st;
+    A.tw = W.tw_y;
+    A.err = W.err;
+    A.rho_it = -1;
+    A.CW = L.CW;
+    A.lgCW = L.lgCW;
+    A.line0 = line;
+    A.nl = 1;
+    A.check_done = 0;
+    A.kind = kind;
+    A.kscale = kscale;
+    const dim3 grid(C.half / L.CW, 1, batch);
+    cudaError_t e;
+    if (L.EPT == 8)
+        e = epr_launch_kernel(false, k_col<8>, grid, dim3(L.threads), L.smem, stream, C, A);
+    else
+        e = epr_launch_kernel(false, k_col<16>, grid, dim3(L.threads), L.smem, stream, C, A);
     epr_count_launch(1);
     return e != cudaSuccess ? e : cudaGetLastError();
 }

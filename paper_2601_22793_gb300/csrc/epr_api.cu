@@ -19,6 +19,7 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include <cuda.h>
@@ -60,6 +61,27 @@ cudaError_t epr_launch_local(const EprConsts& C, const EprWork& W, const float* 
 cudaError_t epr_local_init();
 cudaError_t epr_launch_wkb1(const EprConsts& C, const EprWork& W, const float* T, int fixed_point,
                             int batch, int check_done, cudaStream_t stream);
+cudaError_t epr_launch_col_kind(const EprConsts& C, const EprWork& W, int line, int batch, int kind,
+                                float kscale, cudaStream_t stream);
+int epr_sv_blocks();
+cudaError_t epr_launch_sv_split(const EprConsts& C, const float* D, const float* P, const float* Ps,
+                                float* r, float* RS, int B, cudaStream_t s);
+cudaError_t epr_launch_sv_update_adj(const EprConsts& C, const float* T, const float* Hs, const float* tb,
+                                     float* HB, double* part, int B, float omega, float eps,
+                                     float inv_den, cudaStream_t s);
+cudaError_t epr_launch_sv_dot(const float* a, const float* b, size_t npix, double* part, int B,
+                              cudaStream_t s);
+cudaError_t epr_launch_sv_splat_field(const EprConsts& C, const float* T, const float* field, float* out,
+                                      int line, int B, cudaStream_t s);
+cudaError_t epr_launch_sv_interp_du(const EprConsts& C, int mode, const float* T, const float* e,
+                                    const float* wmap, const float* HB, float* vx, float* vy, float* tn,
+                                    double* part, int line, float omega, int B, cudaStream_t s);
+cudaError_t epr_launch_sv_split_adj(const EprConsts& C, float* RSB, const float* P, const float* Ps,
+                                    const float* r, float* Db, int B, cudaStream_t s);
+cudaError_t epr_launch_sv_gT(const EprConsts& C, const float* vx, const float* vy, float* tn, int B,
+                             cudaStream_t s);
+cudaError_t epr_launch_sv_accum(const double* part, size_t npix, int nslot, int slot, double* acc,
+                                int nacc, int slot_acc, double scale, int B, cudaStream_t s);
 cudaError_t epr_launch_vjp(const EprConsts& C, const float* T, const float* gbar, float* Tbar,
                            float* vx, float* vy, double* part, int nblk, int batch,
                            cudaStream_t stream);
@@ -138,6 +160,12 @@ struct epr_plan_s {
     // here while a table is set) and the uniform preconditioner constants
     float* xt_dev;
     float ha_uniform[EPR_MAX_LINES], hb_uniform[EPR_MAX_LINES];
+    // reverse mode through the solve (allocated on first use, kept for reuse)
+    std::vector<void*> sv_allocs;
+    int sv_batch, sv_nck, sv_nseg;
+    float *sv_r, *sv_RS, *sv_GA, *sv_H, *sv_HB, *sv_GB, *sv_TMP, *sv_RSB;
+    float *sv_tb, *sv_tn, *sv_vx, *sv_vy, *sv_Db, *sv_ck, *sv_seg;
+    double *sv_part, *sv_acc, *h_sv_acc;
 };
 
 namespace {
@@ -611,6 +639,49 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
     return EPR_OK;
 }
 
+// The per-line constants of a plan from its energies and weights (already
+// in p) and L, delta_s, beta_s, derived in double and rounded once to float.
+// Returns false when no line is both weighted and absorbing.
+bool line_constants(epr_plan_s* p, double L_m, const double* delta, const double* beta)
+{
+    EprConsts& C = p->C;
+    const int n_lines = C.ns, nx = C.nx, ny = C.ny;
+    const double pixel_m = p->pixel;
+    double wsum = 0.0;
+    for (int s = 0; s < n_lines; ++s) wsum += p->w[s];
+    double den = 0.0;
+    double mu[EPR_MAX_LINES], f[EPR_MAX_LINES];
+    EprConsts T = C;   // written back only when valid
+    for (int s = 0; s < n_lines; ++s) {
+        const double lam = kHcEvM / (p->E[s] * 1e3);
+        const double k = 2.0 * kPi / lam;
+        mu[s] = 2.0 * k * beta[s];
+        f[s] = p->w[s] / wsum;
+        den += f[s] * mu[s] * mu[s];
+        const double Ld = L_m * delta[s];
+        T.f[s] = (float)f[s];
+        T.mu[s] = (float)mu[s];
+        T.c[s] = (float)(-Ld / (pixel_m * pixel_m));
+        const double fx1 = 1.0 / (nx * pixel_m), fy1 = 1.0 / (ny * pixel_m);
+        T.ha[s] = mu[s] > 0.0 ? (float)(Ld * 4.0 * kPi * kPi * fx1 * fx1 / mu[s]) : 0.f;
+        T.hb[s] = mu[s] > 0.0 ? (float)(Ld * 4.0 * kPi * kPi * fy1 * fy1 / mu[s]) : 0.f;
+        const double eps = L_m / k;
+        T.qc[s] = (float)(eps * eps / (4.0 * pixel_m * pixel_m * pixel_m * pixel_m));
+        T.tneg[s] = mu[s] > 0.0 ? (float)(-0.6931471805599453 / mu[s]) : -3.0e38f;
+    }
+    if (!(den > 0.0)) return false;
+    for (int s = 0; s < n_lines; ++s) T.wproj[s] = (float)(f[s] * mu[s] / den);
+    C = T;
+    p->L = L_m;
+    for (int s = 0; s < n_lines; ++s) {
+        p->delta[s] = delta[s];
+        p->beta[s] = beta[s];
+        p->ha_uniform[s] = C.ha[s];
+        p->hb_uniform[s] = C.hb[s];
+    }
+    return true;
+}
+
 std::mutex g_init_mu;
 int g_init_done[64];
 
@@ -706,37 +777,13 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     C.ovf_cap = o.overflow_capacity > 0 ? o.overflow_capacity
                                         : (int)(npix / 16 > 4096 ? npix / 16 : 4096);
     C.inv_n = (float)(1.0 / ((double)nx * ny));
-    double den = 0.0;
-    double mu[EPR_MAX_LINES], f[EPR_MAX_LINES];
     for (int s = 0; s < n_lines; ++s) {
-        const double lam = kHcEvM / (energy_keV[s] * 1e3);
-        const double k = 2.0 * kPi / lam;
-        mu[s] = 2.0 * k * beta[s];
-        f[s] = weights[s] / wsum;
-        den += f[s] * mu[s] * mu[s];
         p->E[s] = energy_keV[s];
-        p->delta[s] = delta[s];
-        p->beta[s] = beta[s];
         p->w[s] = weights[s];
-        const double Ld = L_m * delta[s];
-        C.f[s] = (float)f[s];
-        C.mu[s] = (float)mu[s];
-        C.c[s] = (float)(-Ld / (pixel_m * pixel_m));
-        const double fx1 = 1.0 / (nx * pixel_m), fy1 = 1.0 / (ny * pixel_m);
-        C.ha[s] = mu[s] > 0.0 ? (float)(Ld * 4.0 * kPi * kPi * fx1 * fx1 / mu[s]) : 0.f;
-        C.hb[s] = mu[s] > 0.0 ? (float)(Ld * 4.0 * kPi * kPi * fy1 * fy1 / mu[s]) : 0.f;
-        const double eps = L_m / k;
-        C.qc[s] = (float)(eps * eps / (4.0 * pixel_m * pixel_m * pixel_m * pixel_m));
-        C.tneg[s] = mu[s] > 0.0 ? (float)(-0.6931471805599453 / mu[s]) : -3.0e38f;
     }
-    if (!(den > 0.0)) {
+    if (!line_constants(p, L_m, delta, beta)) {
         delete p;
         return EPR_ERR_INVALID_ARG;  // no line both weighted and absorbing
-    }
-    for (int s = 0; s < n_lines; ++s) C.wproj[s] = (float)(f[s] * mu[s] / den);
-    for (int s = 0; s < n_lines; ++s) {
-        p->ha_uniform[s] = C.ha[s];
-        p->hb_uniform[s] = C.hb[s];
     }
 
     epr_status st = init_kernels(p->device);
@@ -790,6 +837,8 @@ void epr_plan_destroy(epr_plan_t p)
     if (p->vjp_part) cudaFree(p->vjp_part);
     if (p->h_vjp_part) cudaFreeHost(p->h_vjp_part);
     if (p->xt_dev) cudaFree(p->xt_dev);
+    for (void* a : p->sv_allocs) cudaFree(a);
+    if (p->h_sv_acc) cudaFreeHost(p->h_sv_acc);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto& r : p->recs) {
         cudaEventDestroy(r.a);
@@ -972,6 +1021,277 @@ epr_status epr_vjp(epr_plan_t p, const float* T, const float* gbar, float* Tbar,
             }
             if (L_bar) L_bar[b] = lbar;
         }
+    }
+    return EPR_OK;
+}
+
+}  // extern "C"
+
+// --- reverse mode through the unrolled non-local solve ----------------------
+namespace {
+
+// Buffers of the reverse pass for `batch` projections, nck checkpoints and a
+// segment of nseg recomputed iterates (allocated once, grown on demand).
+epr_status sv_buffers(epr_plan_s* p, int batch, int nck, int nseg)
+{
+    if (batch <= p->sv_batch && nck <= p->sv_nck && nseg <= p->sv_nseg && p->sv_batch > 0)
+        return EPR_OK;
+    EPR_TRY(cudaDeviceSynchronize());
+    for (void* a : p->sv_allocs) cudaFree(a);
+    p->sv_allocs.clear();
+    p->sv_batch = p->sv_nck = p->sv_nseg = 0;
+    const EprConsts& C = p->C;
+    const size_t m = (size_t)batch * C.nx * C.ny, ml = m * C.ns;
+    const int nacc = 1 + 3 * C.ns;
+    auto get = [&](auto** out, size_t n) -> cudaError_t {
+        void* ptr = nullptr;
+        cudaError_t e = cudaMalloc(&ptr, n * sizeof(**out) > 0 ? n * sizeof(**out) : 16);
+        if (e != cudaSuccess) return e;
+        p->sv_allocs.push_back(ptr);
+        *out = reinterpret_cast<std::remove_reference_t<decltype(*out)>>(ptr);
+        return cudaSuccess;
+    };
+    cudaError_t e = get(&p->sv_r, m);
+    if (e == cudaSuccess) e = get(&p->sv_RS, ml);
+    if (e == cudaSuccess) e = get(&p->sv_GA, ml);
+    if (e == cudaSuccess) e = get(&p->sv_H, ml);
+    if (e == cudaSuccess) e = get(&p->sv_HB, ml);
+    if (e == cudaSuccess) e = get(&p->sv_RSB, ml);
+    if (e == cudaSuccess) e = get(&p->sv_GB, m);
+    if (e == cudaSuccess) e = get(&p->sv_TMP, m);
+    if (e == cudaSuccess) e = get(&p->sv_tb, m);
+    if (e == cudaSuccess) e = get(&p->sv_tn, m);
+    if (e == cudaSuccess) e = get(&p->sv_vx, m);
+    if (e == cudaSuccess) e = get(&p->sv_vy, m);
+    if (e == cudaSuccess) e = get(&p->sv_Db, m);
+    if (e == cudaSuccess) e = get(&p->sv_ck, m * nck);
+    if (e == cudaSuccess) e = get(&p->sv_seg, m * (nseg > 0 ? nseg : 1));
+    if (e == cudaSuccess) e = get(&p->sv_part, (size_t)batch * epr_sv_blocks() * (C.ns + 1));
+    if (e == cudaSuccess) e = get(&p->sv_acc, (size_t)batch * nacc);
+    if (e == cudaSuccess) {
+        if (p->h_sv_acc) cudaFreeHost(p->h_sv_acc);
+        p->h_sv_acc = nullptr;
+        e = cudaMallocHost((void**)&p->h_sv_acc, (size_t)batch * nacc * sizeof(double));
+    }
+    if (e != cudaSuccess) {
+        for (void* a : p->sv_allocs) cudaFree(a);
+        p->sv_allocs.clear();
+        return cuda_status(e);
+    }
+    p->sv_batch = batch;
+    p->sv_nck = nck;
+    p->sv_nseg = nseg;
+    return EPR_OK;
+}
+
+// one iteration of the non-local solve in place on T (batch projections)
+epr_status sv_step(epr_plan_s* p, const float* D, float* T, int batch, double omega, double eps,
+                   cudaStream_t s)
+{
+    epr_solve_opts o1 = {1, omega, 0.0, eps, 1};
+    return launch_solve(p, D, T, batch, &o1, EPR_MODEL_NONLOCAL, s);
+}
+
+// the preconditioner of line s in place on a batch of maps, or with symbol
+// kind 1 / 2 (dH/dmu, dH/d(L delta)) of the generic column pass
+epr_status sv_filter(epr_plan_s* p, float* g, int s, int kind, float kscale, int batch,
+                     cudaStream_t st)
+{
+    const EprConsts& C = p->C;
+    EPR_TRY(epr_launch_row_fwd(C, p->W, 2, nullptr, nullptr, g, s, 1, 0, 0.f, batch, 0, st));
+    if (kind == 0) EPR_TRY(epr_launch_col(C, p->W, s, 1, batch, 0, 0, -1, st));
+    else EPR_TRY(epr_launch_col_kind(C, p->W, s, batch, kind, kscale, st));
+    EPR_TRY(epr_launch_row_inv(C, p->W, 1, g, s, 1, 0, 1.f, 0.f, 0.f, batch, 0, st));
+    return EPR_OK;
+}
+
+// The reverse of one iteration at thickness T: tb (dF/dT') -> tn (dF/dT),
+// Db += dF/dD, scalar accumulators += their shares.
+epr_status sv_reverse_iteration(epr_plan_s* p, const float* D, const float* T, int B, double omega,
+                                double eps, cudaStream_t st)
+{
+    const EprConsts& C = p->C;
+    const int ns = C.ns, nacc = 1 + 3 * ns;
+    const size_t npix = (size_t)C.nx * C.ny, m = (size_t)B * npix;
+    // forward of this iteration, recomputed: P, P_s (float), r, r_s, g_s, h_s
+    EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)B * sizeof(EprProjState), st));
+    epr_status es = launch_forward(p, T, nullptr, 0, B, EPR_MODEL_NONLOCAL, 0, st);
+    if (es != EPR_OK) return es;
+    if (C.det) {
+        EPR_TRY(epr_launch_fx_to_float(p->W.Pq, p->W.P, m, st));
+        if (ns > 1) EPR_TRY(epr_launch_fx_to_float(p->W.Psq, p->W.Ps, m * ns, st));
+    }
+    EPR_TRY(epr_launch_sv_split(C, D, p->W.P, p->W.Ps, p->sv_r, p->sv_RS, B, st));
+    for (int s = 0; s < ns; ++s) {
+        EPR_TRY(epr_launch_gather(C, T, p->sv_RS + s * m, p->sv_GA + s * m, s, B, st));
+        EPR_TRY(cudaMemcpyAsync(p->sv_H + s * m, p->sv_GA + s * m, m * sizeof(float),
+                                cudaMemcpyDeviceToDevice, st));
+        es = sv_filter(p, p->sv_H + s * m, s, 0, 0.f, B, st);
+        if (es != EPR_OK) return es;
+    }
+    // reverse
+    EPR_TRY(cudaMemsetAsync(p->sv_tn, 0, m * sizeof(float), st));
+    EPR_TRY(cudaMemsetAsync(p->sv_vx, 0, m * sizeof(float), st));
+    EPR_TRY(cudaMemsetAsync(p->sv_vy, 0, m * sizeof(float), st));
+    EPR_TRY(cudaMemsetAsync(p->sv_RSB, 0, m * ns * sizeof(float), st));
+    double den = 0.0;
+    for (int s = 0; s < ns; ++s) den += (double)C.f[s] * C.mu[s] * C.mu[s];
+    EPR_TRY(epr_launch_sv_update_adj(C, T, p->sv_H, p->sv_tb, p->sv_HB, p->sv_part, B,
+                                     (float)omega, (float)eps, (float)(1.0 / den), st));
+    EPR_TRY(epr_launch_sv_accum(p->sv_part, npix, ns + 1, 0, p->sv_acc, nacc, 0, 1.0, B, st));
+    for (int s = 0; s < ns; ++s)
+        EPR_TRY(epr_launch_sv_accum(p->sv_part, npix, ns + 1, 1 + s, p->sv_acc, nacc, 1 + s, 1.0, B, st));
+    for (int s = 0; s < ns; ++s) {
+        float* HBs = p->sv_HB + s * m;
+        // gbar_s = H_s hbar_s
+        EPR_TRY(cudaMemcpyAsync(p->sv_GB, HBs, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        es = sv_filter(p, p->sv_GB, s, 0, 0.f, B, st);
+        if (es != EPR_OK) return es;
+        // the symbol's dependence on mu_s and L delta_s: <hbar_s, dH g_s>
+        const double Ld = p->L * p->delta[s];
+        for (int kind = 1; kind <= 2; ++kind) {
+            EPR_TRY(cudaMemcpyAsync(p->sv_TMP, p->sv_GA + s * m, m * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+            const float ks = kind == 1 ? (float)(1.0 / C.mu[s]) : (float)(-1.0 / Ld);
+            es = sv_filter(p, p->sv_TMP, s, kind, ks, B, st);
+            if (es != EPR_OK) return es;
+            EPR_TRY(epr_launch_sv_dot(HBs, p->sv_TMP, npix, p->sv_part, B, st));
+            EPR_TRY(epr_launch_sv_accum(p->sv_part, npix, 1, 0, p->sv_acc, nacc,
+                                        kind == 1 ? 1 + s : 1 + ns + s, 1.0, B, st));
+        }
+        // the gather backwards: input adjoint (a splat) and shift term
+        EPR_TRY(epr_launch_sv_splat_field(C, T, p->sv_GB, p->sv_RSB + s * m, s, B, st));
+        EPR_TRY(epr_launch_sv_interp_du(C, 0, T, p->sv_RS + s * m, p->sv_GB, nullptr, p->sv_vx,
+                                        p->sv_vy, p->sv_tn, p->sv_part, s, (float)omega, B, st));
+        EPR_TRY(epr_launch_sv_accum(p->sv_part, npix, 2, 0, p->sv_acc, nacc, 1 + 2 * ns + s, 1.0, B, st));
+    }
+    // the split, then the splat backwards (input and shift) with I_s's share
+    EPR_TRY(epr_launch_sv_split_adj(C, p->sv_RSB, p->W.P, p->W.Ps, p->sv_r, p->sv_Db, B, st));
+    for (int s = 0; s < ns; ++s) {
+        EPR_TRY(epr_launch_sv_interp_du(C, 1, T, p->sv_RSB + s * m, nullptr, p->sv_HB + s * m,
+                                        p->sv_vx, p->sv_vy, p->sv_tn, p->sv_part, s, (float)omega,
+                                        B, st));
+        EPR_TRY(epr_launch_sv_accum(p->sv_part, npix, 2, 0, p->sv_acc, nacc, 1 + 2 * ns + s, 1.0, B, st));
+        EPR_TRY(epr_launch_sv_accum(p->sv_part, npix, 2, 1, p->sv_acc, nacc, 1 + s, 1.0, B, st));
+    }
+    EPR_TRY(epr_launch_sv_gT(C, p->sv_vx, p->sv_vy, p->sv_tn, B, st));
+    std::swap(p->sv_tb, p->sv_tn);
+    return EPR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+epr_status epr_solve_vjp(epr_plan_t p, const float* D, const float* T0, int batch, int n_iter,
+                         double omega, double eps_I, int checkpoint_every, const float* Tbar,
+                         float* T_out, float* T0_bar, float* D_bar, double* delta_bar,
+                         double* beta_bar, double* L_bar, void* stream)
+{
+    if (!p || !D || !Tbar || batch <= 0 || n_iter < 0 || !(omega > 0.0) || checkpoint_every < 0)
+        return EPR_ERR_INVALID_ARG;
+    const EprConsts& C = p->C;
+    if (C.os > 1 || C.xt) return EPR_ERR_INVALID_ARG;
+    for (int s = 0; s < C.ns; ++s)
+        if (!(C.mu[s] > 0.f) || !(p->L * p->delta[s] > 0.0)) return EPR_ERR_INVALID_ARG;
+    const float* dev_in[3] = {D, T0, Tbar};
+    float* dev_out[3] = {T_out, T0_bar, D_bar};
+    for (const float* a : dev_in)
+        if (a && (!is_device_ptr(a) || !aligned16(a))) return EPR_ERR_INVALID_ARG;
+    for (float* a : dev_out)
+        if (a && (!is_device_ptr(a) || !aligned16(a))) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const double eps = eps_I > 0 ? eps_I : 1e-8;
+    const int mck = checkpoint_every > 0 ? checkpoint_every : 1;   // iterations per checkpoint
+    const int nck = n_iter / mck + 1;
+    epr_status es = ensure_workspace(p, batch, 1);
+    if (es != EPR_OK) return es;
+    es = sv_buffers(p, batch, nck, mck > 1 ? mck : 0);
+    if (es != EPR_OK) return es;
+    const size_t m = (size_t)batch * C.nx * C.ny;
+    const int nacc = 1 + 3 * C.ns;
+    // forward: the iterates tau_0, tau_mck, tau_2 mck, ... kept; tau_N in sv_tn
+    float* Tc = p->sv_tn;
+    if (T0) EPR_TRY(cudaMemcpyAsync(Tc, T0, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else EPR_TRY(cudaMemsetAsync(Tc, 0, m * sizeof(float), st));
+    for (int it = 0; it < n_iter; ++it) {
+        if (it % mck == 0)
+            EPR_TRY(cudaMemcpyAsync(p->sv_ck + (size_t)(it / mck) * m, Tc, m * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+        es = sv_step(p, D, Tc, batch, omega, eps, st);
+        if (es != EPR_OK) return es;
+    }
+    if (T_out) EPR_TRY(cudaMemcpyAsync(T_out, Tc, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    // reverse, segment by segment from the last
+    EPR_TRY(cudaMemcpyAsync(p->sv_tb, Tbar, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    EPR_TRY(cudaMemsetAsync(p->sv_Db, 0, m * sizeof(float), st));
+    EPR_TRY(cudaMemsetAsync(p->sv_acc, 0, (size_t)batch * nacc * sizeof(double), st));
+    for (int seg = (n_iter - 1) / mck; n_iter > 0 && seg >= 0; --seg) {
+        const int base = seg * mck, len = (n_iter - base) < mck ? (n_iter - base) : mck;
+        const float* ck = p->sv_ck + (size_t)seg * m;
+        if (mck > 1) {   // recompute the segment's iterates from its checkpoint
+            EPR_TRY(cudaMemcpyAsync(p->sv_seg, ck, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            for (int i = 1; i < len; ++i) {
+                float* Ti = p->sv_seg + (size_t)i * m;
+                EPR_TRY(cudaMemcpyAsync(Ti, Ti - m, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                es = sv_step(p, D, Ti, batch, omega, eps, st);
+                if (es != EPR_OK) return es;
+            }
+        }
+        for (int i = len - 1; i >= 0; --i) {
+            const float* Ti = mck > 1 ? p->sv_seg + (size_t)i * m : ck;
+            es = sv_reverse_iteration(p, D, Ti, batch, omega, eps, st);
+            if (es != EPR_OK) return es;
+        }
+    }
+    if (T0_bar) EPR_TRY(cudaMemcpyAsync(T0_bar, p->sv_tb, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (D_bar) EPR_TRY(cudaMemcpyAsync(D_bar, p->sv_Db, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    const bool scalars = delta_bar || beta_bar || L_bar;
+    if (scalars) {
+        EPR_TRY(cudaMemcpyAsync(p->h_sv_acc, p->sv_acc, (size_t)batch * nacc * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+        EPR_TRY(cudaStreamSynchronize(st));
+        // back from c_s = -L delta_s / p^2, the filter's L delta_s and mu_s = 2 k_s beta_s
+        const double p2 = p->pixel * p->pixel;
+        double wsum = 0.0;
+        for (int s = 0; s < C.ns; ++s) wsum += p->w[s];
+        for (int b = 0; b < batch; ++b) {
+            const double* a = p->h_sv_acc + (size_t)b * nacc;
+            double lbar = 0.0;
+            for (int s = 0; s < C.ns; ++s) {
+                const double lam = kHcEvM / (p->E[s] * 1e3);
+                const double k = 2.0 * kPi / lam;
+                const double mu = 2.0 * k * p->beta[s], f = p->w[s] / wsum;
+                const double mub = a[1 + s] + a[0] * 2.0 * f * mu;
+                const double Ldb = a[1 + C.ns + s], cb = a[1 + 2 * C.ns + s];
+                if (delta_bar) delta_bar[(size_t)b * C.ns + s] = -p->L / p2 * cb + p->L * Ldb;
+                if (beta_bar) beta_bar[(size_t)b * C.ns + s] = 2.0 * k * mub;
+                lbar += -p->delta[s] / p2 * cb + p->delta[s] * Ldb;
+            }
+            if (L_bar) L_bar[b] = lbar;
+        }
+    }
+    return EPR_OK;
+}
+
+epr_status epr_plan_set_params(epr_plan_t p, double L_m, const double* delta, const double* beta)
+{
+    if (!p || !delta || !beta || !(L_m >= 0.0) || !isfinite(L_m) || p->C.xt)
+        return EPR_ERR_INVALID_ARG;
+    for (int s = 0; s < p->C.ns; ++s)
+        if (!(beta[s] >= 0.0) || !isfinite(beta[s]) || !isfinite(delta[s])) return EPR_ERR_INVALID_ARG;
+    EPR_TRY(cudaSetDevice(p->device));
+    // graphs and work in flight hold the old constants by value; nothing is
+    // reallocated, so letting queued work finish first is enough
+    if (!line_constants(p, L_m, delta, beta)) return EPR_ERR_INVALID_ARG;
+    if (p->has_graph) {
+        cudaGraphExecDestroy(p->gexec);
+        p->has_graph = false;
+    }
+    if (p->prof_exec) {
+        cudaGraphExecDestroy(p->prof_exec);
+        p->prof_exec = nullptr;
     }
     return EPR_OK;
 }

@@ -41,7 +41,7 @@ SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
            "epr_check_device_status", "epr_status_string", "epr_launch_count",
            "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc", "epr_vjp",
            "epr_batch_create", "epr_batch_destroy", "epr_solve_nonlocal_batched",
-           "epr_plan_set_xspec")
+           "epr_plan_set_xspec", "epr_solve_vjp", "epr_plan_set_params")
 
 KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 
@@ -139,6 +139,10 @@ def load(path: str | None = None):
                                                    ctypes.POINTER(epr_solve_opts),
                                                    ctypes.POINTER(epr_solve_info), vp]
         lib.epr_solve_nonlocal_batched.restype = i
+        lib.epr_solve_vjp.argtypes = [vp, vp, vp, i, i, d, d, i, vp, vp, vp, vp, dp, dp, dp, vp]
+        lib.epr_solve_vjp.restype = i
+        lib.epr_plan_set_params.argtypes = [vp, d, dp, dp]
+        lib.epr_plan_set_params.restype = i
         lib.epr_plan_set_xspec.argtypes = [vp, ctypes.POINTER(epr_xspec)]
         lib.epr_plan_set_xspec.restype = i
         lib.epr_launch_count.argtypes = []
@@ -219,6 +223,13 @@ def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
     return h.value
 
 
+def epr_plan_set_params(plan, L_m, delta, beta):
+    """New L, delta_s, beta_s for an existing plan (no reallocation)."""
+    dl, dp_ = _darr(delta)
+    bt, bp = _darr(beta)
+    _check(load().epr_plan_set_params(plan, float(L_m), dp_, bp), "epr_plan_set_params")
+
+
 def epr_plan_set_xspec(plan, x_knots=None, weights=None, delta=None, beta=None):
     """x-dependent spectrum: knot columns [K] and per-line tables [n_lines][K]
     of weights, delta, beta (see the C header).  x_knots None returns the plan
@@ -275,6 +286,27 @@ def epr_vjp(plan, T, gbar, Tbar, n_lines, batch=1, scalars=True, stream=None):
         ptrs = [None, None, None]
     _check(load().epr_vjp(plan, _ptr(T), _ptr(gbar), _ptr(Tbar), *ptrs, int(batch),
                           _stream(stream)), "epr_vjp")
+    return (db, bb, lb) if scalars else None
+
+
+def epr_solve_vjp(plan, D, Tbar, n_lines, n_iter, omega=1.0, T0=None, eps_I=1e-8,
+                  checkpoint_every=0, batch=1, T_out=None, T0_bar=None, D_bar=None,
+                  scalars=True, stream=None):
+    """Reverse mode through n_iter iterations of the non-local solve (device
+    tensors): fills T_out, T0_bar, D_bar when given and returns (delta_bar
+    [batch][n_lines], beta_bar [batch][n_lines], L_bar [batch]) when
+    `scalars`, else None."""
+    if scalars:
+        db = np.zeros((batch, n_lines))
+        bb = np.zeros((batch, n_lines))
+        lb = np.zeros(batch)
+        ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in (db, bb, lb)]
+    else:
+        ptrs = [None, None, None]
+    _check(load().epr_solve_vjp(plan, _ptr(D), _ptr(T0), int(batch), int(n_iter), float(omega),
+                                float(eps_I), int(checkpoint_every), _ptr(Tbar), _ptr(T_out),
+                                _ptr(T0_bar), _ptr(D_bar), *ptrs, _stream(stream)),
+           "epr_solve_vjp")
     return (db, bb, lb) if scalars else None
 
 
