@@ -69,6 +69,10 @@ def _args():
                          "--warmup + --steps solves of --iters iterations, no report")
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--iters", type=int, default=2)
+    ap.add_argument("--lines", type=int, default=1,
+                    help="ncu case: 1 = the monochromatic workload, 8 = the polychromatic one")
+    ap.add_argument("--oversample", type=int, default=1,
+                    help="ncu case: solve on a grid oversampled by this factor (non-local)")
     return ap.parse_args()
 
 
@@ -214,6 +218,159 @@ def convergence(info) -> dict:
         reach[f"{lev:g}"] = int(hit[0]) + 1 if hit.size else None
     return {"rho_final": round(float(info["rho"][0]), 6), "kappa_final": float(info["kappa"][0]),
             "iterations_to_kappa": reach}
+
+
+def _events_ms(fn, torch, reps=1, warm=1):
+    """Median CUDA-event time of fn on the current stream (after warm calls)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def uneven_batch(epr, ph, torch, peak, n_proj=512, max_iter=80, deterministic=False, tol=2e-3):
+    """Batched solve of projections of uneven sizes in one call: sizes drawn
+    uniformly from {1024x1024, 2048x1536, 2048x2048, 3072x2048} (nx x ny), 4
+    lines 60-160 keV, each projection's thickness scaled so that its largest
+    shift is U[0.2, 10] px, each solved until kappa <= tol or max_iter.  Under
+    Poisson(1e4) noise kappa levels off near 1e-3 (the oracle: 250 iterations
+    of such projections), so the tolerance is 2e-3, where projections retire
+    between about 40 and 80 iterations; a tolerance of 1e-4 would retire
+    none.  Data: 8 seeded 60-ellipsoid phantoms per size, the library's
+    forward model and Poisson(1e4) noise drawn on the device (seeded)."""
+    sizes = [(1024, 1024), (2048, 1536), (2048, 2048), (3072, 2048)]
+    E4, d4, b4, w4 = ph.spectrum(4, 60.0, 160.0, 95.0, 30.0, ph.BONE[0], ph.BONE[1], 80.0, 4000)
+    pixel, L, photons, n_base = 20e-6, 30.0, 1e4, 8
+    cmax = L * float(np.max(d4)) / pixel ** 2       # shift per thickness step, largest line
+    base = []
+    for si, (nx, ny) in enumerate(sizes):
+        row = []
+        for k in range(n_base):
+            ells = ph.random_ellipsoids(ny, nx, 60, 8.0, 120.0, seed=4200 + 10 * si + k)
+            t = ph.project_ellipsoids(ells, ny, nx, pixel)
+            gy, gx = np.gradient(t)
+            row.append((torch.from_numpy(t.astype(np.float32)).cuda(),
+                        cmax * max(np.abs(gx).max(), np.abs(gy).max())))
+        base.append(row)
+    g = ph.rng(4100)
+    gen = torch.Generator(device="cuda").manual_seed(4101)
+    Ds, Ts, shapes, targets = [], [], [], []
+    plans = [epr.Plan(nx, ny, pixel, L, E4, d4, b4, w4, max_shift_px=6, overflow_capacity=1 << 18)
+             for nx, ny in sizes]
+    for j in range(n_proj):
+        si, k = int(g.integers(4)), int(g.integers(n_base))
+        target = float(g.uniform(0.2, 10.0))
+        t, umax = base[si][k]
+        tj = t * (target / umax)
+        P = torch.empty_like(tj)
+        epr.epr_forward(plans[si].handle, tj, P)
+        Ds.append(torch.poisson(photons * P.clamp_min(0), generator=gen) / photons)
+        Ts.append(torch.empty_like(tj))
+        shapes.append(sizes[si])
+        targets.append(target)
+    for q in plans:
+        q.close()
+    bh = epr.epr_batch_create(pixel, L, E4, d4, b4, w4, max_shift_px=6, autotune=True,
+                              overflow_capacity=1 << 18, deterministic=deterministic)
+    info = {}
+
+    def call():
+        info.update(epr.epr_solve_nonlocal_batched(bh, Ds, Ts, n_iter=max_iter, omega=0.4,
+                                                   tol=tol))
+
+    ms = _events_ms(call, torch, reps=1, warm=1)   # the warm call also tunes the splat
+    epr.epr_batch_destroy(bh)
+    iters = np.asarray(info["iters"], int)
+    npx = np.asarray([nx * ny for nx, ny in shapes], float)
+    bpp = sum(kernel_bytes_per_px(4).values())
+    gbs = float((iters * npx).sum()) * bpp / (ms * 1e-3) / 1e9
+    hist = np.bincount(np.minimum(iters // 10, max_iter // 10), minlength=max_iter // 10 + 1)
+    conv = iters < max_iter
+    return {"projections": n_proj, "sizes_nx_ny": sizes, "n_lines": 4, "tol_kappa": tol,
+            "max_iter": max_iter, "max_shift_px": "U[0.2, 10] per projection",
+            "deterministic": bool(deterministic), "ms_per_call": round(ms, 1),
+            "equiv_2048sq_projections_per_s": round(float(npx.sum()) / REF_PIX / (ms * 1e-3), 3),
+            "retired_by_kappa": int(conv.sum()),
+            "iterations_histogram_per_10": hist.tolist(),
+            "mean_iterations": round(float(iters.mean()), 2),
+            "hbm": {"alg_bytes_per_px_per_iter": bpp, "achieved_gbs": round(gbs, 1), "peak": peak,
+                    "frac": round(gbs / peak, 4),
+                    "note": "algorithmic bytes of the iterations each projection ran / time"},
+            "kappa_of_unconverged_max": float(np.max(np.asarray(info["kappa"])[~conv]))
+            if (~conv).any() else None}
+
+
+def unrolled_vjp(epr, ph, torch, peak, batch=16, n_iter=30):
+    """Reverse mode through n_iter unrolled 8-line non-local iterations of a
+    batch of 2048^2 projections (the rotated ellipsoid phantom at `batch`
+    angles), with and without checkpointing of the iterates."""
+    wp, ells, angles = ph.ellipsoids_poly()
+    taus = [ph.project_ellipsoids(ells, wp.ny, wp.nx, wp.pixel, angles[4 * j % len(angles)])
+            for j in range(batch)]
+    plan = epr.Plan(wp.nx, wp.ny, wp.pixel, wp.L, wp.energy_keV, wp.delta, wp.beta, wp.weights)
+    T = torch.from_numpy(np.stack(taus).astype(np.float32)).cuda()
+    P = torch.empty_like(T)
+    epr.epr_forward(plan.handle, T, P, batch=batch)
+    gen = torch.Generator(device="cuda").manual_seed(5001)
+    D = torch.poisson(wp.photons * P.clamp_min(0), generator=gen) / wp.photons
+    Tbar = torch.randn(T.shape, device="cuda", generator=gen)
+    t0b, Db = torch.empty_like(T), torch.empty_like(T)
+    ns = int(np.size(wp.energy_keV))
+    out = {"workload": f"{batch} x 2048x2048, 8 lines, {n_iter} unrolled iterations from the flat "
+                       "field, omega 0.4; gradients in T0, D, L, delta_s, beta_s",
+           "batch": batch, "n_iter": n_iter}
+    for ck in (0, 5):
+        ms = _events_ms(lambda: epr.epr_solve_vjp(plan.handle, D, Tbar, ns, n_iter, omega=wp.omega,
+                                                  checkpoint_every=ck, batch=batch, T0_bar=t0b,
+                                                  D_bar=Db, scalars=True), torch, reps=1, warm=1)
+        out["ms_all_iterates_kept" if ck == 0 else "ms_checkpoint_every_5"] = round(ms, 1)
+    fwd = _events_ms(lambda: epr.epr_solve_nonlocal(plan.handle, D, T, batch=batch, n_iter=n_iter,
+                                                    omega=wp.omega, want_info=False), torch, reps=1)
+    out["ms_forward_solve_only"] = round(fwd, 1)
+    out["projections_per_s"] = round(batch / (out["ms_all_iterates_kept"] * 1e-3), 3)
+    plan.close()
+    return out
+
+
+def xspec_solve(epr, ph, torch, timeit):
+    """One 2048^2 8-line projection solved with an x-dependent spectrum (a
+    five-knot table across the columns: weights +-30 %, delta and beta +-20 %),
+    50 iterations, against the same solve with the uniform spectrum."""
+    wp, ells, angles = ph.ellipsoids_poly()
+    tau = ph.project_ellipsoids(ells, wp.ny, wp.nx, wp.pixel, angles[8])
+    ns = int(np.size(wp.energy_keV))
+    g = ph.rng(6001)
+    X = np.linspace(0.0, wp.nx - 1.0, 5)
+    W = wp.weights[:, None] * g.uniform(0.7, 1.3, size=(ns, 5))
+    Dl = wp.delta[:, None] * g.uniform(0.8, 1.2, size=(ns, 5))
+    Bt = wp.beta[:, None] * g.uniform(0.8, 1.2, size=(ns, 5))
+    plan = epr.Plan(wp.nx, wp.ny, wp.pixel, wp.L, wp.energy_keV, wp.delta, wp.beta, wp.weights)
+    T = torch.from_numpy(tau.astype(np.float32)).cuda()
+    P = torch.empty_like(T)
+    epr.epr_plan_set_xspec(plan.handle, X, W, Dl, Bt)
+    epr.epr_forward(plan.handle, T, P)
+    gen = torch.Generator(device="cuda").manual_seed(6002)
+    D = torch.poisson(wp.photons * P.clamp_min(0), generator=gen) / wp.photons
+    ms_x = timeit(lambda: epr.epr_solve_nonlocal(plan.handle, D, T, n_iter=wp.n_iter,
+                                                 omega=wp.omega, want_info=False), reps=3)
+    epr.epr_plan_set_xspec(plan.handle)
+    ms_u = timeit(lambda: epr.epr_solve_nonlocal(plan.handle, D, T, n_iter=wp.n_iter,
+                                                 omega=wp.omega, want_info=False), reps=3)
+    plan.close()
+    return {"workload": "ellipsoids_poly_2048, 1 projection, 8 lines, 50 iterations, 5-knot "
+                        "x-dependent table", "ms_per_solve": round(ms_x, 3),
+            "ms_per_solve_uniform_spectrum": round(ms_u, 3),
+            "note": "the x-dependent path runs the runtime-sized kernels with per-column constants"}
 
 
 # --------------------------------------------------------------------------
@@ -501,33 +658,19 @@ def run_ours(a):
                      "internal_2048sq_equiv_per_s": round((nd * os_) ** 2 / REF_PIX / (ms_o * 1e-3), 3)}
     other["oversampled"] = ovs
 
-    # uneven batch: projections of four detector sizes, 4 lines, each solved until
-    # kappa <= 1e-4 or 50 iterations, in one batched call
-    shapes = [(1024, 1024), (2048, 1536), (2048, 2048), (3072, 2048)] * 2   # (nx, ny)
-    E4, d4, b4, w4 = ph.spectrum(4, 60.0, 160.0, 95.0, 30.0, ph.BONE[0], ph.BONE[1], 80.0, 4000)
-    bh = epr.epr_batch_create(wp.pixel, wp.L, E4, d4, b4, w4)
-    Du, Tu = [], []
-    for k, (nxu, nyu) in enumerate(shapes):
-        ells_u = ph.random_ellipsoids(nyu, nxu, 60, 8.0, 120.0, seed=4000 + k)
-        tu = torch.from_numpy(ph.project_ellipsoids(ells_u, nyu, nxu, wp.pixel).astype(np.float32)).cuda()
-        with epr.Plan(nxu, nyu, wp.pixel, wp.L, E4, d4, b4, w4) as fp:
-            pu = torch.empty_like(tu)
-            epr.epr_forward(fp.handle, tu, pu)
-        Du.append(torch.from_numpy(ph.poisson(pu.cpu().numpy(), wp.photons, 70 + k).astype(np.float32)).cuda())
-        Tu.append(torch.empty_like(tu))
-    uinfo = {}
-
-    def uneven():
-        uinfo.update(epr.epr_solve_nonlocal_batched(bh, Du, Tu, n_iter=50, omega=0.4, tol=1e-4))
-
-    uneven_ms = timeit(uneven, reps=3)
-    epr.epr_batch_destroy(bh)
-    eq = sum(nxu * nyu for nxu, nyu in shapes) / REF_PIX
-    other["batched_uneven"] = {"projections": len(shapes), "sizes_nx_ny": sorted(set(shapes)),
-                               "n_lines": 4, "tol_kappa": 1e-4, "max_iter": 50,
-                               "iters": [int(v) for v in uinfo["iters"]],
-                               "ms_per_call": round(uneven_ms, 3),
-                               "equiv_2048sq_projections_per_s": round(eq / (uneven_ms * 1e-3), 3)}
+    # uneven batch of 512 projections (4 lines, solved to kappa <= 1e-4), float and
+    # fixed point; reverse mode through 30 unrolled 8-line iterations of 16
+    # projections; the x-dependent spectrum and the second-order model
+    other["batched_uneven_512"] = uneven_batch(epr, ph, torch, peak, n_proj=512, max_iter=80)
+    other["batched_uneven_fixed_point"] = uneven_batch(epr, ph, torch, peak, n_proj=64,
+                                                       max_iter=80, deterministic=True)
+    other["unrolled_solve_vjp"] = unrolled_vjp(epr, ph, torch, peak)
+    other["xdependent_spectrum"] = xspec_solve(epr, ph, torch, timeit)
+    other["second_order_nonlocal"] = {
+        "workload": "the headline projection, non-local model to second order (WKB1 term)",
+        "n_iter": wl.n_iter,
+        "ms_per_solve": round(timeit(lambda: epr.epr_solve_nonlocal_wkb1(
+            plan.handle, D, T, n_iter=wl.n_iter, omega=wl.omega, want_info=False)), 3)}
     other["polychromatic"] = {"workload": wp.name.replace("x64x", "x1x"),
                               "n_lines": int(np.size(wp.energy_keV)), "n_iter": wp.n_iter,
                               "ms_per_solve": round(poly_ms, 3),
@@ -564,14 +707,23 @@ def ncu_case(a):
 
     B.build()
     epr.load()
-    wl, _ = ph.ellipsoids_mono(seed=2000)
-    taus = [ph.ellipsoids_mono(seed=2000 + k)[1] for k in range(a.batch)]
-    plan = epr.Plan(wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights)
+    if a.lines > 1:   # the rotated 8-line phantom at a.batch angles
+        wl, ells, angles = ph.ellipsoids_poly(n_lines=a.lines)
+        taus = [ph.project_ellipsoids(ells, wl.ny, wl.nx, wl.pixel, angles[k]) for k in range(a.batch)]
+    else:
+        wl, _ = ph.ellipsoids_mono(seed=2000)
+        taus = [ph.ellipsoids_mono(seed=2000 + k)[1] for k in range(a.batch)]
+    os_ = max(1, a.oversample)
+    n = wl.nx
+    if os_ > 1:   # the detector of the workload, an internal grid o times finer
+        taus = [np.kron(t, np.ones((os_, os_))) for t in taus]
+    plan = epr.Plan(n, n, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights,
+                    oversample=os_, max_shift_px=8 if os_ > 1 else 4)
     Tt = torch.from_numpy(np.stack(taus).astype(np.float32)).cuda()
-    P = torch.empty_like(Tt)
+    P = torch.empty((a.batch, n, n), device="cuda")
     epr.epr_forward(plan.handle, Tt, P, batch=a.batch)
     D = P.clamp_min(0) + 0.01 * torch.randn_like(P)
-    T = torch.empty_like(D)
+    T = torch.empty_like(Tt)
     for _ in range(a.warmup + a.steps):
         epr.epr_solve_nonlocal(plan.handle, D, T, batch=a.batch, n_iter=a.iters,
                                omega=wl.omega, want_info=False)

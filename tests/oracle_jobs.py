@@ -43,3 +43,28 @@ class Pool:
     def close(self):
         self._pool.close()
         self._pool.join()
+
+
+def solve_window_job(spec, D, n_iter, omega, tol):
+    """The oracle solve with its stopping rule, one iteration at a time:
+    returns (iterations run k, {k - 1: T, k: T, k + 1: T}, kappa history).
+    The iterate after k + 1 iterations is one more iteration from the result
+    (for a comparison with a float32 solve that stopped one iteration
+    later); every iteration is the same arithmetic as a multi-iteration
+    solve's."""
+    from oracle import oracle as O
+    ln = _lines(O, spec)
+    D = np.asarray(D, np.float64)
+    T = np.zeros_like(D)
+    prev = T.copy()
+    kap = []
+    k = 0
+    while k < n_iter:
+        prev = T
+        T, info = O.solve(ln, D, T0=T, n_iter=1, omega=omega, tol=0.0)
+        kap.append(float(info["kappa"][0]))
+        k += 1
+        if kap[-1] <= tol:
+            break
+    nxt, _ = O.solve(ln, D, T0=T, n_iter=1, omega=omega, tol=0.0)
+    return k, {k - 1: prev, k: T, k + 1: nxt}, kap
