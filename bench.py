@@ -208,6 +208,15 @@ def kernel_bytes_per_px(ns: int) -> dict:
             "row_inv": 8 + 4 * ns}
 
 
+def model_bytes_per_px(ns: int) -> int:
+    """The per-iteration streaming model of the hot path, one pass per step:
+    splat (read T, write P [and P_s]), gather (read T, D, P [, P_s], write g_s),
+    R2C rows, columns, C2R rows with the update: 52 B/px for one line,
+    28 + 32 n_s for n_s lines.  The fused kernels move fewer bytes (44 for one
+    line; kernel_bytes_per_px); fractions on both are reported."""
+    return 52 if ns == 1 else 28 + 32 * ns
+
+
 def convergence(info) -> dict:
     """Residual and relative update of the headline solve, and the first
     iteration at which the relative update kappa falls to each level."""
@@ -292,7 +301,7 @@ def uneven_batch(epr, ph, torch, peak, n_proj=512, max_iter=80, deterministic=Fa
     epr.epr_batch_destroy(bh)
     iters = np.asarray(info["iters"], int)
     npx = np.asarray([nx * ny for nx, ny in shapes], float)
-    bpp = sum(kernel_bytes_per_px(4).values())
+    bpp = model_bytes_per_px(4)
     gbs = float((iters * npx).sum()) * bpp / (ms * 1e-3) / 1e9
     hist = np.bincount(np.minimum(iters // 10, max_iter // 10), minlength=max_iter // 10 + 1)
     conv = iters < max_iter
@@ -496,6 +505,7 @@ def run_ours(a):
     iter_us = sum(v["avg_us"] for v in per_kernel.values())
     tr = _traffic(dom)
     live_us = ms * 1e3 / wl.n_iter   # one iteration of the timed (graph-replayed) solve
+    model_bytes = model_bytes_per_px(1) * npix
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["gbs"], "peak": peak,
                 "unit": "GB/s", "frac": round(dk["gbs"] / peak, 4),
                 "traffic": tr, "peak_source": f"{peak_src} hbm_gbs",
@@ -506,10 +516,13 @@ def run_ours(a):
                 "iteration_serialised": {"alg_bytes": iter_bytes, "kernel_us": round(iter_us, 2),
                                          "gbs": round(iter_bytes / (iter_us * 1e-6) / 1e9, 1),
                                          "frac": round(iter_bytes / (iter_us * 1e-6) / 1e9 / peak, 4)},
-                "iteration_live": {"alg_bytes": iter_bytes, "us": round(live_us, 2),
-                                   "gbs": round(iter_bytes / (live_us * 1e-6) / 1e9, 1),
-                                   "frac": round(iter_bytes / (live_us * 1e-6) / 1e9 / peak, 4),
-                                   "note": "ms_per_step / n_iter of the timed solves"},
+                "iteration_live": {"alg_bytes": model_bytes, "us": round(live_us, 2),
+                                   "gbs": round(model_bytes / (live_us * 1e-6) / 1e9, 1),
+                                   "frac": round(model_bytes / (live_us * 1e-6) / 1e9 / peak, 4),
+                                   "frac_fused_kernel_bytes":
+                                       round(iter_bytes / (live_us * 1e-6) / 1e9 / peak, 4),
+                                   "note": "ms_per_step / n_iter of the timed solves; bytes of "
+                                           "the 52 B/px model (fused kernels: 44 B/px)"},
                 "kernels": per_kernel}
     # the bound the kernels actually meet: instruction issue (4 warp instructions
     # per clock per SM), with the instructions ncu counted per launch
@@ -596,13 +609,16 @@ def run_ours(a):
     t_b = timeit(batched)
     t_p = timeit(plain_run)
     plain.close()
-    it_bytes = sum(kernel_bytes_per_px(1).values()) * npix   # algorithmic bytes per iteration
+    it_bytes = model_bytes_per_px(1) * npix   # algorithmic bytes per iteration (model)
     b_gbs = it_bytes * wl.n_iter * nb / (t_b * 1e-3) / 1e9
+    f_gbs = sum(kernel_bytes_per_px(1).values()) * npix * wl.n_iter * nb / (t_b * 1e-3) / 1e9
     bvp = {"batch": nb, "batched_ms": round(t_b, 3), "plain_ms": round(t_p, 3),
            "factor": round(t_p / t_b, 3),
            "batched_projections_per_s": round(nb / (t_b * 1e-3), 3),
            "batched_hbm": {"achieved_gbs": round(b_gbs, 1), "peak": peak,
                            "frac": round(b_gbs / peak, 4),
+                           "alg_bytes_per_px_per_iter": model_bytes_per_px(1),
+                           "frac_fused_kernel_bytes": round(f_gbs / peak, 4),
                            "note": "algorithmic bytes of all kernels of all iterations / time; "
                                    f"{nb} x 64 MiB working set exceeds L2"},
            "plain": "one projection per call, kernels launched one by one (no graph)",
@@ -623,6 +639,13 @@ def run_ours(a):
     Dp = torch.from_numpy(ph.poisson(Pp.cpu().numpy(), wp.photons, 9).astype(np.float32)).cuda()
     poly_ms = timeit(lambda: epr.epr_solve_nonlocal(pplan.handle, Dp, Tp, n_iter=wp.n_iter,
                                                     omega=wp.omega, want_info=False), reps=3)
+    # per-kernel times of the 8-line solve (events in a profiled graph: serialised)
+    epr.epr_profile_enable(pplan.handle, True)
+    epr.epr_solve_nonlocal(pplan.handle, Dp, Tp, n_iter=wp.n_iter, omega=wp.omega, want_info=False)
+    torch.cuda.synchronize()
+    pk = epr.epr_profile_read(pplan.handle)
+    epr.epr_profile_enable(pplan.handle, False)
+    poly_kernels = {k: round(tot * 1e3 / wp.n_iter, 2) for k, (cnt, tot) in pk.items() if cnt}
     # vector-Jacobian product of the 8-line forward (the calibration backward)
     gbar = torch.randn(wp.ny, wp.nx, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
     Tbar = torch.empty_like(Tp)
@@ -652,10 +675,13 @@ def run_ours(a):
                 fn = lambda: epr.epr_solve_local(op.handle, Do, Tf, order=model, n_iter=wl.n_iter,
                                                  omega=wl.omega, want_info=False)
             ms_o = timeit(fn, reps=3)
+        o_gbs = model_bytes_per_px(1) * (nd * os_) ** 2 * wl.n_iter / (ms_o * 1e-3) / 1e9
         ovs[name] = {"detector": nd, "oversample": os_, "internal": nd * os_,
                      "model": "nonlocal" if model == 0 else f"local order {model}",
                      "n_iter": wl.n_iter, "ms_per_solve": round(ms_o, 3),
-                     "internal_2048sq_equiv_per_s": round((nd * os_) ** 2 / REF_PIX / (ms_o * 1e-3), 3)}
+                     "internal_2048sq_equiv_per_s": round((nd * os_) ** 2 / REF_PIX / (ms_o * 1e-3), 3),
+                     "hbm": {"alg_bytes_per_internal_px_per_iter": model_bytes_per_px(1),
+                             "achieved_gbs": round(o_gbs, 1), "frac": round(o_gbs / peak, 4)}}
     other["oversampled"] = ovs
 
     # uneven batch of 512 projections (4 lines, solved to kappa <= 1e-4), float and
@@ -671,10 +697,16 @@ def run_ours(a):
         "n_iter": wl.n_iter,
         "ms_per_solve": round(timeit(lambda: epr.epr_solve_nonlocal_wkb1(
             plan.handle, D, T, n_iter=wl.n_iter, omega=wl.omega, want_info=False)), 3)}
+    nlp8 = int(np.size(wp.energy_keV))
+    p_gbs = model_bytes_per_px(nlp8) * wp.nx * wp.ny * wp.n_iter / (poly_ms * 1e-3) / 1e9
     other["polychromatic"] = {"workload": wp.name.replace("x64x", "x1x"),
-                              "n_lines": int(np.size(wp.energy_keV)), "n_iter": wp.n_iter,
+                              "n_lines": nlp8, "n_iter": wp.n_iter,
                               "ms_per_solve": round(poly_ms, 3),
-                              "projections_per_s": round(1e3 / poly_ms, 3)}
+                              "projections_per_s": round(1e3 / poly_ms, 3),
+                              "hbm": {"alg_bytes_per_px_per_iter": model_bytes_per_px(nlp8),
+                                      "achieved_gbs": round(p_gbs, 1), "peak": peak,
+                                      "frac": round(p_gbs / peak, 4)},
+                              "kernels_serialised_us_per_iteration": poly_kernels}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),

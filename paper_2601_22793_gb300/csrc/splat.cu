@@ -48,7 +48,11 @@
 
 namespace {
 
-constexpr int kSplatThreads = 256;
+// Threads of a splat block: 256 for one line; 512 when the line count is a
+// runtime value (several lines), whose per-line accumulators limit a 32 x 64
+// tile to two blocks per SM: the wider block doubles the warps that hide the
+// latency of the shared-memory atomics.
+__host__ __device__ constexpr int splat_threads(int NS) { return NS == 0 ? 512 : 256; }
 
 struct SplatArgs {
     const float* T;          // [B][ny][nx]
@@ -107,9 +111,11 @@ constexpr int kQuad = 4;   // sources per scan work item
 // XT: an x-dependent spectrum, the line constants read per source column
 // from the plan's table (runtime line count and reach only).
 template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0, bool XT = false>
-__global__ void __launch_bounds__(kSplatThreads, (NS == 1 && RESID && RC == 0) ? 4 : 5)
+__global__ void __launch_bounds__(splat_threads(NS),
+                                  NS == 0 ? 2 : ((NS == 1 && RESID && RC == 0) ? 4 : 5))
 k_splat(const EprConsts C, const SplatArgs A)
 {
+    constexpr int kSplatThreads = splat_threads(NS);
     static_assert((TW & (TW - 1)) == 0 && TH * TW <= 4 * 4 * kSplatThreads, "tile shape");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_far_idx[kFarList];
@@ -434,6 +440,14 @@ __global__ void __launch_bounds__(128) k_splat_overflow(const EprConsts C, const
 // overflow sources are in: P <- D - P and P_s <- (D - P) P_s / P as float
 // maps, so that the adjoint gather reads one value per corner and line.  In
 // fixed-point mode the sums are read from the integer maps.
+// The float mode takes four pixels per thread and loads every line's P_s
+// before it stores any r_s (the stores could alias the later loads as far as
+// the compiler knows, which would serialise one memory round trip per line).
+__device__ __forceinline__ float split_one(float r, float p, float pl, float fs)
+{
+    return (p > 1e-30f) ? r * (pl / p) : r * fs;
+}
+
 template <bool DET, bool XT = false>
 __global__ void __launch_bounds__(256) k_split(const EprConsts C, const SplatArgs A)
 {
@@ -443,6 +457,40 @@ __global__ void __launch_bounds__(256) k_split(const EprConsts C, const SplatArg
     epr_grid_release();
     const int ns = C.ns;
     const size_t npix = (size_t)C.nx * C.ny, pb = (size_t)b * npix;
+    if constexpr (!DET) {   // nx % 4 == 0: four pixels of one row per thread
+        const size_t n4 = npix / 4;
+        for (size_t q4 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q4 < n4;
+             q4 += (size_t)gridDim.x * blockDim.x) {
+            const size_t q = 4 * q4;
+            const float4 d = __ldg(reinterpret_cast<const float4*>(A.D + pb + q));
+            const float4 p = *reinterpret_cast<const float4*>(A.P + pb + q);
+            const float4 r = make_float4(d.x - p.x, d.y - p.y, d.z - p.z, d.w - p.w);
+            const int x = (int)(q % (size_t)C.nx);
+            float4 pl[EPR_MAX_LINES];
+#pragma unroll
+            for (int s = 0; s < EPR_MAX_LINES; ++s)
+                if (s < ns && ns > 1)
+                    pl[s] = *reinterpret_cast<const float4*>(A.Ps + (pb * ns) + (size_t)s * npix + q);
+#pragma unroll
+            for (int s = 0; s < EPR_MAX_LINES; ++s) {
+                if (!(s < ns && ns > 1)) continue;
+                float4 o;
+                if constexpr (XT) {
+                    o = make_float4(split_one(r.x, p.x, pl[s].x, xt_get(C, EPR_XT_F, s, x)),
+                                    split_one(r.y, p.y, pl[s].y, xt_get(C, EPR_XT_F, s, x + 1)),
+                                    split_one(r.z, p.z, pl[s].z, xt_get(C, EPR_XT_F, s, x + 2)),
+                                    split_one(r.w, p.w, pl[s].w, xt_get(C, EPR_XT_F, s, x + 3)));
+                } else {
+                    const float fs = C.f[s];
+                    o = make_float4(split_one(r.x, p.x, pl[s].x, fs), split_one(r.y, p.y, pl[s].y, fs),
+                                    split_one(r.z, p.z, pl[s].z, fs), split_one(r.w, p.w, pl[s].w, fs));
+                }
+                *reinterpret_cast<float4*>(A.Ps + (pb * ns) + (size_t)s * npix + q) = o;
+            }
+            *reinterpret_cast<float4*>(A.P + pb + q) = r;
+        }
+        return;
+    }
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < npix;
          q += (size_t)gridDim.x * blockDim.x) {
         const float d = __ldg(&A.D[pb + q]);
@@ -452,7 +500,7 @@ __global__ void __launch_bounds__(256) k_split(const EprConsts C, const SplatArg
             const size_t o = (pb * ns) + (size_t)s * npix + q;
             const float pl = DET ? (float)A.Psq[o] * EPR_FX_INV : A.Ps[o];
             const float fs = XT ? xt_get(C, EPR_XT_F, s, (int)(q % (size_t)C.nx)) : line_const(C.f, s);
-            A.Ps[o] = (p > 1e-30f) ? r * (pl / p) : r * fs;
+            A.Ps[o] = split_one(r, p, pl, fs);
         }
         A.P[pb + q] = r;
     }
@@ -557,7 +605,7 @@ cudaError_t launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t s
 {
     const bool pdl = C.pdl != 0;
     const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID, TH, TW, RC, XT>, grid,
-                                            dim3(kSplatThreads), smem, stream, C, A);
+                                            dim3(splat_threads(NS)), smem, stream, C, A);
     if (e != cudaSuccess) return e;
     return epr_launch_kernel(pdl, k_splat_overflow<DET, RESID, XT>, dim3(128, batch), dim3(128), 0,
                              stream, C, A);

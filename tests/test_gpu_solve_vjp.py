@@ -106,8 +106,11 @@ def test_checkpointing_gives_the_same_gradients(torch, case):
     full = _gpu_vjp(torch, E_, T0, D, wts, checkpoint_every=0)
     for m in (2, 3):
         seg = _gpu_vjp(torch, E_, T0, D, wts, checkpoint_every=m)
-        for a, b in zip(full, seg):
-            assert np.allclose(a, b, rtol=1e-6, atol=1e-6 * np.abs(b).max()), m
+        # maps to 1e-6; the scalars to the ordering of the reverse splat's
+        # float atomics (1e-5)
+        for k, (a, b) in enumerate(zip(full, seg)):
+            tol = 1e-5 if k in (2, 3, 4) else 1e-6
+            assert np.allclose(a, b, rtol=tol, atol=tol * np.abs(b).max()), (m, k)
 
 
 def test_batch_of_projections_is_per_projection(torch, case):
