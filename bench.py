@@ -414,7 +414,10 @@ def run_ours(a):
 
     wl, tau = ph.ellipsoids_mono(seed=rank_seed(rank))
     npix = wl.nx * wl.ny
-    plan = epr.Plan(wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights)
+    # the autotuner picks the splat tile and reach, the column plan and tile width and
+    # the row passes' blocks per SM during the first (warm-up) solve
+    plan = epr.Plan(wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights,
+                    autotune=True)
     stream = torch.cuda.current_stream()
     Tt = torch.from_numpy(tau.astype(np.float32)).cuda()
     Pt = torch.empty_like(Tt)
@@ -580,10 +583,13 @@ def run_ours(a):
     Db = torch.from_numpy(np.stack(Ds)).cuda()
     Tb = torch.empty_like(Db)
     plain = epr.Plan(wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights,
-                     use_graphs=False)
+                     use_graphs=False, autotune=True)
+    # the batch has its own plan, tuned on its first (untimed) call
+    bplan = epr.Plan(wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights,
+                     autotune=True)
 
     def batched():
-        epr.epr_solve_nonlocal(plan.handle, Db, Tb, batch=nb, n_iter=wl.n_iter, omega=wl.omega,
+        epr.epr_solve_nonlocal(bplan.handle, Db, Tb, batch=nb, n_iter=wl.n_iter, omega=wl.omega,
                                want_info=False)
 
     def plain_run():
@@ -609,6 +615,7 @@ def run_ours(a):
     t_b = timeit(batched)
     t_p = timeit(plain_run)
     plain.close()
+    bplan.close()
     it_bytes = model_bytes_per_px(1) * npix   # algorithmic bytes per iteration (model)
     b_gbs = it_bytes * wl.n_iter * nb / (t_b * 1e-3) / 1e9
     f_gbs = sum(kernel_bytes_per_px(1).values()) * npix * wl.n_iter * nb / (t_b * 1e-3) / 1e9
@@ -692,6 +699,15 @@ def run_ours(a):
                                                        max_iter=80, deterministic=True)
     other["unrolled_solve_vjp"] = unrolled_vjp(epr, ph, torch, peak)
     other["xdependent_spectrum"] = xspec_solve(epr, ph, torch, timeit)
+    # the same solves on an untuned plan (the library's default choices)
+    with epr.Plan(wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights) as up:
+        other["untuned_plan"] = {
+            "ms_per_solve": round(timeit(lambda: epr.epr_solve_nonlocal(
+                up.handle, D, T, n_iter=wl.n_iter, omega=wl.omega, want_info=False)), 3),
+            "batched_32_ms": round(timeit(lambda: epr.epr_solve_nonlocal(
+                up.handle, Db, Tb, batch=nb, n_iter=wl.n_iter, omega=wl.omega, want_info=False),
+                reps=3), 3),
+            "ms_per_solve_tuned": round(timeit(solve), 3)}
     other["second_order_nonlocal"] = {
         "workload": "the headline projection, non-local model to second order (WKB1 term)",
         "n_iter": wl.n_iter,

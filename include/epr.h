@@ -86,10 +86,15 @@ typedef struct {
     int use_graphs;        /* 1 = capture solver iterations in a CUDA graph
                               and replay it (default 1). */
     int autotune;          /* 1 = after the first solve, time the splat's tile
-                              shapes and reach on that solve's result and keep
-                              the fastest for later solves (default 0).  The
-                              choice changes only the rounding of the float
-                              splat (fixed-point results are unchanged). */
+                              shapes and reach, and (one-line float solves)
+                              the column pass's radix plan and column-tile
+                              width and the row passes' blocks per SM, on
+                              that solve's result, and keep the fastest for
+                              later solves (default 0).  The choices change
+                              only the rounding of the float path
+                              (fixed-point splat sums are unchanged).  The
+                              tuning allocates a scratch map: the first solve
+                              of a tuned plan must not be stream-captured. */
     int serial_launches;   /* 1 = launch every kernel only after its predecessor
                               has finished.  0 (default) = the solver kernels use
                               programmatic dependent launch: a kernel starts
@@ -108,7 +113,12 @@ typedef struct {
                               map, epr_adjoint and epr_precondition act on fine
                               maps, and epr_vjp and the batch API are not
                               available (EPR_ERR_INVALID_ARG). */
-    int reserved[5];       /* must be zero */
+    int fft_radix;         /* largest radix of the column transforms: 0 = the
+                              default (8; with autotune the tuner may pick 16),
+                              8, or 16 (radix-16 stages where the 2048-row
+                              bulk-copy column pass has them).  Changes only
+                              the rounding of the preconditioner. */
+    int reserved[4];       /* must be zero */
 } epr_options;
 
 /* Solver options. */

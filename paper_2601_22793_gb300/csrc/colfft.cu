@@ -217,7 +217,7 @@ k_col_ct(const EprConsts C, const ColArgs A)
 // off the load/store unit.
 constexpr unsigned int kTmaWaitPolls = 1u << 22;
 
-template <int NY, int CW, int EPT>
+template <int NY, int CW, int EPT, int MAXR = 8>
 __global__ void __launch_bounds__(NY * CW / EPT, NY * CW / EPT == 512 ? 3 : (65536 / 64) / (NY * CW / EPT))
 k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMap map)
 {
@@ -259,12 +259,12 @@ k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMa
     const int s = A.line0 + sl;
     if (kx0 != 0) {   // the filter as the output map of the forward transform
         const ColPaganin<NY, CW, LGCW> f{line_const(C.ha, s), line_const(C.hb, s), C.inv_n, kx0};
-        eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1>(buf, buf, A.tw, tid, f);
+        eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1, MAXR>(buf, buf, A.tw, tid, f);
     } else {
-        eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1>(buf, buf, A.tw, tid);
+        eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1, MAXR>(buf, buf, A.tw, tid);
         col_filter0<NY, CW, LGCW, T>(buf, C, s, tid);
     }
-    eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1>(buf, A.tw, tid);
+    eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1, 0, MAXR>(buf, A.tw, tid);
     epr_grid_release();
     // back to the dense layout in place, in two halves of the elements: the
     // dense slot e holds the padded element e' <= e, so writing the first
@@ -317,8 +317,18 @@ EprColLaunch epr_col_config(const EprConsts& C, int cw_hint)
 }
 
 // The column passes that move their tile by bulk tensor copies.
+// Column tile width of the bulk-copy pass: the plain pass's, except for
+// 8192-row columns (oversampled internal grids), whose bulk-copy tile is two
+// columns wide (a 128 KB tile, one 1024-thread block per SM) where the plain
+// pass takes one.
+static int col_tma_cw(const EprConsts& C, const EprColLaunch& L)
+{
+    return C.ny == 8192 ? 2 : L.CW;
+}
+
 static bool col_tma_case(const EprConsts& C, const EprColLaunch& L)
 {
+    if (C.ny == 8192) return L.EPT == 8 && C.half % 2 == 0;
     if (L.EPT != 8) return false;
     return (L.CW == 4 && (C.ny == 256 || C.ny == 512 || C.ny == 1024)) ||
            (L.CW == 2 && (C.ny == 1536 || C.ny == 2048));
@@ -327,11 +337,11 @@ static bool col_tma_case(const EprConsts& C, const EprColLaunch& L)
 // elements per thread of the bulk-copy pass: 16 for 2048-point columns (256
 // threads and 37 KB per block, four blocks per SM, so the 512 blocks of a
 // 2048^2 projection are resident at once), 8 otherwise
-static int col_tma_ept(const EprConsts& C) { return C.ny == 2048 ? 16 : 8; }
+static int col_tma_ept(const EprConsts& C) { return (C.ny == 2048 || C.ny == 8192) ? 16 : 8; }
 
 static size_t col_tma_smem(const EprConsts& C, const EprColLaunch& L)
 {
-    return 128 + (size_t)PC::len(C.ny * L.CW) * sizeof(float2);
+    return 128 + (size_t)PC::len(C.ny * col_tma_cw(C, L)) * sizeof(float2);
 }
 
 // Tensor map of S seen as `rows` rows of nx floats, with [ny or 256][2 CW]
@@ -354,7 +364,7 @@ bool epr_col_make_map(const EprConsts& C, const float2* S, long long rows, CUten
     }
     const cuuint64_t dims[2] = {(cuuint64_t)C.nx, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)C.nx * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)(2 * L.CW), (cuuint32_t)(C.ny < 256 ? C.ny : 256)};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * col_tma_cw(C, L)), (cuuint32_t)(C.ny < 256 ? C.ny : 256)};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(S), dims,
                               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -405,6 +415,18 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
         EPR_COL_TMA_CASE(512, 4, 8)
         EPR_COL_TMA_CASE(1024, 4, 8)
         EPR_COL_TMA_CASE(1536, 2, 8)
+        if (!done && C.ny == 2048 && L.CW == 2 && ept == 16 && W.col_radix16) {
+            e = epr_launch_kernel(pdl, k_col_tma<2048, 2, 16, 16>, grid, dim3(2048 * 2 / 16), smem,
+                                  stream, C, A, map);
+            done = true;
+        }
+        if (!done && C.ny == 8192) {   // 2 columns per block, radix-16 stages 16, 16, 16, 2
+            A.CW = 2;
+            A.lgCW = 1;
+            e = epr_launch_kernel(pdl, k_col_tma<8192, 2, 16, 16>, dim3(C.half / 2, nl, batch),
+                                  dim3(8192 * 2 / 16), smem, stream, C, A, map);
+            done = true;
+        }
         EPR_COL_TMA_CASE(2048, 2, 16)
 #undef EPR_COL_TMA_CASE
     }
@@ -476,6 +498,8 @@ cudaError_t epr_col_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1024, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1536, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 16>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 16, 16>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<8192, 2, 16, 16>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1536, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<3072, 1, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<4096, 1, 8>);

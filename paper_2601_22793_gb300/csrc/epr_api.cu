@@ -134,6 +134,7 @@ struct epr_plan_s {
     size_t h_hist_elems;
     // tiles
     int splat_TH, splat_TW;
+    int col_cw;          // column tile width of the solver's column pass (0 = default)
     // kernel timing (benchmarks)
     bool profiling;
     struct Rec {
@@ -214,7 +215,10 @@ void free_workspace(epr_plan_s* p)
 {
     for (void* a : p->allocs) cudaFree(a);
     p->allocs.clear();
+    const int radix16 = p->W.col_radix16, occ6 = p->W.row_occ6;   // tuner choices
     memset(&p->W, 0, sizeof(p->W));
+    p->W.col_radix16 = radix16;
+    p->W.row_occ6 = occ6;
     p->W.tw_x = p->tw_x;
     p->W.tw_y = p->tw_y;
     p->cap_batch = 0;
@@ -274,6 +278,7 @@ epr_status ensure_workspace(epr_plan_s* p, int batch, int hist)
     }
     W.tw_x = p->tw_x;
     W.tw_y = p->tw_y;
+    if (p->opt.fft_radix == 16) W.col_radix16 = 1;
     W.col_map = epr_col_make_map(C, W.S, (long long)nb * C.ns * C.ny, &p->col_map) ? &p->col_map
                                                                                    : nullptr;
     p->cap_batch = nb;
@@ -439,7 +444,7 @@ epr_status launch_solve(epr_plan_s* p, const float* D, float* T, int batch, cons
         }
         {
             ProfScope ps(p, EPR_KERNEL_COL, s);
-            EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 1, 0, it, s));
+            EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 1, p->col_cw, it, s));
         }
         {
             ProfScope ps(p, EPR_KERNEL_ROW_INV, s);
@@ -553,6 +558,95 @@ epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int bat
     return EPR_OK;
 }
 
+// Times the column pass's plans on the spectrum of the solve that just ran
+// (each candidate after a fresh forward row pass of the same residual, so
+// every timing sees real data): the bulk-copy pass with radix-8 or radix-16
+// stages where it exists, and the plain passes with column tiles of 1, 2 and
+// 4.  Keeps the fastest and drops the cached graph.  The transforms differ
+// only in rounding.
+epr_status autotune_col(epr_plan_s* p, const float* D, const float* T, int batch, cudaStream_t s)
+{
+    const EprConsts& C = p->C;
+    const int fwd_mode = 0;
+    struct Cand {
+        int cw, radix16;
+    };
+    const Cand cands[5] = {{0, 0}, {0, 1}, {1, 0}, {2, 0}, {4, 0}};
+    cudaEvent_t e0, e1;
+    EPR_TRY(cudaEventCreate(&e0));
+    EPR_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand pick = {p->col_cw, p->W.col_radix16};
+    for (const Cand& c : cands) {
+        if (c.radix16 && !(C.ny == 2048 && p->W.col_map)) continue;
+        if (p->opt.fft_radix != 0 && c.radix16 != (p->opt.fft_radix == 16)) continue;
+        if (c.cw > 0 && C.half % c.cw != 0) continue;
+        p->W.col_radix16 = c.radix16;
+        EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)batch * sizeof(EprProjState), s));
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms up
+            EPR_TRY(cudaEventRecord(e0, s));
+            for (int k = 0; k < 3; ++k) {
+                EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, T, D, nullptr, 0, C.ns, 0, 0.f, batch,
+                                           0, s));
+                EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 0, c.cw, -1, s));
+            }
+            EPR_TRY(cudaEventRecord(e1, s));
+            EPR_TRY(cudaEventSynchronize(e1));
+            EPR_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    p->col_cw = pick.cw;
+    p->W.col_radix16 = pick.radix16;
+    // the one-line 2048-point row passes at five or six blocks per SM: the
+    // forward row pass, the chosen column pass and the inverse row pass on a
+    // scratch copy of the thickness (the solve's result stays as it is)
+    if (C.nx == 2048 && C.ny % 2 == 0) {
+        float* Tc = nullptr;
+        const size_t n = (size_t)batch * C.nx * C.ny;
+        if (cudaMalloc((void**)&Tc, n * sizeof(float)) == cudaSuccess) {
+            float best_r = 1e30f;
+            int pick_r = p->W.row_occ6;
+            for (int occ = 0; occ <= 1; ++occ) {
+                p->W.row_occ6 = occ;
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    EPR_TRY(cudaMemcpyAsync(Tc, T, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+                    EPR_TRY(cudaEventRecord(e0, s));
+                    for (int k = 0; k < 3; ++k) {
+                        EPR_TRY(epr_launch_row_fwd(C, p->W, fwd_mode, Tc, D, nullptr, 0, C.ns, 0,
+                                                   0.f, batch, 0, s));
+                        EPR_TRY(epr_launch_col(C, p->W, 0, C.ns, batch, 0, p->col_cw, -1, s));
+                        EPR_TRY(epr_launch_row_inv(C, p->W, 0, Tc, 0, C.ns, 0, 0.4f, 1e-8f, 0.f,
+                                                   batch, 0, s));
+                    }
+                    EPR_TRY(cudaEventRecord(e1, s));
+                    EPR_TRY(cudaEventSynchronize(e1));
+                    EPR_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                }
+                if (ms < best_r) {
+                    best_r = ms;
+                    pick_r = occ;
+                }
+            }
+            p->W.row_occ6 = pick_r;
+            cudaStreamSynchronize(s);
+            cudaFree(Tc);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (p->has_graph) {
+        cudaGraphExecDestroy(p->gexec);
+        p->has_graph = false;
+    }
+    return EPR_OK;
+}
+
 epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int model,
                         const epr_solve_opts* o, epr_solve_info* info, cudaStream_t s)
 {
@@ -634,6 +728,12 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
     if (p->opt.autotune && !p->tuned && model == EPR_MODEL_NONLOCAL && o->n_iter > 0) {
         st = autotune_splat(p, Dd, Td, batch, s);
         if (st != EPR_OK) return st;
+        // the column pass needs the residual of a plain forward in P (the
+        // monochromatic float solve stores it there; the others after the split)
+        if (p->C.ns == 1 && !p->C.det && p->C.os == 1 && !p->C.xt) {
+            st = autotune_col(p, Dd, Td, batch, s);
+            if (st != EPR_OK) return st;
+        }
     }
     if (info) return collect_info(p, batch, o->n_iter, info, s, 0);
     return EPR_OK;
@@ -729,12 +829,13 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     if (!energy_keV || !delta || !beta || !weights) return EPR_ERR_INVALID_ARG;
     if (n_lines < 1 || n_lines > EPR_MAX_LINES || !(pixel_m > 0.0) || !(L_m >= 0.0))
         return EPR_ERR_INVALID_ARG;
-    epr_options o = {4, 0, 0, 1, 0, 0, 0, {0}};
+    epr_options o = {4, 0, 0, 1, 0, 0, 0, 0, {0}};
     if (opt) o = *opt;
     if (o.max_shift_px < 1 || o.max_shift_px > EPR_MAX_SHIFT || o.overflow_capacity < 0 ||
-        o.oversample < 0 || o.oversample > 16)
+        o.oversample < 0 || o.oversample > 16 ||
+        !(o.fft_radix == 0 || o.fft_radix == 8 || o.fft_radix == 16))
         return EPR_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (o.reserved[i] != 0) return EPR_ERR_INVALID_ARG;
     // oversampled internal grid: everything below is the fine grid's
     const int os = o.oversample > 1 ? o.oversample : 1;
@@ -1544,7 +1645,7 @@ epr_status epr_batch_create(epr_batch_t* out, double pixel_m, double L_m, int n_
         bp->beta[s] = beta[s];
         bp->w[s] = weights[s];
     }
-    epr_options o = {4, 0, 0, 1, 0, 0, 0, {0}};
+    epr_options o = {4, 0, 0, 1, 0, 0, 0, 0, {0}};
     if (opt) o = *opt;
     if (o.oversample > 1) {   // detector and internal sizes differ: plans only
         delete bp;

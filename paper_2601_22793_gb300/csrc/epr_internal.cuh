@@ -93,6 +93,10 @@ struct EprWork {
     int max_blocks;      // columns of part_a / part_b / part_c
     const void* col_map; // host: CUtensorMap of S for the column pass's bulk
                          // copies (NULL: the column pass uses plain loads)
+    int col_radix16;     // host: 1 = the bulk-copy column pass of 2048 rows
+                         // runs radix-16 stages (16, 16, 8 instead of 8, 8, 8, 4)
+    int row_occ6;        // host: 1 = the one-line 2048-point row passes run six
+                         // blocks per SM (40 registers) instead of five
 };
 
 // --- small helpers ---------------------------------------------------------

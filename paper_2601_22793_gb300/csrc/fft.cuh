@@ -130,12 +130,52 @@ __device__ __forceinline__ void dft3(float2& a0, float2& a1, float2& a2)
     a2 = make_float2(m.x - s3 * rd.x, m.y - s3 * rd.y);
 }
 
+// 16-point DFT as 4 x 4: with n = 4 n1 + n2 and k = k1 + 4 k2,
+// X[k1 + 4 k2] = sum_n2 W4^(n2 k2) W16^(n2 k1) sum_n1 W4^(n1 k1) x[4 n1 + n2]:
+// four 4-point DFTs down the columns n2, twiddles W16^(n2 k1), four 4-point
+// DFTs along the rows k1, and the 4 x 4 transpose of the result (register
+// renaming).
+template <int DIR>
+__device__ __forceinline__ void dft16(float2* v)
+{
+    const float c1 = 0.92387953251128675613f;   // cos(pi / 8)
+    const float s1 = 0.38268343236508977173f;   // sin(pi / 8)
+    const float h = 0.70710678118654752440f;
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<DIR>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    // v[n2 + 4 k1] *= exp(DIR 2 pi i n2 k1 / 16)
+    auto rot = [](float2 a, float c, float s) {   // a (c + i s)
+        return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    };
+    const float d = (float)DIR;
+    v[1 + 4] = rot(v[1 + 4], c1, d * s1);           // n2 k1 = 1
+    v[1 + 8] = rot(v[1 + 8], h, d * h);             // 2
+    v[1 + 12] = rot(v[1 + 12], s1, d * c1);         // 3
+    v[2 + 4] = rot(v[2 + 4], h, d * h);             // 2
+    v[2 + 8] = mul_i<DIR>(v[2 + 8]);                // 4
+    v[2 + 12] = rot(v[2 + 12], -h, d * h);          // 6
+    v[3 + 4] = rot(v[3 + 4], s1, d * c1);           // 3
+    v[3 + 8] = rot(v[3 + 8], -h, d * h);            // 6
+    v[3 + 12] = rot(v[3 + 12], -c1, -d * s1);       // 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<DIR>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // v[4 k1 + k2] holds X[k1 + 4 k2]
+    float2 o[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) o[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = o[k];
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void dft(float2* v)
 {
     if constexpr (R == 2) dft2<DIR>(v[0], v[1]);
     else if constexpr (R == 3) dft3<DIR>(v[0], v[1], v[2]);
     else if constexpr (R == 4) dft4<DIR>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 16) dft16<DIR>(v);
     else dft8<DIR>(v);
 }
 
@@ -230,21 +270,24 @@ __host__ __device__ constexpr int ct_pow2_part(int n)
     while (n % 3 == 0) n /= 3;
     return n;
 }
-__host__ __device__ constexpr int ct_n_stages(int n)
+// Stage plans: as many stages of the largest radix maxr (8, or 16 for blocks
+// with 16 elements per thread) as divide the power of two, then one stage of
+// the remaining power of two, then the factors of 3.
+__host__ __device__ constexpr int ct_n_stages(int n, int maxr = 8)
 {
     int p = ct_pow2_part(n), c = 0;
-    while (p >= 8) { p /= 8; ++c; }
+    while (p >= maxr) { p /= maxr; ++c; }
     if (p > 1) ++c;
     int t = n / ct_pow2_part(n);
     while (t > 1) { t /= 3; ++c; }
     return c;
 }
-__host__ __device__ constexpr int ct_radix(int n, int s)
+__host__ __device__ constexpr int ct_radix(int n, int s, int maxr = 8)
 {
     int p = ct_pow2_part(n), k = 0;
-    while (p >= 8) {
-        if (k == s) return 8;
-        p /= 8;
+    while (p >= maxr) {
+        if (k == s) return maxr;
+        p /= maxr;
         ++k;
     }
     if (p > 1) {
@@ -253,10 +296,10 @@ __host__ __device__ constexpr int ct_radix(int n, int s)
     }
     return 3;
 }
-__host__ __device__ constexpr int ct_ns(int n, int s)
+__host__ __device__ constexpr int ct_ns(int n, int s, int maxr = 8)
 {
     int v = 1;
-    for (int i = 0; i < s; ++i) v *= ct_radix(n, i);
+    for (int i = 0; i < s; ++i) v *= ct_radix(n, i, maxr);
     return v;
 }
 
@@ -302,19 +345,27 @@ __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const fl
             }
             if constexpr (NS > 1) {
                 // w^r = (cos r theta, sin r theta) by the three-term recurrence
-                // x_{r+1} = 2 cos(theta) x_r - x_{r-1} (two multiply-adds per power)
+                // x_{r+1} = 2 cos(theta) x_r - x_{r-1} (two multiply-adds per power);
+                // a radix-16 stage runs it to w^7 only and takes w^8 = (w^4)^2 and
+                // w^(8 + r) = w^8 w^r, which keeps every power within a few ulp
                 float2 w = __ldg(&tw[jm * TWSTEP]);
                 if (DIR > 0) w.y = -w.y;
                 const float c2 = w.x + w.x;
-                float2 wp = make_float2(1.f, 0.f), wr = w;
+                constexpr int RREC = R > 8 ? 8 : R;
+                float2 wpow[RREC];
+                wpow[0] = make_float2(1.f, 0.f);
+                if constexpr (RREC > 1) wpow[1] = w;
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    v[k][r] = cmul(v[k][r], wr);
-                    if (r + 1 < R) {
-                        const float2 wn = make_float2(fmaf(c2, wr.x, -wp.x), fmaf(c2, wr.y, -wp.y));
-                        wp = wr;
-                        wr = wn;
-                    }
+                for (int r = 2; r < RREC; ++r)
+                    wpow[r] = make_float2(fmaf(c2, wpow[r - 1].x, -wpow[r - 2].x),
+                                          fmaf(c2, wpow[r - 1].y, -wpow[r - 2].y));
+#pragma unroll
+                for (int r = 1; r < RREC; ++r) v[k][r] = cmul(v[k][r], wpow[r]);
+                if constexpr (R > 8) {
+                    const float2 w8 = cmul(wpow[4], wpow[4]);
+                    v[k][8] = cmul(v[k][8], w8);
+#pragma unroll
+                    for (int r = 9; r < R; ++r) v[k][r] = cmul(v[k][r], cmul(w8, wpow[r - 8]));
                 }
             }
             dst[k] = (jd * NS * R + jm) * SJ + base;
@@ -341,31 +392,36 @@ __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const fl
 }
 
 // Stages S.. of the transform; the last one maps its outputs through post.
-template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int S = 0, class POST = Identity>
+// MAXR = 16 takes radix-16 stages (blocks with at least 16 elements per thread).
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int S = 0, int MAXR = 8,
+          class POST = Identity>
 __device__ __forceinline__ void fft_ct(float2* buf, const float2* __restrict__ tw, int tid,
                                        const POST& post = POST())
 {
-    if constexpr (S + 1 < ct_n_stages(N)) {
-        stage_ct<PAD, PAD, ct_radix(N, S), DIR, EPT, N, ct_ns(N, S), LGSEQ, SJ, SM>(buf, buf, tw, tid);
-        fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, S + 1>(buf, tw, tid, post);
-    } else if constexpr (S + 1 == ct_n_stages(N)) {
-        stage_ct<PAD, PAD, ct_radix(N, S), DIR, EPT, N, ct_ns(N, S), LGSEQ, SJ, SM>(buf, buf, tw, tid,
-                                                                                     post);
+    static_assert(MAXR <= EPT, "a stage's butterfly holds MAXR elements of one thread");
+    if constexpr (S + 1 < ct_n_stages(N, MAXR)) {
+        stage_ct<PAD, PAD, ct_radix(N, S, MAXR), DIR, EPT, N, ct_ns(N, S, MAXR), LGSEQ, SJ, SM>(buf, buf,
+                                                                                              tw, tid);
+        fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, S + 1, MAXR>(buf, tw, tid, post);
+    } else if constexpr (S + 1 == ct_n_stages(N, MAXR)) {
+        stage_ct<PAD, PAD, ct_radix(N, S, MAXR), DIR, EPT, N, ct_ns(N, S, MAXR), LGSEQ, SJ, SM>(
+            buf, buf, tw, tid, post);
     }
 }
 
 // The same transform with its input in a dense tile `in` (element j of
 // sequence m at in[j * SJ + m * SM]), which may be buf itself; the result is
 // in buf.
-template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, class POST = Identity>
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int MAXR = 8,
+          class POST = Identity>
 __device__ __forceinline__ void fft_ct_from(const float2* in, float2* buf, const float2* __restrict__ tw,
                                             int tid, const POST& post = POST())
 {
-    if constexpr (ct_n_stages(N) == 1) {
-        stage_ct<Dense, PAD, ct_radix(N, 0), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid, post);
+    if constexpr (ct_n_stages(N, MAXR) == 1) {
+        stage_ct<Dense, PAD, ct_radix(N, 0, MAXR), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid, post);
     } else {
-        stage_ct<Dense, PAD, ct_radix(N, 0), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid);
-        fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, 1>(buf, tw, tid, post);
+        stage_ct<Dense, PAD, ct_radix(N, 0, MAXR), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid);
+        fft_ct<PAD, DIR, N, EPT, LGSEQ, SJ, SM, 1, MAXR>(buf, tw, tid, post);
     }
 }
 

@@ -441,8 +441,11 @@ __device__ __forceinline__ int row_of(int e) { return RP == 1 ? 0 : (int)((unsig
 // gradient, alias the FFT rows, which are written only after the last
 // thickness read (row_fwd_mono_smem).  256-thread monochromatic blocks run
 // five per SM (48 registers).
-template <int NX, int RP, bool POLY, bool GATHER>
-__global__ void __launch_bounds__(NX * RP / kEPT, (NX * RP / kEPT == 256 && !POLY) ? 5 : (65536 / 64) / (NX * RP / kEPT))
+//
+// OCC6: six 256-thread blocks per SM (40 registers) instead of five: better
+// in a batch of projections, worse for one (the autotuner decides).
+template <int NX, int RP, bool POLY, bool GATHER, bool OCC6 = false>
+__global__ void __launch_bounds__(NX * RP / kEPT, OCC6 ? 6 : (NX * RP / kEPT == 256 && !POLY) ? 5 : (65536 / 64) / (NX * RP / kEPT))
 k_row_fwd_mono(const EprConsts C, const RowArgs A)
 {
     constexpr int T = NX * RP / kEPT;
@@ -583,8 +586,8 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
 
 // five 256-thread blocks per SM (48 registers): its shared memory is the FFT
 // rows and 2 RP thickness rows only (row_inv_mono_smem)
-template <int NX, int RP>
-__global__ void __launch_bounds__(NX * RP / kEPT, NX * RP / kEPT == 256 ? 5 : (65536 / 64) / (NX * RP / kEPT))
+template <int NX, int RP, bool OCC6 = false>
+__global__ void __launch_bounds__(NX * RP / kEPT, OCC6 ? 6 : NX * RP / kEPT == 256 ? 5 : (65536 / 64) / (NX * RP / kEPT))
 k_row_inv_mono(const EprConsts C, const RowArgs A)
 {
     constexpr int T = NX * RP / kEPT;
@@ -777,7 +780,7 @@ size_t row_inv_poly_smem(int nx, int rp)
 // launch a specialised mono kernel when nx has one; returns false otherwise
 template <bool FWD, bool GATHER = true>
 bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream, const EprConsts& C,
-                    const RowArgs& A, cudaError_t& err)
+                    const RowArgs& A, cudaError_t& err, bool W_occ6 = false)
 {
     // one line: the mono kernels; several: forward with a line per grid z,
     // inverse looping over the lines
@@ -805,6 +808,15 @@ bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream,
     EPR_MONO_CASE(512, 4)
     EPR_MONO_CASE(1024, 2)
     EPR_MONO_CASE(1536, 1)
+    if (nx == 2048 && rp == 1 && !poly && GATHER && W_occ6) {   // six blocks per SM
+        if (FWD)
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<2048, 1, false, true, true>, grid,
+                                    dim3(256), row_fwd_mono_smem(2048, 1), stream, C, A);
+        else
+            err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<2048, 1, true>, grid, dim3(256),
+                                    row_inv_mono_smem(2048, 1), stream, C, A);
+        return true;
+    }
     EPR_MONO_CASE(2048, 1)
     EPR_MONO_CASE(3072, 1)
     EPR_MONO_CASE(4096, 1)
@@ -831,6 +843,8 @@ cudaError_t init_mono_ct()
     EPR_MONO_INIT(1024, 2)
     EPR_MONO_INIT(1536, 1)
     EPR_MONO_INIT(2048, 1)
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<2048, 1, false, true, true>);
+    if (e == cudaSuccess) e = allow(k_row_inv_mono<2048, 1, true>);
     EPR_MONO_INIT(3072, 1)
     EPR_MONO_INIT(4096, 1)
     EPR_MONO_INIT(8192, 1)
@@ -888,7 +902,7 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, c
     } else if (mode == FWD_SOLVE_NL) {
         // the residual D - P is in P and, with several lines, the split
         // residuals in P_s (written by the splat flush or the split kernel)
-        if (!launch_mono_ct<true>(C.nx, L.RP, grid, L.smem, stream, C, A, e)) {
+        if (!launch_mono_ct<true>(C.nx, L.RP, grid, L.smem, stream, C, A, e, W.row_occ6 != 0)) {
             if (mono) go(k_row_fwd<FWD_SOLVE_NL, false, true, 1>);
             else go(k_row_fwd<FWD_SOLVE_NL, false, true, 0>);
         }
@@ -920,7 +934,7 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
     if (mode == INV_UPDATE && C.xt) {
         go(k_row_inv<INV_UPDATE, 0, true>);   // per-column update constants
     } else if (mode == INV_UPDATE) {
-        if (launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A, e)) {
+        if (launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A, e, W.row_occ6 != 0)) {
         } else if (nl == 1) go(k_row_inv<INV_UPDATE, 1>);
         else go(k_row_inv<INV_UPDATE, 0>);
     } else {

@@ -50,7 +50,8 @@ class epr_options(ctypes.Structure):
     _fields_ = [("max_shift_px", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("overflow_capacity", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("serial_launches", ctypes.c_int),
-                ("oversample", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("oversample", ctypes.c_int), ("fft_radix", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class epr_batch_desc(ctypes.Structure):
@@ -198,15 +199,15 @@ def _darr(x):
 
 
 def _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune,
-             serial_launches=False, oversample=1):
+             serial_launches=False, oversample=1, fft_radix=0):
     return epr_options(int(max_shift_px), int(bool(deterministic)), int(overflow_capacity),
                        int(bool(use_graphs)), int(bool(autotune)), int(bool(serial_launches)),
-                       int(oversample), (ctypes.c_int * 5)())
+                       int(oversample), int(fft_radix), (ctypes.c_int * 4)())
 
 
 def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
                     max_shift_px=4, deterministic=False, overflow_capacity=0, use_graphs=True,
-                    autotune=False, serial_launches=False, oversample=1):
+                    autotune=False, serial_launches=False, oversample=1, fft_radix=0):
     """Returns an opaque plan handle (int).  With oversample = o > 1, nx, ny
     and pixel_m are the detector's and the solve runs on the o-times finer
     grid (see epr_options in the C header)."""
@@ -216,7 +217,7 @@ def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
     bt, bp = _darr(beta)
     w, wp = _darr(np.ones(E.size) if weights is None else weights)
     opt = _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune,
-                   serial_launches, oversample)
+                   serial_launches, oversample, fft_radix)
     h = ctypes.c_void_p()
     _check(lib.epr_plan_create(ctypes.byref(h), int(nx), int(ny), float(pixel_m), float(L_m),
                                int(E.size), Ep, dp_, bp, wp, ctypes.byref(opt)), "epr_plan_create")
@@ -372,7 +373,7 @@ def epr_solve_local(plan, D, T, batch=1, order=2, n_iter=20, omega=1.0, tol=0.0,
 
 def epr_batch_create(pixel_m, L_m, energy_keV, delta, beta, weights=None, max_shift_px=4,
                      deterministic=False, overflow_capacity=0, use_graphs=True, autotune=False,
-                     serial_launches=False, oversample=1):
+                     serial_launches=False, oversample=1, fft_radix=0):
     """Returns an opaque batch handle (int) for epr_solve_nonlocal_batched
     (oversample > 1 is refused)."""
     lib = load()
@@ -381,7 +382,7 @@ def epr_batch_create(pixel_m, L_m, energy_keV, delta, beta, weights=None, max_sh
     bt, bp = _darr(beta)
     w, wp = _darr(np.ones(E.size) if weights is None else weights)
     opt = _options(max_shift_px, deterministic, overflow_capacity, use_graphs, autotune,
-                   serial_launches, oversample)
+                   serial_launches, oversample, fft_radix)
     h = ctypes.c_void_p()
     _check(lib.epr_batch_create(ctypes.byref(h), float(pixel_m), float(L_m), int(E.size), Ep, dp_,
                                 bp, wp, ctypes.byref(opt)), "epr_batch_create")
