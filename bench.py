@@ -478,6 +478,7 @@ def run_ours(a):
 
     # convergence figures of this workload
     info = epr.epr_solve_nonlocal(plan.handle, D, T, n_iter=wl.n_iter, omega=wl.omega)
+    tuning = epr.epr_plan_get_tuning(plan.handle)
 
     # kernel roofline: the same solves with per-kernel CUDA events
     epr.epr_profile_enable(plan.handle, True)
@@ -614,6 +615,7 @@ def run_ours(a):
 
     t_b = timeit(batched)
     t_p = timeit(plain_run)
+    btuning = epr.epr_plan_get_tuning(bplan.handle)
     plain.close()
     bplan.close()
     it_bytes = model_bytes_per_px(1) * npix   # algorithmic bytes per iteration (model)
@@ -628,6 +630,7 @@ def run_ours(a):
                            "frac_fused_kernel_bytes": round(f_gbs / peak, 4),
                            "note": "algorithmic bytes of all kernels of all iterations / time; "
                                    f"{nb} x 64 MiB working set exceeds L2"},
+           "tuning": btuning,
            "plain": "one projection per call, kernels launched one by one (no graph)",
            "batched": "one call for all projections, iteration loop replayed as a CUDA graph"}
 
@@ -730,6 +733,7 @@ def run_ours(a):
            "data": data_src,
            "config": bench_config(wl, world),
            "convergence": convergence(info),
+           "tuning": tuning,
            "roofline": roofline, "e2e": e2e, "batched_vs_plain": bvp, "other_workloads": other,
            "gpu_launches": int(launches),
            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],

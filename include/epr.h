@@ -282,6 +282,13 @@ epr_status epr_solve_nonlocal_wkb1(epr_plan_t plan, const float* D, float* T, in
 epr_status epr_solve_local(epr_plan_t plan, const float* D, float* T, int batch, int order,
                            const epr_solve_opts* opts, epr_solve_info* info, void* stream);
 
+/* The plan's kernel choices (not in the paper), as 7 host ints: splat tile
+ * rows and columns, splat reach (px), column tile width (0 = the default
+ * pass), largest radix of the column transforms (8 or 16), row-pass blocks
+ * per SM (5 or 6) and whether the autotuner has run (1) or the defaults hold
+ * (0). */
+epr_status epr_plan_get_tuning(epr_plan_t plan, int* out);
+
 /* Synchronise `stream`, read and clear the plan's device error word:
  * EPR_ERR_NONFINITE if the data of a solve since the last check held a NaN or
  * an infinity, EPR_ERR_TIMEOUT if a bounded device wait on a bulk copy ran

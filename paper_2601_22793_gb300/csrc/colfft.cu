@@ -441,6 +441,7 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
     EPR_COL_CASE(1024, 4, 8)
     EPR_COL_CASE(1536, 2, 8)
     EPR_COL_CASE(2048, 2, 8)
+    EPR_COL_CASE(2048, 1, 8)
     EPR_COL_CASE(3072, 1, 8)
     EPR_COL_CASE(4096, 1, 8)
     EPR_COL_CASE(8192, 1, 8)
@@ -493,6 +494,7 @@ cudaError_t epr_col_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<512, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1024, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<2048, 2, 8>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<2048, 1, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<256, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<512, 4, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1024, 4, 8>);

@@ -1488,6 +1488,19 @@ epr_status epr_plan_set_xspec(epr_plan_t p, const epr_xspec* tab)
     return EPR_OK;
 }
 
+epr_status epr_plan_get_tuning(epr_plan_t p, int* out)
+{
+    if (!p || !out) return EPR_ERR_INVALID_ARG;
+    out[0] = p->splat_TH;
+    out[1] = p->splat_TW;
+    out[2] = p->C.smax;
+    out[3] = p->col_cw;
+    out[4] = p->W.col_radix16 ? 16 : 8;
+    out[5] = p->W.row_occ6 ? 6 : 5;
+    out[6] = p->tuned ? 1 : 0;
+    return EPR_OK;
+}
+
 epr_status epr_check_device_status(epr_plan_t p, void* stream)
 {
     if (!p) return EPR_ERR_INVALID_ARG;

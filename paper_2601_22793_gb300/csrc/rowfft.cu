@@ -444,7 +444,9 @@ __device__ __forceinline__ int row_of(int e) { return RP == 1 ? 0 : (int)((unsig
 //
 // OCC6: six 256-thread blocks per SM (40 registers) instead of five: better
 // in a batch of projections, worse for one (the autotuner decides).
-template <int NX, int RP, bool POLY, bool GATHER, bool OCC6 = false>
+// XT: an x-dependent spectrum, the shift constant of each object column from
+// the plan's table.
+template <int NX, int RP, bool POLY, bool GATHER, bool OCC6 = false, bool XT = false>
 __global__ void __launch_bounds__(NX * RP / kEPT, OCC6 ? 6 : (NX * RP / kEPT == 256 && !POLY) ? 5 : (65536 / 64) / (NX * RP / kEPT))
 k_row_fwd_mono(const EprConsts C, const RowArgs A)
 {
@@ -519,8 +521,9 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
             else if (yhi) gy = t - tr[x - NX];
             else gy = 0.5f * (tr[NX + x] - tr[x - NX]);
             const float lim = 2.f * (float)(NX > ny ? NX : ny);
-            const float ux = fminf(fmaxf(cs * gx, -lim), lim);
-            const float uy = fminf(fmaxf(cs * gy, -lim), lim);
+            const float csx = XT ? xt_get(C, EPR_XT_C, A.line0 + sl, x) : cs;
+            const float ux = fminf(fmaxf(csx * gx, -lim), lim);
+            const float uy = fminf(fmaxf(csx * gy, -lim), lim);
             const float fx = floorf(ux), fy = floorf(uy);
             const float dx = ux - fx, dy = uy - fy;
             const int cx = x + (int)fx, cy = y + (int)fy;
@@ -586,7 +589,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
 
 // five 256-thread blocks per SM (48 registers): its shared memory is the FFT
 // rows and 2 RP thickness rows only (row_inv_mono_smem)
-template <int NX, int RP, bool OCC6 = false>
+template <int NX, int RP, bool OCC6 = false, bool XT = false>
 __global__ void __launch_bounds__(NX * RP / kEPT, OCC6 ? 6 : NX * RP / kEPT == 256 ? 5 : (65536 / 64) / (NX * RP / kEPT))
 k_row_inv_mono(const EprConsts C, const RowArgs A)
 {
@@ -648,8 +651,14 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
         const float2 h = zs[PR::idx(m * SM + x)];
         const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
         const float t0 = Tsh[(2 * m) * NX + x], t1 = Tsh[(2 * m + 1) * NX + x];
-        const float l0 = w * log_ratio(t0, h.x, om_f, mus, A.eps);
-        const float l1 = w * log_ratio(t1, h.y, om_f, mus, A.eps);
+        float wx = w, omx = om_f, mux = mus;
+        if constexpr (XT) {
+            wx = xt_get(C, EPR_XT_WPROJ, 0, x);
+            mux = xt_get(C, EPR_XT_MU, 0, x);
+            omx = A.omega / xt_get(C, EPR_XT_F, 0, x);
+        }
+        const float l0 = wx * log_ratio(t0, h.x, omx, mux, A.eps);
+        const float l1 = wx * log_ratio(t1, h.y, omx, mux, A.eps);
         const float n0 = t0 - l0, n1 = t1 - l1;
         A.Out[q0] = n0;
         A.Out[q0 + NX] = n1;
@@ -664,7 +673,7 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
 // rows of its filtered spectrum and w_s ln(I'_s / I_s), accumulated per
 // pixel in shared memory (each thread owns its pixels); then T' = T - sum
 // and the kappa partial sums.
-template <int NX, int RP>
+template <int NX, int RP, bool XT = false>
 __global__ void __launch_bounds__(NX * RP / kEPT, (65536 / 64) / (NX * RP / kEPT))
 k_row_inv_poly(const EprConsts C, const RowArgs A)
 {
@@ -729,8 +738,14 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
             const int m = row_of<NX, RP>(e), x = e - m * NX;
             const float2 h = zs[PR::idx(m * SM + x)];
             const int i0 = (2 * m) * NX + x;
-            const float l0 = w * log_ratio(Tsh[i0], h.x, om_f, mus, A.eps);
-            const float l1 = w * log_ratio(Tsh[i0 + NX], h.y, om_f, mus, A.eps);
+            float wx = w, omx = om_f, mux = mus;
+            if constexpr (XT) {
+                wx = xt_get(C, EPR_XT_WPROJ, s, x);
+                mux = xt_get(C, EPR_XT_MU, s, x);
+                omx = A.omega / xt_get(C, EPR_XT_F, s, x);
+            }
+            const float l0 = wx * log_ratio(Tsh[i0], h.x, omx, mux, A.eps);
+            const float l1 = wx * log_ratio(Tsh[i0 + NX], h.y, omx, mux, A.eps);
             acc[i0] = sl == 0 ? l0 : acc[i0] + l0;
             acc[i0 + NX] = sl == 0 ? l1 : acc[i0 + NX] + l1;
         }
@@ -778,6 +793,38 @@ size_t row_inv_poly_smem(int nx, int rp)
 }
 
 // launch a specialised mono kernel when nx has one; returns false otherwise
+// The compile-time row kernels with per-column constants (x-dependent
+// spectrum) for the common row lengths; false when nx has none.
+template <bool FWD>
+bool launch_xt_ct(int nx, int rp, dim3 grid, cudaStream_t stream, const EprConsts& C,
+                  const RowArgs& A, cudaError_t& err)
+{
+    const bool poly = A.nl > 1;
+#define EPR_XT_CASE(NXV, RPV)                                                                 \
+    if (nx == NXV && rp == RPV) {                                                             \
+        const dim3 blk(NXV * RPV / kEPT);                                                     \
+        if (FWD && !poly)                                                                     \
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, false, true, false, true>, \
+                                    grid, blk, row_fwd_mono_smem(NXV, RPV), stream, C, A);     \
+        else if (FWD)                                                                         \
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<NXV, RPV, true, true, false, true>, \
+                                    dim3(grid.x, grid.y, A.nl), blk, row_fwd_mono_smem(NXV, RPV), \
+                                    stream, C, A);                                            \
+        else if (!poly)                                                                       \
+            err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<NXV, RPV, false, true>, grid, blk, \
+                                    row_inv_mono_smem(NXV, RPV), stream, C, A);               \
+        else                                                                                  \
+            err = epr_launch_kernel(C.pdl != 0, k_row_inv_poly<NXV, RPV, true>, grid, blk,     \
+                                    row_inv_poly_smem(NXV, RPV), stream, C, A);               \
+        return true;                                                                          \
+    }
+    EPR_XT_CASE(1024, 2)
+    EPR_XT_CASE(2048, 1)
+    EPR_XT_CASE(4096, 1)
+#undef EPR_XT_CASE
+    return false;
+}
+
 template <bool FWD, bool GATHER = true>
 bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream, const EprConsts& C,
                     const RowArgs& A, cudaError_t& err, bool W_occ6 = false)
@@ -845,6 +892,15 @@ cudaError_t init_mono_ct()
     EPR_MONO_INIT(2048, 1)
     if (e == cudaSuccess) e = allow(k_row_fwd_mono<2048, 1, false, true, true>);
     if (e == cudaSuccess) e = allow(k_row_inv_mono<2048, 1, true>);
+#define EPR_XT_INIT(NXV, RPV)                                                        \
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, false, true, false, true>); \
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<NXV, RPV, true, true, false, true>);  \
+    if (e == cudaSuccess) e = allow(k_row_inv_mono<NXV, RPV, false, true>);              \
+    if (e == cudaSuccess) e = allow(k_row_inv_poly<NXV, RPV, true>);
+    EPR_XT_INIT(1024, 2)
+    EPR_XT_INIT(2048, 1)
+    EPR_XT_INIT(4096, 1)
+#undef EPR_XT_INIT
     EPR_MONO_INIT(3072, 1)
     EPR_MONO_INIT(4096, 1)
     EPR_MONO_INIT(8192, 1)
@@ -897,8 +953,9 @@ cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, c
     const bool mono = nl == 1, pdl = C.pdl != 0;
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kernel) { e = epr_launch_kernel(pdl, kernel, grid, blk, L.smem, stream, C, A); };
-    if (mode == FWD_SOLVE_NL && C.xt) {
-        go(k_row_fwd<FWD_SOLVE_NL, false, true, 0, true>);   // per-column shift constants
+    if (mode == FWD_SOLVE_NL && C.xt) {   // per-column shift constants
+        if (!launch_xt_ct<true>(C.nx, L.RP, grid, stream, C, A, e))
+            go(k_row_fwd<FWD_SOLVE_NL, false, true, 0, true>);
     } else if (mode == FWD_SOLVE_NL) {
         // the residual D - P is in P and, with several lines, the split
         // residuals in P_s (written by the splat flush or the split kernel)
@@ -931,8 +988,9 @@ cudaError_t epr_launch_row_inv(const EprConsts& C, const EprWork& W, int mode, f
     const bool pdl = C.pdl != 0;
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kernel) { e = epr_launch_kernel(pdl, kernel, grid, blk, L.smem, stream, C, A); };
-    if (mode == INV_UPDATE && C.xt) {
-        go(k_row_inv<INV_UPDATE, 0, true>);   // per-column update constants
+    if (mode == INV_UPDATE && C.xt) {   // per-column update constants
+        if (!launch_xt_ct<false>(C.nx, L.RP, grid, stream, C, A, e))
+            go(k_row_inv<INV_UPDATE, 0, true>);
     } else if (mode == INV_UPDATE) {
         if (launch_mono_ct<false>(C.nx, L.RP, grid, L.smem, stream, C, A, e, W.row_occ6 != 0)) {
         } else if (nl == 1) go(k_row_inv<INV_UPDATE, 1>);

@@ -48,11 +48,13 @@
 
 namespace {
 
-// Threads of a splat block: 256 for one line; 512 when the line count is a
-// runtime value (several lines), whose per-line accumulators limit a 32 x 64
-// tile to two blocks per SM: the wider block doubles the warps that hide the
-// latency of the shared-memory atomics.
-__host__ __device__ constexpr int splat_threads(int NS) { return NS == 0 ? 512 : 256; }
+// Threads of a splat block: 256 for one line; 512 for several lines (a
+// runtime count, or 4 or 8 at compile time), whose per-line accumulators
+// limit a 32 x 64 tile to two blocks per SM: the wider block doubles the
+// warps that hide the latency of the shared-memory atomics.  With the line
+// count known at compile time the line loop unrolls, so the compiler can
+// interleave the lines' dependency chains.
+__host__ __device__ constexpr int splat_threads(int NS) { return NS == 1 ? 256 : 512; }
 
 struct SplatArgs {
     const float* T;          // [B][ny][nx]
@@ -112,7 +114,7 @@ constexpr int kQuad = 4;   // sources per scan work item
 // from the plan's table (runtime line count and reach only).
 template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0, bool XT = false>
 __global__ void __launch_bounds__(splat_threads(NS),
-                                  NS == 0 ? 2 : ((NS == 1 && RESID && RC == 0) ? 4 : 5))
+                                  NS != 1 ? 2 : ((RESID && RC == 0) ? 4 : 5))
 k_splat(const EprConsts C, const SplatArgs A)
 {
     constexpr int kSplatThreads = splat_threads(NS);
@@ -631,6 +633,12 @@ cudaError_t launch_shape(const EprConsts& C, const SplatArgs& A, int resid, dim3
         }
     }
     if (mono) return launch_t<1, false, false, TH, TW>(C, A, grid, smem, batch, stream);
+    if (C.ns == 8)   // the common polychromatic counts with an unrolled line loop
+        return C.smax == 4 ? launch_t<8, false, false, TH, TW, 4>(C, A, grid, smem, batch, stream)
+                           : launch_t<8, false, false, TH, TW>(C, A, grid, smem, batch, stream);
+    if (C.ns == 4)
+        return C.smax == 4 ? launch_t<4, false, false, TH, TW, 4>(C, A, grid, smem, batch, stream)
+                           : launch_t<4, false, false, TH, TW>(C, A, grid, smem, batch, stream);
     switch (C.smax) {
     case 3: return launch_t<0, false, false, TH, TW, 3>(C, A, grid, smem, batch, stream);
     case 4: return launch_t<0, false, false, TH, TW, 4>(C, A, grid, smem, batch, stream);
@@ -653,6 +661,10 @@ cudaError_t init_shape()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 3>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 4>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 6>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<8, false, false, TH, TW, 4>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<8, false, false, TH, TW>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<4, false, false, TH, TW, 4>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<4, false, false, TH, TW>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, true, false, TH, TW, 0, true>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 0, true>);
     return e;

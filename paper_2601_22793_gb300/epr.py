@@ -41,7 +41,7 @@ SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
            "epr_check_device_status", "epr_status_string", "epr_launch_count",
            "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc", "epr_vjp",
            "epr_batch_create", "epr_batch_destroy", "epr_solve_nonlocal_batched",
-           "epr_plan_set_xspec", "epr_solve_vjp", "epr_plan_set_params")
+           "epr_plan_set_xspec", "epr_solve_vjp", "epr_plan_set_params", "epr_plan_get_tuning")
 
 KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 
@@ -142,6 +142,8 @@ def load(path: str | None = None):
         lib.epr_solve_nonlocal_batched.restype = i
         lib.epr_solve_vjp.argtypes = [vp, vp, vp, i, i, d, d, i, vp, vp, vp, vp, dp, dp, dp, vp]
         lib.epr_solve_vjp.restype = i
+        lib.epr_plan_get_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        lib.epr_plan_get_tuning.restype = i
         lib.epr_plan_set_params.argtypes = [vp, d, dp, dp]
         lib.epr_plan_set_params.restype = i
         lib.epr_plan_set_xspec.argtypes = [vp, ctypes.POINTER(epr_xspec)]
@@ -222,6 +224,14 @@ def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
     _check(lib.epr_plan_create(ctypes.byref(h), int(nx), int(ny), float(pixel_m), float(L_m),
                                int(E.size), Ep, dp_, bp, wp, ctypes.byref(opt)), "epr_plan_create")
     return h.value
+
+
+def epr_plan_get_tuning(plan) -> dict:
+    """The plan's kernel choices (defaults, or the autotuner's)."""
+    v = (ctypes.c_int * 7)()
+    _check(load().epr_plan_get_tuning(plan, v), "epr_plan_get_tuning")
+    return {"splat_tile": [v[0], v[1]], "splat_reach": v[2], "col_tile_width": v[3],
+            "col_radix": v[4], "row_blocks_per_sm": v[5], "tuned": bool(v[6])}
 
 
 def epr_plan_set_params(plan, L_m, delta, beta):

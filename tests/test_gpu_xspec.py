@@ -2,7 +2,9 @@
 spatially varying spectra"; a knot table of per-line weights, delta and beta
 across the detector columns) against the FP64 oracle, through the C ABI:
 forward, adjoint and preconditioner at <= 1e-5 relative L2, the solve at
-<= 1e-4, float and fixed-point splat, ragged sizes."""
+<= 1e-4, float and fixed-point splat, ragged sizes, and the row lengths with
+compile-time row kernels that read the per-column constants (1024, 2048,
+4096)."""
 import numpy as np
 import pytest
 
@@ -84,7 +86,9 @@ def test_xspec_forward_adjoint_precondition(torch, oracle, n_lines, ny, nx, det)
 
 
 @pytest.mark.parametrize("n_lines,ny,nx,det", [(2, 128, 192, False), (4, 256, 512, True),
-                                               (1, 256, 256, False)])
+                                               (1, 256, 256, False), (3, 64, 1024, False),
+                                               (1, 48, 2048, False), (2, 32, 2048, True),
+                                               (2, 32, 4096, False)])
 def test_xspec_solve_vs_oracle(torch, oracle, n_lines, ny, nx, det):
     from paper_2601_22793_gb300 import epr as E
     phys, tab, tau = _case(n_lines, ny, nx, 21 + n_lines)
