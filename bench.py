@@ -73,6 +73,10 @@ def _args():
                     help="ncu case: 1 = the monochromatic workload, 8 = the polychromatic one")
     ap.add_argument("--oversample", type=int, default=1,
                     help="ncu case: solve on a grid oversampled by this factor (non-local)")
+    ap.add_argument("--tuned", action="store_true",
+                    help="ncu case: an autotuned plan (tuned by the first warm-up solve); the "
+                         "steps run inside the NVTX range 'steps' (ncu --nvtx --nvtx-include "
+                         "steps/)")
     return ap.parse_args()
 
 
@@ -770,16 +774,23 @@ def ncu_case(a):
     if os_ > 1:   # the detector of the workload, an internal grid o times finer
         taus = [np.kron(t, np.ones((os_, os_))) for t in taus]
     plan = epr.Plan(n, n, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights,
-                    oversample=os_, max_shift_px=8 if os_ > 1 else 4)
+                    oversample=os_, max_shift_px=8 if os_ > 1 else 4, autotune=a.tuned)
     Tt = torch.from_numpy(np.stack(taus).astype(np.float32)).cuda()
     P = torch.empty((a.batch, n, n), device="cuda")
     epr.epr_forward(plan.handle, Tt, P, batch=a.batch)
     D = P.clamp_min(0) + 0.01 * torch.randn_like(P)
     T = torch.empty_like(Tt)
-    for _ in range(a.warmup + a.steps):
+    for k in range(a.warmup + a.steps):
+        if k == a.warmup:
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("steps")
         epr.epr_solve_nonlocal(plan.handle, D, T, batch=a.batch, n_iter=a.iters,
                                omega=wl.omega, want_info=False)
     torch.cuda.synchronize()
+    if a.steps > 0:
+        torch.cuda.nvtx.range_pop()
+    if a.tuned:
+        print("tuning:", epr.epr_plan_get_tuning(plan.handle))
     plan.close()
     print(f"ncu case done: batch {a.batch}, {a.warmup + a.steps} solves of {a.iters} iterations")
 
