@@ -73,6 +73,9 @@ def _args():
                     help="ncu case: 1 = the monochromatic workload, 8 = the polychromatic one")
     ap.add_argument("--oversample", type=int, default=1,
                     help="ncu case: solve on a grid oversampled by this factor (non-local)")
+    ap.add_argument("--tuning", default="",
+                    help="ncu case: kernel choices as printed by a --tuned run (JSON), applied "
+                         "instead of tuning under the profiler")
     ap.add_argument("--tuned", action="store_true",
                     help="ncu case: an autotuned plan (tuned by the first warm-up solve); the "
                          "steps run inside the NVTX range 'steps' (ncu --nvtx --nvtx-include "
@@ -780,6 +783,8 @@ def ncu_case(a):
     epr.epr_forward(plan.handle, Tt, P, batch=a.batch)
     D = P.clamp_min(0) + 0.01 * torch.randn_like(P)
     T = torch.empty_like(Tt)
+    if a.tuning:
+        epr.epr_plan_set_tuning(plan.handle, json.loads(a.tuning))
     for k in range(a.warmup + a.steps):
         if k == a.warmup:
             torch.cuda.synchronize()
@@ -789,8 +794,8 @@ def ncu_case(a):
     torch.cuda.synchronize()
     if a.steps > 0:
         torch.cuda.nvtx.range_pop()
-    if a.tuned:
-        print("tuning:", epr.epr_plan_get_tuning(plan.handle))
+    if a.tuned or a.tuning:
+        print("tuning:", json.dumps(epr.epr_plan_get_tuning(plan.handle)))
     plan.close()
     print(f"ncu case done: batch {a.batch}, {a.warmup + a.steps} solves of {a.iters} iterations")
 

@@ -289,6 +289,12 @@ epr_status epr_solve_local(epr_plan_t plan, const float* D, float* T, int batch,
  * (0). */
 epr_status epr_plan_get_tuning(epr_plan_t plan, int* out);
 
+/* Set those choices (the first 6 ints of the same layout), e.g. to reproduce
+ * a tuned plan in another process.  The splat tile must fit the plan's
+ * lines in shared memory.  The autotuner does not run over them.
+ * EPR_ERR_INVALID_ARG for a value outside the supported set. */
+epr_status epr_plan_set_tuning(epr_plan_t plan, const int* in);
+
 /* Synchronise `stream`, read and clear the plan's device error word:
  * EPR_ERR_NONFINITE if the data of a solve since the last check held a NaN or
  * an infinity, EPR_ERR_TIMEOUT if a bounded device wait on a bulk copy ran

@@ -1501,6 +1501,34 @@ epr_status epr_plan_get_tuning(epr_plan_t p, int* out)
     return EPR_OK;
 }
 
+epr_status epr_plan_set_tuning(epr_plan_t p, const int* in)
+{
+    if (!p || !in) return EPR_ERR_INVALID_ARG;
+    const int th = in[0], tw = in[1], reach = in[2], cw = in[3], radix = in[4], occ = in[5];
+    const bool tile_ok = (th == 64 || th == 32) && (tw == 64 || tw == 32);
+    if (!tile_ok || reach < 1 || reach > EPR_MAX_SHIFT || !(cw == 0 || cw == 1 || cw == 2 || cw == 4) ||
+        !(radix == 8 || radix == 16) || !(occ == 5 || occ == 6))
+        return EPR_ERR_INVALID_ARG;
+    EprConsts C = p->C;
+    C.smax = reach;
+    if ((size_t)C.ns * th * tw * (C.det ? 8 : 4) > 65536) return EPR_ERR_INVALID_ARG;
+    int optin = 0;
+    EPR_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    if (epr_splat_smem(C, th, tw) + 4096 > (size_t)optin) return EPR_ERR_INVALID_ARG;
+    p->C.smax = reach;
+    p->splat_TH = th;
+    p->splat_TW = tw;
+    p->col_cw = cw;
+    p->W.col_radix16 = radix == 16;
+    p->W.row_occ6 = occ == 6;
+    p->tuned = true;   // the autotuner does not run over an explicit choice
+    if (p->has_graph) {
+        cudaGraphExecDestroy(p->gexec);
+        p->has_graph = false;
+    }
+    return EPR_OK;
+}
+
 epr_status epr_check_device_status(epr_plan_t p, void* stream)
 {
     if (!p) return EPR_ERR_INVALID_ARG;

@@ -41,7 +41,8 @@ SYMBOLS = ("epr_plan_create", "epr_plan_destroy", "epr_forward", "epr_adjoint",
            "epr_check_device_status", "epr_status_string", "epr_launch_count",
            "epr_profile_enable", "epr_profile_read", "epr_precondition_noalloc", "epr_vjp",
            "epr_batch_create", "epr_batch_destroy", "epr_solve_nonlocal_batched",
-           "epr_plan_set_xspec", "epr_solve_vjp", "epr_plan_set_params", "epr_plan_get_tuning")
+           "epr_plan_set_xspec", "epr_solve_vjp", "epr_plan_set_params", "epr_plan_get_tuning",
+           "epr_plan_set_tuning")
 
 KERNEL_KINDS = ("splat", "row_fwd", "col", "row_inv", "local", "other")
 
@@ -144,6 +145,8 @@ def load(path: str | None = None):
         lib.epr_solve_vjp.restype = i
         lib.epr_plan_get_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         lib.epr_plan_get_tuning.restype = i
+        lib.epr_plan_set_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        lib.epr_plan_set_tuning.restype = i
         lib.epr_plan_set_params.argtypes = [vp, d, dp, dp]
         lib.epr_plan_set_params.restype = i
         lib.epr_plan_set_xspec.argtypes = [vp, ctypes.POINTER(epr_xspec)]
@@ -232,6 +235,14 @@ def epr_plan_get_tuning(plan) -> dict:
     _check(load().epr_plan_get_tuning(plan, v), "epr_plan_get_tuning")
     return {"splat_tile": [v[0], v[1]], "splat_reach": v[2], "col_tile_width": v[3],
             "col_radix": v[4], "row_blocks_per_sm": v[5], "tuned": bool(v[6])}
+
+
+def epr_plan_set_tuning(plan, tuning: dict):
+    """Apply kernel choices in the form epr_plan_get_tuning returns."""
+    v = (ctypes.c_int * 7)(tuning["splat_tile"][0], tuning["splat_tile"][1], tuning["splat_reach"],
+                           tuning["col_tile_width"], tuning["col_radix"],
+                           tuning["row_blocks_per_sm"], 1)
+    _check(load().epr_plan_set_tuning(plan, v), "epr_plan_set_tuning")
 
 
 def epr_plan_set_params(plan, L_m, delta, beta):

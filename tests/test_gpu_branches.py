@@ -11,6 +11,9 @@ against the FP64 oracle through the C ABI.
 * The residual split without transport (L = 0): with omega = 1 every line is
   scaled by D / P (the positivity-preserving split), on data far from the
   model.
+* An overflow list too small for the long-shift sources: the condition is
+  reported (and cleared by the check), and a list with room for every pixel
+  gives the oracle's forward.
 
 Tolerance: relative L2 <= 1e-4 on the thickness."""
 import numpy as np
@@ -117,3 +120,37 @@ def test_split_without_transport_scales_every_line(torch, oracle):
                          omega=1.0)
     Tg, _ = _gpu_solve(torch, E, nx, ny, p, 0.0, Es, d, b, w, D, 1, 1.0, T0=tau)
     assert rel(Tg, Tr) < 1e-5
+
+
+def test_full_overflow_list_is_reported(torch, oracle):
+    """Long-shift sources beyond the overflow list's capacity are reported:
+    EPR_ERR_SHIFT_OVERFLOW from a solve with info, and from
+    epr_check_device_status after a forward, which is then cleared; with room
+    in the list the same forward matches the oracle."""
+    from paper_2601_22793_gb300 import epr as E
+    wl, tau = ph.ellipsoids_mono(n=256, n_ell=20, seed=41, semi=(6.0, 40.0))
+    tau = (4.0 * tau).astype(np.float32)          # shifts of many pixels at the edges
+    ln = oracle.Lines(wl.energy_keV, wl.delta, wl.beta, wl.weights, wl.L, wl.pixel)
+    gy, gx = oracle.gradient(tau.astype(np.float64))
+    c = ln.params()[3][0]
+    n_far = int(np.sum((np.abs(c * gx) > 2) | (np.abs(c * gy) > 2)))
+    assert n_far > 64
+    args = (wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights)
+    Tt = torch.from_numpy(tau).cuda()
+    P = torch.empty_like(Tt)
+    with E.Plan(*args, max_shift_px=2, overflow_capacity=16) as p:
+        E.epr_forward(p.handle, Tt, P)
+        with pytest.raises(E.EprError) as e:
+            E.epr_check_device_status(p.handle)
+        assert e.value.status == E.EPR_ERR_SHIFT_OVERFLOW
+        E.epr_check_device_status(p.handle)          # cleared
+        D = torch.ones_like(Tt)
+        T = tau.copy()
+        Td = torch.from_numpy(T).cuda()
+        with pytest.raises(E.EprError) as e:
+            E.epr_solve_nonlocal(p.handle, D, Td, n_iter=1, omega=0.4, init=1)
+        assert e.value.status == E.EPR_ERR_SHIFT_OVERFLOW
+    with E.Plan(*args, max_shift_px=2, overflow_capacity=wl.nx * wl.ny) as p:
+        E.epr_forward(p.handle, Tt, P)
+        E.epr_check_device_status(p.handle)
+        assert rel(P.cpu().numpy(), oracle.forward(ln, tau.astype(np.float64))) < 1e-5

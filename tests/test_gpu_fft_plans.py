@@ -85,3 +85,31 @@ def test_autotuned_plan_solves_like_the_default(torch, oracle):
             outs[tune] = T.cpu().numpy()
     assert rel(outs[True], outs[False]) < 1e-5
     assert rel(outs[True], Tr) < 1e-4
+
+
+def test_tuning_carries_over_between_plans(torch, oracle):
+    """epr_plan_get_tuning / epr_plan_set_tuning: a second plan given the
+    first plan's tuned choices solves as the tuned plan does; invalid choices
+    are refused."""
+    from paper_2601_22793_gb300 import epr as E
+    wl, tau = ph.ellipsoids_mono(n=1024, n_ell=60, seed=33, n_iter=4)
+    ln = oracle.Lines(wl.energy_keV, wl.delta, wl.beta, wl.weights, wl.L, wl.pixel)
+    D = ph.poisson(oracle.forward(ln, tau), 1e4, 34).astype(np.float32)
+    args = (wl.nx, wl.ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights)
+    Dd = torch.from_numpy(D).cuda()
+    with E.Plan(*args, autotune=True) as a, E.Plan(*args) as b:
+        T = torch.empty_like(Dd)
+        E.epr_solve_nonlocal(a.handle, Dd, T, n_iter=4, omega=0.4)   # tunes
+        tun = E.epr_plan_get_tuning(a.handle)
+        assert tun["tuned"]
+        E.epr_solve_nonlocal(a.handle, Dd, T, n_iter=4, omega=0.4)
+        Ta = T.cpu().numpy()
+        assert not E.epr_plan_get_tuning(b.handle)["tuned"]
+        E.epr_plan_set_tuning(b.handle, tun)
+        assert E.epr_plan_get_tuning(b.handle) == tun
+        T2 = torch.empty_like(Dd)
+        E.epr_solve_nonlocal(b.handle, Dd, T2, n_iter=4, omega=0.4)
+        assert rel(T2.cpu().numpy(), Ta) < 1e-6
+        bad = dict(tun, col_radix=12)
+        with pytest.raises(E.EprError):
+            E.epr_plan_set_tuning(b.handle, bad)
