@@ -86,9 +86,11 @@ typedef struct {
     int use_graphs;        /* 1 = capture solver iterations in a CUDA graph
                               and replay it (default 1). */
     int autotune;          /* 1 = after the first solve, time the splat's tile
-                              shapes and reach, and (one-line float solves)
-                              the column pass's radix plan and column-tile
-                              width and the row passes' blocks per SM, on
+                              shapes, reach and blocks per SM, the column
+                              pass's radix plan, column-tile width and blocks
+                              per SM (float mode, no oversampling, uniform
+                              spectrum) and
+                              the one-line row passes' blocks per SM, on
                               that solve's result, and keep the fastest for
                               later solves (default 0).  The choices change
                               only the rounding of the float path
@@ -282,17 +284,21 @@ epr_status epr_solve_nonlocal_wkb1(epr_plan_t plan, const float* D, float* T, in
 epr_status epr_solve_local(epr_plan_t plan, const float* D, float* T, int batch, int order,
                            const epr_solve_opts* opts, epr_solve_info* info, void* stream);
 
-/* The plan's kernel choices (not in the paper), as 7 host ints: splat tile
+/* The plan's kernel choices (not in the paper), as 9 host ints: splat tile
  * rows and columns, splat reach (px), column tile width (0 = the default
  * pass), largest radix of the column transforms (8 or 16), row-pass blocks
- * per SM (5 or 6) and whether the autotuner has run (1) or the defaults hold
- * (0). */
+ * per SM (5 or 6), blocks per SM of the radix-16 column pass (4 or 5),
+ * blocks per SM of the one-line residual splat (5 or 6; 6 exists for tiles
+ * below 64 x 64 at reach 3 and 4) and whether the autotuner has run (1) or
+ * the defaults hold (0). */
 epr_status epr_plan_get_tuning(epr_plan_t plan, int* out);
 
-/* Set those choices (the first 6 ints of the same layout), e.g. to reproduce
+/* Set those choices (the first 8 ints of the same layout), e.g. to reproduce
  * a tuned plan in another process.  The splat tile must fit the plan's
- * lines in shared memory.  The autotuner does not run over them.
- * EPR_ERR_INVALID_ARG for a value outside the supported set. */
+ * lines in shared memory; 5 column-pass blocks per SM need radix 16, 6 splat
+ * blocks per SM a tile and reach that have the variant.  The
+ * autotuner does not run over them.  EPR_ERR_INVALID_ARG for a value outside
+ * the supported set. */
 epr_status epr_plan_set_tuning(epr_plan_t plan, const int* in);
 
 /* Synchronise `stream`, read and clear the plan's device error word:

@@ -217,8 +217,11 @@ k_col_ct(const EprConsts C, const ColArgs A)
 // off the load/store unit.
 constexpr unsigned int kTmaWaitPolls = 1u << 22;
 
-template <int NY, int CW, int EPT, int MAXR = 8>
-__global__ void __launch_bounds__(NY * CW / EPT, NY * CW / EPT == 512 ? 3 : (65536 / 64) / (NY * CW / EPT))
+// OCC > 0: that many blocks per SM (the radix-16 2048-row pass at five: 48
+// registers, no spills), else the default bound.
+template <int NY, int CW, int EPT, int MAXR = 8, int OCC = 0>
+__global__ void __launch_bounds__(NY * CW / EPT,
+                                  OCC > 0 ? OCC : NY * CW / EPT == 512 ? 3 : (65536 / 64) / (NY * CW / EPT))
 k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMap map)
 {
     constexpr int T = NY * CW / EPT;
@@ -416,8 +419,10 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
         EPR_COL_TMA_CASE(1024, 4, 8)
         EPR_COL_TMA_CASE(1536, 2, 8)
         if (!done && C.ny == 2048 && L.CW == 2 && ept == 16 && W.col_radix16) {
-            e = epr_launch_kernel(pdl, k_col_tma<2048, 2, 16, 16>, grid, dim3(2048 * 2 / 16), smem,
-                                  stream, C, A, map);
+            e = W.col_occ5 ? epr_launch_kernel(pdl, k_col_tma<2048, 2, 16, 16, 5>, grid,
+                                               dim3(2048 * 2 / 16), smem, stream, C, A, map)
+                           : epr_launch_kernel(pdl, k_col_tma<2048, 2, 16, 16>, grid,
+                                               dim3(2048 * 2 / 16), smem, stream, C, A, map);
             done = true;
         }
         if (!done && C.ny == 8192) {   // 2 columns per block, radix-16 stages 16, 16, 16, 2
@@ -501,6 +506,7 @@ cudaError_t epr_col_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<1536, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 16>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 16, 16>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 16, 16, 5>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<8192, 2, 16, 16>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1536, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<3072, 1, 8>);

@@ -31,6 +31,7 @@ cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* 
                              int resid, int parity, int batch, int TH, int TW, int check_done,
                              cudaStream_t stream);
 size_t epr_splat_smem(const EprConsts& C, int TH, int TW);
+bool epr_splat_has_occ6(int TH, int TW, int reach);
 cudaError_t epr_splat_init();
 cudaError_t epr_launch_row_fwd(const EprConsts& C, const EprWork& W, int mode, const float* T,
                                const float* D, const float* G, int line0, int nl, int it,
@@ -215,10 +216,14 @@ void free_workspace(epr_plan_s* p)
 {
     for (void* a : p->allocs) cudaFree(a);
     p->allocs.clear();
-    const int radix16 = p->W.col_radix16, occ6 = p->W.row_occ6;   // tuner choices
+    // tuner choices
+    const int radix16 = p->W.col_radix16, occ6 = p->W.row_occ6, cocc5 = p->W.col_occ5;
+    const int socc6 = p->W.splat_occ6;
     memset(&p->W, 0, sizeof(p->W));
     p->W.col_radix16 = radix16;
     p->W.row_occ6 = occ6;
+    p->W.col_occ5 = cocc5;
+    p->W.splat_occ6 = socc6;
     p->W.tw_x = p->tw_x;
     p->W.tw_y = p->tw_y;
     p->cap_batch = 0;
@@ -500,9 +505,11 @@ epr_status collect_info(epr_plan_s* p, int batch, int n_iter, epr_solve_info* in
     return EPR_OK;
 }
 
-// Times the splat's tile shapes and reach on the thickness T of the solve
-// that just ran (the real shift field), keeps the fastest and drops the
-// cached graph.  Changes only the float summation order of the splat.
+// Times the splat's tile shapes and reach (and, where the one-line residual
+// kernel has the variant, five or six blocks per SM) on the thickness T of
+// the solve that just ran (the real shift field), keeps the fastest and
+// drops the cached graph.  Changes only the float summation order of the
+// splat.
 epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int batch, cudaStream_t s)
 {
     p->tuned = true;
@@ -514,17 +521,19 @@ epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int bat
     int optin = 0;
     EPR_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     float best = 1e30f;
-    int bTH = sTH, bTW = sTW, bR = saved.smax;
+    int bTH = sTH, bTW = sTW, bR = saved.smax, bO = p->W.splat_occ6;
     cudaEvent_t e0, e1;
     EPR_TRY(cudaEventCreate(&e0));
     EPR_TRY(cudaEventCreate(&e1));
     for (const auto& t : tiles) {
-        for (int r : reaches) {
+        for (int r : reaches) for (int occ6 = 0; occ6 <= 1; ++occ6) {
+            if (occ6 && !(resid && epr_splat_has_occ6(t[0], t[1], r))) continue;
             p->C.smax = r;
             if ((size_t)p->C.ns * t[0] * t[1] * (p->C.det ? 8 : 4) > 65536) continue;
             if (epr_splat_smem(p->C, t[0], t[1]) + 4096 > (size_t)optin) continue;
             p->splat_TH = t[0];
             p->splat_TW = t[1];
+            p->W.splat_occ6 = occ6;
             EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)batch * sizeof(EprProjState), s));
             epr_status st = launch_forward(p, T, resid ? D : nullptr, 0, batch, EPR_MODEL_NONLOCAL, 0, s);
             if (st != EPR_OK) return st;
@@ -542,6 +551,7 @@ epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int bat
                 bTH = t[0];
                 bTW = t[1];
                 bR = r;
+                bO = occ6;
             }
         }
     }
@@ -551,6 +561,7 @@ epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int bat
     p->C.smax = bR;
     p->splat_TH = bTH;
     p->splat_TW = bTW;
+    p->W.splat_occ6 = bO;
     if (p->has_graph) {
         cudaGraphExecDestroy(p->gexec);
         p->has_graph = false;
@@ -569,19 +580,20 @@ epr_status autotune_col(epr_plan_s* p, const float* D, const float* T, int batch
     const EprConsts& C = p->C;
     const int fwd_mode = 0;
     struct Cand {
-        int cw, radix16;
+        int cw, radix16, occ5;
     };
-    const Cand cands[5] = {{0, 0}, {0, 1}, {1, 0}, {2, 0}, {4, 0}};
+    const Cand cands[6] = {{0, 0, 0}, {0, 1, 0}, {0, 1, 1}, {1, 0, 0}, {2, 0, 0}, {4, 0, 0}};
     cudaEvent_t e0, e1;
     EPR_TRY(cudaEventCreate(&e0));
     EPR_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    Cand pick = {p->col_cw, p->W.col_radix16};
+    Cand pick = {p->col_cw, p->W.col_radix16, p->W.col_occ5};
     for (const Cand& c : cands) {
         if (c.radix16 && !(C.ny == 2048 && p->W.col_map)) continue;
         if (p->opt.fft_radix != 0 && c.radix16 != (p->opt.fft_radix == 16)) continue;
         if (c.cw > 0 && C.half % c.cw != 0) continue;
         p->W.col_radix16 = c.radix16;
+        p->W.col_occ5 = c.occ5;
         EPR_TRY(cudaMemsetAsync(p->W.st, 0, (size_t)batch * sizeof(EprProjState), s));
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms up
@@ -602,10 +614,11 @@ epr_status autotune_col(epr_plan_s* p, const float* D, const float* T, int batch
     }
     p->col_cw = pick.cw;
     p->W.col_radix16 = pick.radix16;
+    p->W.col_occ5 = pick.occ5;
     // the one-line 2048-point row passes at five or six blocks per SM: the
     // forward row pass, the chosen column pass and the inverse row pass on a
     // scratch copy of the thickness (the solve's result stays as it is)
-    if (C.nx == 2048 && C.ny % 2 == 0) {
+    if (C.nx == 2048 && C.ny % 2 == 0 && C.ns == 1) {
         float* Tc = nullptr;
         const size_t n = (size_t)batch * C.nx * C.ny;
         if (cudaMalloc((void**)&Tc, n * sizeof(float)) == cudaSuccess) {
@@ -728,9 +741,12 @@ epr_status solve_common(epr_plan_s* p, const float* D, float* T, int batch, int 
     if (p->opt.autotune && !p->tuned && model == EPR_MODEL_NONLOCAL && o->n_iter > 0) {
         st = autotune_splat(p, Dd, Td, batch, s);
         if (st != EPR_OK) return st;
-        // the column pass needs the residual of a plain forward in P (the
-        // monochromatic float solve stores it there; the others after the split)
-        if (p->C.ns == 1 && !p->C.det && p->C.os == 1 && !p->C.xt) {
+        // the column pass is timed on the residual of a plain forward (the
+        // monochromatic float solve's splat stores it in P; with several
+        // lines the split after the last forward of the splat tuner).  Not
+        // in fixed-point mode, whose results stay those of the default plan.
+        if (p->C.os == 1 && !p->C.xt && !p->C.det) {
+            if (p->C.ns > 1) EPR_TRY(epr_launch_split(p->C, p->W, Dd, batch, 0, 0, s));
             st = autotune_col(p, Dd, Td, batch, s);
             if (st != EPR_OK) return st;
         }
@@ -915,6 +931,7 @@ epr_status epr_plan_create(epr_plan_t* out, int nx, int ny, double pixel_m, doub
     }
     p->W.tw_x = p->tw_x;
     p->W.tw_y = p->tw_y;
+    p->W.col_radix16 = p->opt.fft_radix == 16;   // the choice the tuning calls report
     choose_splat_tiles(p);
     *out = p;
     return EPR_OK;
@@ -1497,7 +1514,9 @@ epr_status epr_plan_get_tuning(epr_plan_t p, int* out)
     out[3] = p->col_cw;
     out[4] = p->W.col_radix16 ? 16 : 8;
     out[5] = p->W.row_occ6 ? 6 : 5;
-    out[6] = p->tuned ? 1 : 0;
+    out[6] = p->W.col_occ5 ? 5 : 4;
+    out[7] = p->W.splat_occ6 ? 6 : 5;
+    out[8] = p->tuned ? 1 : 0;
     return EPR_OK;
 }
 
@@ -1505,9 +1524,12 @@ epr_status epr_plan_set_tuning(epr_plan_t p, const int* in)
 {
     if (!p || !in) return EPR_ERR_INVALID_ARG;
     const int th = in[0], tw = in[1], reach = in[2], cw = in[3], radix = in[4], occ = in[5];
+    const int cocc = in[6], socc = in[7];
     const bool tile_ok = (th == 64 || th == 32) && (tw == 64 || tw == 32);
     if (!tile_ok || reach < 1 || reach > EPR_MAX_SHIFT || !(cw == 0 || cw == 1 || cw == 2 || cw == 4) ||
-        !(radix == 8 || radix == 16) || !(occ == 5 || occ == 6))
+        !(radix == 8 || radix == 16) || !(occ == 5 || occ == 6) || !(cocc == 4 || cocc == 5) ||
+        (cocc == 5 && radix != 16) || !(socc == 5 || socc == 6) ||
+        (socc == 6 && !epr_splat_has_occ6(th, tw, reach)))
         return EPR_ERR_INVALID_ARG;
     EprConsts C = p->C;
     C.smax = reach;
@@ -1521,6 +1543,8 @@ epr_status epr_plan_set_tuning(epr_plan_t p, const int* in)
     p->col_cw = cw;
     p->W.col_radix16 = radix == 16;
     p->W.row_occ6 = occ == 6;
+    p->W.col_occ5 = cocc == 5;
+    p->W.splat_occ6 = socc == 6;
     p->tuned = true;   // the autotuner does not run over an explicit choice
     if (p->has_graph) {
         cudaGraphExecDestroy(p->gexec);

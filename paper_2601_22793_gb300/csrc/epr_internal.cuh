@@ -97,6 +97,10 @@ struct EprWork {
                          // runs radix-16 stages (16, 16, 8 instead of 8, 8, 8, 4)
     int row_occ6;        // host: 1 = the one-line 2048-point row passes run six
                          // blocks per SM (40 registers) instead of five
+    int col_occ5;        // host: 1 = that radix-16 column pass runs five blocks
+                         // per SM (48 registers) instead of four
+    int splat_occ6;      // host: 1 = the one-line residual splat runs six blocks
+                         // per SM (tiles below 64 x 64, reach 3 or 4)
 };
 
 // --- small helpers ---------------------------------------------------------

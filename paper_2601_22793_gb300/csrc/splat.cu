@@ -112,9 +112,11 @@ constexpr int kQuad = 4;   // sources per scan work item
 // registers and runs four.
 // XT: an x-dependent spectrum, the line constants read per source column
 // from the plan's table (runtime line count and reach only).
-template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0, bool XT = false>
+// OCC > 0: that many blocks per SM (six for the one-line residual kernels of
+// the tiles smaller than 64 x 64 at reach 3 and 4: 40 registers, no spills).
+template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0, bool XT = false, int OCC = 0>
 __global__ void __launch_bounds__(splat_threads(NS),
-                                  NS != 1 ? 2 : ((RESID && RC == 0) ? 4 : 5))
+                                  OCC > 0 ? OCC : NS != 1 ? 2 : ((RESID && RC == 0) ? 4 : 5))
 k_splat(const EprConsts C, const SplatArgs A)
 {
     constexpr int kSplatThreads = splat_threads(NS);
@@ -601,21 +603,25 @@ __global__ void __launch_bounds__(256) k_bin_os(const EprConsts C, const SplatAr
     }
 }
 
-template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0, bool XT = false>
+template <int NS, bool DET, bool RESID, int TH, int TW, int RC = 0, bool XT = false, int OCC = 0>
 cudaError_t launch_t(const EprConsts& C, const SplatArgs& A, dim3 grid, size_t smem, int batch,
                      cudaStream_t stream)
 {
     const bool pdl = C.pdl != 0;
-    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID, TH, TW, RC, XT>, grid,
+    const cudaError_t e = epr_launch_kernel(pdl, k_splat<NS, DET, RESID, TH, TW, RC, XT, OCC>, grid,
                                             dim3(splat_threads(NS)), smem, stream, C, A);
     if (e != cudaSuccess) return e;
     return epr_launch_kernel(pdl, k_splat_overflow<DET, RESID, XT>, dim3(128, batch), dim3(128), 0,
                              stream, C, A);
 }
 
+// Tiles whose one-line residual kernel has a six-blocks-per-SM variant.
 template <int TH, int TW>
-cudaError_t launch_shape(const EprConsts& C, const SplatArgs& A, int resid, dim3 grid, size_t smem,
-                         int batch, cudaStream_t stream)
+constexpr bool has_occ6() { return TH * TW < 64 * 64; }
+
+template <int TH, int TW>
+cudaError_t launch_shape(const EprConsts& C, const SplatArgs& A, int resid, bool occ6, dim3 grid,
+                         size_t smem, int batch, cudaStream_t stream)
 {
     const bool mono = C.ns == 1;
     if (C.xt)   // x-dependent spectrum: the generic kernels with per-column constants
@@ -624,6 +630,12 @@ cudaError_t launch_shape(const EprConsts& C, const SplatArgs& A, int resid, dim3
     if (C.det)
         return mono ? launch_t<1, true, false, TH, TW>(C, A, grid, smem, batch, stream)
                     : launch_t<0, true, false, TH, TW>(C, A, grid, smem, batch, stream);
+    if constexpr (has_occ6<TH, TW>()) {
+        if (resid && mono && occ6 && C.smax == 3)
+            return launch_t<1, false, true, TH, TW, 3, false, 6>(C, A, grid, smem, batch, stream);
+        if (resid && mono && occ6 && C.smax == 4)
+            return launch_t<1, false, true, TH, TW, 4, false, 6>(C, A, grid, smem, batch, stream);
+    }
     if (resid && mono) {
         switch (C.smax) {
         case 3: return launch_t<1, false, true, TH, TW, 3>(C, A, grid, smem, batch, stream);
@@ -667,10 +679,17 @@ cudaError_t init_shape()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<4, false, false, TH, TW>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, true, false, TH, TW, 0, true>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<0, false, false, TH, TW, 0, true>);
+    if constexpr (has_occ6<TH, TW>()) {
+        if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true, TH, TW, 3, false, 6>);
+        if (e == cudaSuccess) e = epr_allow_max_smem(k_splat<1, false, true, TH, TW, 4, false, 6>);
+    }
     return e;
 }
 
 }  // namespace
+
+// Whether the six-blocks-per-SM residual splat exists for this tile and reach.
+bool epr_splat_has_occ6(int TH, int TW, int reach) { return TH * TW < 64 * 64 && (reach == 3 || reach == 4); }
 
 size_t epr_splat_smem(const EprConsts& C, int TH, int TW)
 {
@@ -712,10 +731,10 @@ cudaError_t epr_launch_splat(const EprConsts& C, const EprWork& W, const float* 
     const size_t smem = epr_splat_smem(C, TH, TW);
     dim3 grid((C.nx + TW - 1) / TW, (C.ny + TH - 1) / TH, batch);
     cudaError_t e;
-    if (TH == 64 && TW == 64) e = launch_shape<64, 64>(C, A, resid, grid, smem, batch, stream);
-    else if (TH == 32 && TW == 64) e = launch_shape<32, 64>(C, A, resid, grid, smem, batch, stream);
-    else if (TH == 64 && TW == 32) e = launch_shape<64, 32>(C, A, resid, grid, smem, batch, stream);
-    else if (TH == 32 && TW == 32) e = launch_shape<32, 32>(C, A, resid, grid, smem, batch, stream);
+    if (TH == 64 && TW == 64) e = launch_shape<64, 64>(C, A, resid, W.splat_occ6 != 0, grid, smem, batch, stream);
+    else if (TH == 32 && TW == 64) e = launch_shape<32, 64>(C, A, resid, W.splat_occ6 != 0, grid, smem, batch, stream);
+    else if (TH == 64 && TW == 32) e = launch_shape<64, 32>(C, A, resid, W.splat_occ6 != 0, grid, smem, batch, stream);
+    else if (TH == 32 && TW == 32) e = launch_shape<32, 32>(C, A, resid, W.splat_occ6 != 0, grid, smem, batch, stream);
     else return cudaErrorInvalidValue;
     epr_count_launch(2);
     return e != cudaSuccess ? e : cudaGetLastError();

@@ -231,17 +231,19 @@ def epr_plan_create(nx, ny, pixel_m, L_m, energy_keV, delta, beta, weights=None,
 
 def epr_plan_get_tuning(plan) -> dict:
     """The plan's kernel choices (defaults, or the autotuner's)."""
-    v = (ctypes.c_int * 7)()
+    v = (ctypes.c_int * 9)()
     _check(load().epr_plan_get_tuning(plan, v), "epr_plan_get_tuning")
     return {"splat_tile": [v[0], v[1]], "splat_reach": v[2], "col_tile_width": v[3],
-            "col_radix": v[4], "row_blocks_per_sm": v[5], "tuned": bool(v[6])}
+            "col_radix": v[4], "row_blocks_per_sm": v[5], "col_blocks_per_sm": v[6],
+            "splat_blocks_per_sm": v[7], "tuned": bool(v[8])}
 
 
 def epr_plan_set_tuning(plan, tuning: dict):
     """Apply kernel choices in the form epr_plan_get_tuning returns."""
-    v = (ctypes.c_int * 7)(tuning["splat_tile"][0], tuning["splat_tile"][1], tuning["splat_reach"],
+    v = (ctypes.c_int * 9)(tuning["splat_tile"][0], tuning["splat_tile"][1], tuning["splat_reach"],
                            tuning["col_tile_width"], tuning["col_radix"],
-                           tuning["row_blocks_per_sm"], 1)
+                           tuning["row_blocks_per_sm"], tuning.get("col_blocks_per_sm", 4),
+                           tuning.get("splat_blocks_per_sm", 5), 1)
     _check(load().epr_plan_set_tuning(plan, v), "epr_plan_set_tuning")
 
 

@@ -154,3 +154,35 @@ def test_full_overflow_list_is_reported(torch, oracle):
         E.epr_forward(p.handle, Tt, P)
         E.epr_check_device_status(p.handle)
         assert rel(P.cpu().numpy(), oracle.forward(ln, tau.astype(np.float64))) < 1e-5
+
+
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_split_where_the_model_vanishes(torch, oracle, deterministic):
+    """The residual split where P <= 1e-30 takes r f_s (the second branch of
+    the split): a block of the starting thickness is so thick (mu T = 75 for
+    the less absorbed of two lines at 80 and 82 keV, 81 for the other, so
+    exp(mu T) stays finite in float32) that no line reaches the detector
+    there; one iteration from that thickness, float and fixed-point splat.
+    Tolerance 1e-4: the update cancels T = 0.9 against ln(1 + q) / mu."""
+    from paper_2601_22793_gb300 import epr as E
+    p, L = 20e-6, 30.0
+    Es = [80.0, 82.0]
+    d = [ph.BONE[0] * (80.0 / e) ** 2 for e in Es]
+    b = [ph.BONE[1] * (80.0 / e) ** 4 for e in Es]
+    w = [0.45, 0.55]
+    ln = oracle.Lines(Es, d, b, w, L=L, pixel=p)
+    _, mu, *_ = ln.params()
+    ny, nx = 128, 192
+    ells = ph.random_ellipsoids(ny, nx, 12, 4.0, 20.0, seed=61)
+    T0 = ph.project_ellipsoids(ells, ny, nx, p)
+    T0[40:80, 50:110] = 75.0 / float(np.min(mu))
+    Pr = oracle.forward(ln, T0)
+    assert np.all(Pr[45:75, 55:105] <= 1e-30)
+    D = (1.0 + 0.02 * np.random.default_rng(62).normal(size=(ny, nx))).astype(np.float32)
+    Tr, _ = oracle.solve(ln, D.astype(np.float64), T0=T0, n_iter=1, omega=0.4)
+    Tg, _ = _gpu_solve(torch, E, nx, ny, p, L, Es, d, b, w, D, 1, 0.4,
+                       T0=T0.astype(np.float32), deterministic=deterministic)
+    assert np.all(np.isfinite(Tg))
+    assert rel(Tg, Tr) < 1e-4
+    blk = (slice(40, 80), slice(50, 110))
+    assert rel(Tg[blk], Tr[blk]) < 1e-4

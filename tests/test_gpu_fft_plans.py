@@ -45,8 +45,11 @@ def test_radix16_preconditioner_vs_oracle(torch, oracle, n_lines):
                 assert rel(out[bb], oracle.precondition(ln, g0[bb].astype(np.float64), line=s)) < 1e-5
 
 
-@pytest.mark.parametrize("n_lines,radix", [(1, 16), (2, 16), (1, 8)])
-def test_solve_with_radix_plan_vs_oracle(torch, oracle, n_lines, radix):
+@pytest.mark.parametrize("n_lines,radix,col_blocks", [(1, 16, 4), (2, 16, 4), (1, 8, 4),
+                                                     (1, 16, 5), (2, 16, 5)])
+def test_solve_with_radix_plan_vs_oracle(torch, oracle, n_lines, radix, col_blocks):
+    """col_blocks = 5: the radix-16 column pass bounded to five blocks per SM
+    (set through epr_plan_set_tuning)."""
     from paper_2601_22793_gb300 import epr as E
     ny, nx = 2048, 512
     Es, d, b, w = ph.spectrum(n_lines, 60.0, 140.0, 90.0, 30.0, ph.BONE[0], ph.BONE[1], 80.0, 5)
@@ -57,10 +60,47 @@ def test_solve_with_radix_plan_vs_oracle(torch, oracle, n_lines, radix):
     D = ph.poisson(oracle.forward(ln, tau), 1e4, 22).astype(np.float32)
     Tr, ir = oracle.solve(ln, D.astype(np.float64), n_iter=5, omega=0.4)
     with E.Plan(nx, ny, wl.pixel, wl.L, Es, d, b, w, fft_radix=radix) as plan:
+        assert E.epr_plan_get_tuning(plan.handle)["col_radix"] == radix
+        if col_blocks != 4:
+            tun = dict(E.epr_plan_get_tuning(plan.handle), col_radix=radix,
+                       col_blocks_per_sm=col_blocks)
+            E.epr_plan_set_tuning(plan.handle, tun)
+            assert E.epr_plan_get_tuning(plan.handle)["col_blocks_per_sm"] == col_blocks
         Dd = torch.from_numpy(D).cuda()
         T = torch.empty_like(Dd)
         info = E.epr_solve_nonlocal(plan.handle, Dd, T, n_iter=5, omega=0.4)
         Tg = T.cpu().numpy()
+    assert rel(Tg, Tr) < 1e-4
+    assert np.allclose(info["rho_hist"][0], ir["rho"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("tile,reach", [((32, 64), 3), ((64, 32), 4), ((32, 32), 3)])
+def test_occupancy_variants_vs_oracle(torch, oracle, tile, reach):
+    """The six-blocks-per-SM residual splat, the five-blocks-per-SM radix-16
+    column pass and the six-blocks-per-SM row passes, set through
+    epr_plan_set_tuning, on a one-line 512 x 2048 solve (5 iterations)."""
+    from paper_2601_22793_gb300 import epr as E
+    ny, nx = 2048, 512
+    wl = ph.Workload("crop", ny, nx, 20e-6, 30.0, [80.0], [ph.BONE[0]], [ph.BONE[1]], [1.0], 5,
+                     0.4, 1e4)
+    ells = ph.random_ellipsoids(ny, nx, 30, 6.0, 60.0, seed=23)
+    tau = ph.project_ellipsoids(ells, ny, nx, wl.pixel)
+    ln = oracle.Lines(wl.energy_keV, wl.delta, wl.beta, wl.weights, L=wl.L, pixel=wl.pixel)
+    D = ph.poisson(oracle.forward(ln, tau), 1e4, 24).astype(np.float32)
+    Tr, ir = oracle.solve(ln, D.astype(np.float64), n_iter=5, omega=0.4)
+    with E.Plan(nx, ny, wl.pixel, wl.L, wl.energy_keV, wl.delta, wl.beta, wl.weights) as plan:
+        tun = dict(E.epr_plan_get_tuning(plan.handle), splat_tile=list(tile), splat_reach=reach,
+                   splat_blocks_per_sm=6, col_tile_width=0, col_radix=16, col_blocks_per_sm=5,
+                   row_blocks_per_sm=6)
+        E.epr_plan_set_tuning(plan.handle, tun)
+        got = E.epr_plan_get_tuning(plan.handle)
+        assert got == dict(tun, tuned=True)
+        Dd = torch.from_numpy(D).cuda()
+        T = torch.empty_like(Dd)
+        info = E.epr_solve_nonlocal(plan.handle, Dd, T, n_iter=5, omega=0.4)
+        Tg = T.cpu().numpy()
+        with pytest.raises(E.EprError):   # no six-block variant of the 64 x 64 tile
+            E.epr_plan_set_tuning(plan.handle, dict(tun, splat_tile=[64, 64]))
     assert rel(Tg, Tr) < 1e-4
     assert np.allclose(info["rho_hist"][0], ir["rho"], rtol=1e-3)
 
@@ -87,6 +127,29 @@ def test_autotuned_plan_solves_like_the_default(torch, oracle):
     assert rel(outs[True], Tr) < 1e-4
 
 
+def test_autotuned_polychromatic_plan_vs_oracle(torch, oracle):
+    """A three-line plan with the tuner on (splat tiles, reach and the column
+    plans, timed on the split residuals of its first solve): its later solves
+    match the oracle."""
+    from paper_2601_22793_gb300 import epr as E
+    ny, nx = 2048, 512
+    Es, d, b, w = ph.spectrum(3, 60.0, 140.0, 90.0, 30.0, ph.BONE[0], ph.BONE[1], 80.0, 7)
+    ells = ph.random_ellipsoids(ny, nx, 30, 6.0, 60.0, seed=25)
+    tau = ph.project_ellipsoids(ells, ny, nx, 20e-6)
+    ln = oracle.Lines(Es, d, b, w, L=30.0, pixel=20e-6)
+    D = ph.poisson(oracle.forward(ln, tau), 1e4, 26).astype(np.float32)
+    Tr, ir = oracle.solve(ln, D.astype(np.float64), n_iter=5, omega=0.4)
+    with E.Plan(nx, ny, 20e-6, 30.0, Es, d, b, w, autotune=True) as plan:
+        Dd = torch.from_numpy(D).cuda()
+        for _ in range(2):   # the first solve runs the tuner
+            T = torch.empty_like(Dd)
+            info = E.epr_solve_nonlocal(plan.handle, Dd, T, n_iter=5, omega=0.4)
+        assert E.epr_plan_get_tuning(plan.handle)["tuned"]
+        Tg = T.cpu().numpy()
+    assert rel(Tg, Tr) < 1e-4
+    assert np.allclose(info["rho_hist"][0], ir["rho"], rtol=1e-3)
+
+
 def test_tuning_carries_over_between_plans(torch, oracle):
     """epr_plan_get_tuning / epr_plan_set_tuning: a second plan given the
     first plan's tuned choices solves as the tuned plan does; invalid choices
@@ -110,6 +173,7 @@ def test_tuning_carries_over_between_plans(torch, oracle):
         T2 = torch.empty_like(Dd)
         E.epr_solve_nonlocal(b.handle, Dd, T2, n_iter=4, omega=0.4)
         assert rel(T2.cpu().numpy(), Ta) < 1e-6
-        bad = dict(tun, col_radix=12)
-        with pytest.raises(E.EprError):
-            E.epr_plan_set_tuning(b.handle, bad)
+        for bad in (dict(tun, col_radix=12), dict(tun, col_radix=8, col_blocks_per_sm=5),
+                    dict(tun, col_blocks_per_sm=6)):
+            with pytest.raises(E.EprError):
+                E.epr_plan_set_tuning(b.handle, bad)
