@@ -210,9 +210,9 @@ k_col_ct(const EprConsts C, const ColArgs A)
 // accelerator: BOXES bulk loads of [NY / BOXES][CW] into a dense tile at the
 // start of the FFT buffer (no L1 traffic, one elected thread).  The first
 // FFT stage reads every operand from the dense tile before its barrier and
-// writes the padded layout over it; at the end the result is read out of the
-// padded layout, and after a barrier written back dense and stored in bulk.
-// So the block needs only the padded buffer.  The tile's row pitch is
+// writes the padded layout over it; the last stage reads the padded layout
+// and writes its results dense over it, which the bulk store reads.  So the
+// block needs only the padded buffer.  The tile's row pitch is
 // CW * 8 bytes, which keeps the strided 16-byte row segments of the column
 // off the load/store unit.
 constexpr unsigned int kTmaWaitPolls = 1u << 22;
@@ -267,20 +267,12 @@ k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMa
         eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1, MAXR>(buf, buf, A.tw, tid);
         col_filter0<NY, CW, LGCW, T>(buf, C, s, tid);
     }
-    eprfft::fft_ct<PC, +1, NY, EPT, LGCW, CW, 1, 0, MAXR>(buf, A.tw, tid);
+    constexpr int NST = eprfft::ct_n_stages(NY, MAXR);
+    eprfft::fft_ct_stages<PC, +1, NY, EPT, LGCW, CW, 1, 0, NST - 1, MAXR>(buf, A.tw, tid);
     epr_grid_release();
-    // back to the dense layout in place, in two halves of the elements: the
-    // dense slot e holds the padded element e' <= e, so writing the first
-    // half destroys only first-half padded elements, already read
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float2 o[EPT / 2];
-#pragma unroll
-        for (int k = 0; k < EPT / 2; ++k) o[k] = buf[PC::idx(tid + (h * EPT / 2 + k) * T)];
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < EPT / 2; ++k) buf[tid + (h * EPT / 2 + k) * T] = o[k];
-    }
+    // the last stage writes the dense tile the bulk store reads, in place:
+    // every operand is read before the stage's barrier
+    eprfft::fft_ct_last<eprfft::Dense, true, false, PC, +1, NY, EPT, LGCW, CW, 1, MAXR>(buf, A.tw, tid);
     epr_tma::fence_async_shared();
     __syncthreads();
     if (tid == 0) {

@@ -311,9 +311,11 @@ struct Identity {
 
 // Reads its operands from `in` (layout PADI) and writes post(result) to
 // `buf` (layout PAD).  Every operand is read before the stage's first
-// barrier, so in == buf works even when PADI != PAD.
+// barrier, so in == buf works even when PADI != PAD.  STORE = false hands
+// each result to post only (post(value, e) for its side effects, nothing is
+// written); SYNC_END = false leaves out the closing barrier.
 template <class PADI, class PAD, int R, int DIR, int EPT, int N, int NS, int LGSEQ, int SJ, int SM,
-          class POST = Identity>
+          class POST = Identity, bool STORE = true, bool SYNC_END = true>
 __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const float2* __restrict__ tw,
                                          int tid, const POST& post = POST())
 {
@@ -376,7 +378,10 @@ __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const fl
     for (int k = 0; k < PER; ++k) {
         if (NB % T == 0 || dst[k] >= 0) {
             dft<R, DIR>(v[k]);
-            if constexpr ((NS * SJ) % PAD::kPeriod == 0) {
+            if constexpr (!STORE) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) post(v[k][r], dst[k] + r * NS * SJ);
+            } else if constexpr ((NS * SJ) % PAD::kPeriod == 0) {
                 const int o0 = PAD::idx(dst[k]);
 #pragma unroll
                 for (int r = 0; r < R; ++r)
@@ -388,6 +393,48 @@ __device__ __forceinline__ void stage_ct(const float2* in, float2* buf, const fl
             }
         }
     }
+    if constexpr (SYNC_END) __syncthreads();
+}
+
+// Stages S .. SEND - 1 of the transform, no output map.
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int S, int SEND, int MAXR = 8>
+__device__ __forceinline__ void fft_ct_stages(float2* buf, const float2* __restrict__ tw, int tid)
+{
+    if constexpr (S < SEND) {
+        stage_ct<PAD, PAD, ct_radix(N, S, MAXR), DIR, EPT, N, ct_ns(N, S, MAXR), LGSEQ, SJ, SM>(buf, buf,
+                                                                                              tw, tid);
+        fft_ct_stages<PAD, DIR, N, EPT, LGSEQ, SJ, SM, S + 1, SEND, MAXR>(buf, tw, tid);
+    }
+}
+
+// The last stage alone, its input in layout PAD: the results go to buf in
+// layout PADO (in place), or with STORE = false to post only.  Follows
+// fft_ct_stages<..., 0, ct_n_stages(N, MAXR) - 1>.
+template <class PADO, bool STORE, bool SYNC_END, class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ,
+          int SM, int MAXR = 8, class POST = Identity>
+__device__ __forceinline__ void fft_ct_last(float2* buf, const float2* __restrict__ tw, int tid,
+                                            const POST& post = POST())
+{
+    constexpr int S = ct_n_stages(N, MAXR) - 1;
+    stage_ct<PAD, PADO, ct_radix(N, S, MAXR), DIR, EPT, N, ct_ns(N, S, MAXR), LGSEQ, SJ, SM, POST, STORE,
+             SYNC_END>(buf, buf, tw, tid, post);
+}
+
+// The first stage with its operands in registers: for one sequence (nseq =
+// 1) with EPT equal to the first radix R, thread tid's operands are elements
+// tid + r N / R, r < R, and the stage has no twiddles.  Writes its results to
+// buf (layout PAD) and synchronises; the caller has synchronised already if
+// buf aliases data that other threads still read.  Stages 1.. follow as
+// fft_ct<..., 1>.
+template <class PAD, int DIR, int N, int EPT, int SJ>
+__device__ __forceinline__ void stage0_regs(float2 (&v)[EPT], float2* buf, int tid)
+{
+    constexpr int R = ct_radix(N, 0);
+    static_assert(R == EPT && ct_n_stages(N) > 1, "operands of the first stage in registers");
+    dft<R, DIR>(v);
+    const int dst = tid * R * SJ;   // (j / Ns) Ns R + (j mod Ns) with Ns = 1, j = tid
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[PAD::idx(dst + r * SJ)] = v[r];
     __syncthreads();
 }
 

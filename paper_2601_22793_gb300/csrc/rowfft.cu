@@ -551,14 +551,20 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
         vk[k] = make_float2(v[0], v[1]);
     }
     if constexpr (GATHER) __syncthreads();   // every thickness read is done
+    if constexpr (RP == 1 && eprfft::ct_radix(NX, 0) == kEPT) {
+        // one row pair: vk[k] = element tid + k T, the first stage's operands
+        eprfft::stage0_regs<PR, -1, NX, kEPT, 1>(vk, zs, tid);
+        eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM, 1>(zs, A.tw, tid);
+    } else {
 #pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        const int e = tid + k * T;
-        const int m = row_of<NX, RP>(e), x = e - m * NX;
-        zs[PR::idx(m * SM + x)] = vk[k];
+        for (int k = 0; k < kEPT; ++k) {
+            const int e = tid + k * T;
+            const int m = row_of<NX, RP>(e), x = e - m * NX;
+            zs[PR::idx(m * SM + x)] = vk[k];
+        }
+        __syncthreads();
+        eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
     }
-    __syncthreads();
-    eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
     epr_grid_release();
     float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * HALF;
 #pragma unroll 2
@@ -586,6 +592,41 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     block_sum2(ra, rb, red);   // |D - P|^2 partials; rho is formed by the column pass
     store_partials(A.part_c + (size_t)b * A.max_blocks, nullptr, ra, rb);
 }
+
+// The update of one result of the last inverse stage of a one-line block:
+// element e = m SM + x holds rows 2m and 2m + 1 of the block at column x;
+// T' = T - w ln(I'/I) from the staged thickness rows, stored, with the kappa
+// partial sums kept in the functor (its call sites are inlined, so they stay
+// in registers).
+template <int NX, int SM, int RP, bool XT>
+struct InvUpdate1 {
+    const EprConsts& C;
+    const float* Tsh;      // [2 RP][NX] thickness rows of the block
+    float* out;            // T at the block's first row
+    float mus, w, om_f, omega, eps;
+    mutable float da, db;
+    __device__ __forceinline__ float2 operator()(float2 h, int e) const
+    {
+        const int m = RP == 1 ? 0 : e / SM;
+        const int x = e - m * SM;
+        const float t0 = Tsh[(2 * m) * NX + x], t1 = Tsh[(2 * m + 1) * NX + x];
+        float wx = w, omx = om_f, mux = mus;
+        if constexpr (XT) {
+            wx = xt_get(C, EPR_XT_WPROJ, 0, x);
+            mux = xt_get(C, EPR_XT_MU, 0, x);
+            omx = omega / xt_get(C, EPR_XT_F, 0, x);
+        }
+        const float l0 = wx * log_ratio(t0, h.x, omx, mux, eps);
+        const float l1 = wx * log_ratio(t1, h.y, omx, mux, eps);
+        const float n0 = t0 - l0, n1 = t1 - l1;
+        float* o = out + (size_t)(2 * m) * NX + x;
+        o[0] = n0;
+        o[NX] = n1;
+        da += l0 * l0 + l1 * l1;
+        db += n0 * n0 + n1 * n1;
+        return h;
+    }
+};
 
 // five 256-thread blocks per SM (48 registers): its shared memory is the FFT
 // rows and 2 RP thickness rows only (row_inv_mono_smem)
@@ -638,33 +679,15 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
         }
     }
     __syncthreads();
-    eprfft::fft_ct<PR, +1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
+    constexpr int NST = eprfft::ct_n_stages(NX);
+    eprfft::fft_ct_stages<PR, +1, NX, kEPT, LGRP, 1, SM, 0, NST - 1>(zs, A.tw, tid);
     epr_grid_release();
-    cp_async_wait_all();
-    __syncthreads();
-    const float mus = C.mu[0], w = C.wproj[0], om_f = A.omega / C.f[0];
-    float da = 0.f, db = 0.f;
-#pragma unroll 2
-    for (int k = 0; k < kEPT; ++k) {
-        const int e = tid + k * T;
-        const int m = row_of<NX, RP>(e), x = e - m * NX;
-        const float2 h = zs[PR::idx(m * SM + x)];
-        const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
-        const float t0 = Tsh[(2 * m) * NX + x], t1 = Tsh[(2 * m + 1) * NX + x];
-        float wx = w, omx = om_f, mux = mus;
-        if constexpr (XT) {
-            wx = xt_get(C, EPR_XT_WPROJ, 0, x);
-            mux = xt_get(C, EPR_XT_MU, 0, x);
-            omx = A.omega / xt_get(C, EPR_XT_F, 0, x);
-        }
-        const float l0 = wx * log_ratio(t0, h.x, omx, mux, A.eps);
-        const float l1 = wx * log_ratio(t1, h.y, omx, mux, A.eps);
-        const float n0 = t0 - l0, n1 = t1 - l1;
-        A.Out[q0] = n0;
-        A.Out[q0 + NX] = n1;
-        da += l0 * l0 + l1 * l1;
-        db += n0 * n0 + n1 * n1;
-    }
+    cp_async_wait_all();   // the thickness rows: visible to all after the last stage's barrier
+    // the last stage hands each result to the update (no store, no barrier)
+    const InvUpdate1<NX, SM, RP, XT> up{C, Tsh, A.Out + pb + (size_t)yb * NX, C.mu[0], C.wproj[0],
+                                        A.omega / C.f[0], A.omega, A.eps, 0.f, 0.f};
+    eprfft::fft_ct_last<PR, false, false, PR, +1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid, up);
+    float da = up.da, db = up.db;
     block_sum2(da, db, red);   // kappa partials, finalised by the next forward pass
     store_partials(A.part_a + (size_t)b * A.max_blocks, A.part_b + (size_t)b * A.max_blocks, da, db);
 }
