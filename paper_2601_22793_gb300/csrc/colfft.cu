@@ -260,19 +260,23 @@ k_col_tma(const EprConsts C, const ColArgs A, const __grid_constant__ CUtensorMa
         return;
     }
     const int s = A.line0 + sl;
-    if (kx0 != 0) {   // the filter as the output map of the forward transform
+    constexpr int NST = eprfft::ct_n_stages(NY, MAXR);
+    // the inverse runs the reversed stage plan, whose first stage takes the
+    // last forward stage's results as they are
+    if (kx0 != 0) {   // last forward stage, filter, first inverse stage in registers
         const ColPaganin<NY, CW, LGCW> f{line_const(C.ha, s), line_const(C.hb, s), C.inv_n, kx0};
-        eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1, MAXR>(buf, buf, A.tw, tid, f);
-    } else {
+        eprfft::fft_ct_from_stages<PC, -1, NY, EPT, LGCW, CW, 1, NST - 1, MAXR>(buf, buf, A.tw, tid);
+        eprfft::stage_turn<PC, -1, +1, EPT, NY, LGCW, CW, 1, MAXR>(buf, A.tw, tid, f);
+        eprfft::fft_ct_rev_stages<PC, +1, NY, EPT, LGCW, CW, 1, 1, NST - 1, MAXR>(buf, A.tw, tid);
+    } else {   // the packed DC / Nyquist column filters mirrored pairs in place
         eprfft::fft_ct_from<PC, -1, NY, EPT, LGCW, CW, 1, MAXR>(buf, buf, A.tw, tid);
         col_filter0<NY, CW, LGCW, T>(buf, C, s, tid);
+        eprfft::fft_ct_rev_stages<PC, +1, NY, EPT, LGCW, CW, 1, 0, NST - 1, MAXR>(buf, A.tw, tid);
     }
-    constexpr int NST = eprfft::ct_n_stages(NY, MAXR);
-    eprfft::fft_ct_stages<PC, +1, NY, EPT, LGCW, CW, 1, 0, NST - 1, MAXR>(buf, A.tw, tid);
     epr_grid_release();
     // the last stage writes the dense tile the bulk store reads, in place:
     // every operand is read before the stage's barrier
-    eprfft::fft_ct_last<eprfft::Dense, true, false, PC, +1, NY, EPT, LGCW, CW, 1, MAXR>(buf, A.tw, tid);
+    eprfft::fft_ct_rev_last<eprfft::Dense, true, false, PC, +1, NY, EPT, LGCW, CW, 1, MAXR>(buf, A.tw, tid);
     epr_tma::fence_async_shared();
     __syncthreads();
     if (tid == 0) {

@@ -303,6 +303,19 @@ __host__ __device__ constexpr int ct_ns(int n, int s, int maxr = 8)
     return v;
 }
 
+// The reversed plan: the same radices in the opposite order (a Stockham
+// transform is valid for any order of the factors).
+__host__ __device__ constexpr int ct_radix_rev(int n, int s, int maxr = 8)
+{
+    return ct_radix(n, ct_n_stages(n, maxr) - 1 - s, maxr);
+}
+__host__ __device__ constexpr int ct_ns_rev(int n, int s, int maxr = 8)
+{
+    int v = 1;
+    for (int i = 0; i < s; ++i) v *= ct_radix_rev(n, i, maxr);
+    return v;
+}
+
 // Output map of a stage: out = post(value, e) with e = j * SJ + m * SM the
 // element's unpadded index; Identity leaves the value.
 struct Identity {
@@ -418,6 +431,117 @@ __device__ __forceinline__ void fft_ct_last(float2* buf, const float2* __restric
     constexpr int S = ct_n_stages(N, MAXR) - 1;
     stage_ct<PAD, PADO, ct_radix(N, S, MAXR), DIR, EPT, N, ct_ns(N, S, MAXR), LGSEQ, SJ, SM, POST, STORE,
              SYNC_END>(buf, buf, tw, tid, post);
+}
+
+// Stages S .. SEND - 1 of the reversed plan, no output map.
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int S, int SEND, int MAXR = 8>
+__device__ __forceinline__ void fft_ct_rev_stages(float2* buf, const float2* __restrict__ tw, int tid)
+{
+    if constexpr (S < SEND) {
+        stage_ct<PAD, PAD, ct_radix_rev(N, S, MAXR), DIR, EPT, N, ct_ns_rev(N, S, MAXR), LGSEQ, SJ, SM>(
+            buf, buf, tw, tid);
+        fft_ct_rev_stages<PAD, DIR, N, EPT, LGSEQ, SJ, SM, S + 1, SEND, MAXR>(buf, tw, tid);
+    }
+}
+
+// The last stage of the reversed plan (input layout PAD, output PADO in
+// place, or post only with STORE = false).
+template <class PADO, bool STORE, bool SYNC_END, class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ,
+          int SM, int MAXR = 8, class POST = Identity>
+__device__ __forceinline__ void fft_ct_rev_last(float2* buf, const float2* __restrict__ tw, int tid,
+                                                const POST& post = POST())
+{
+    constexpr int S = ct_n_stages(N, MAXR) - 1;
+    stage_ct<PAD, PADO, ct_radix_rev(N, S, MAXR), DIR, EPT, N, ct_ns_rev(N, S, MAXR), LGSEQ, SJ, SM, POST,
+             STORE, SYNC_END>(buf, buf, tw, tid, post);
+}
+
+// Stages 0 .. SEND - 1 of the transform with its input in a dense tile `in`
+// (which may be buf itself), no output map.
+template <class PAD, int DIR, int N, int EPT, int LGSEQ, int SJ, int SM, int SEND, int MAXR = 8>
+__device__ __forceinline__ void fft_ct_from_stages(const float2* in, float2* buf,
+                                                   const float2* __restrict__ tw, int tid)
+{
+    static_assert(SEND >= 1, "at least the first stage");
+    stage_ct<Dense, PAD, ct_radix(N, 0, MAXR), DIR, EPT, N, 1, LGSEQ, SJ, SM>(in, buf, tw, tid);
+    fft_ct_stages<PAD, DIR, N, EPT, LGSEQ, SJ, SM, 1, SEND, MAXR>(buf, tw, tid);
+}
+
+// The turn between a forward transform and the inverse of its pointwise
+// image: the last stage of the forward plan (direction DIRF), the output map
+// post, and the first stage of the reversed plan in direction DIRI, in
+// registers.  The last forward stage (radix R, Ns = N / R) leaves butterfly b
+// with elements j + r N / R of its sequence, which are the operands of the
+// reversed plan's first stage (radix R, Ns = 1, no twiddles) for the same
+// butterfly, in the same order.  Reads its operands before its first barrier
+// (in place), writes the inverse stage's results to buf and synchronises.
+template <class PAD, int DIRF, int DIRI, int EPT, int N, int LGSEQ, int SJ, int SM, int MAXR = 8,
+          class POST = Identity>
+__device__ __forceinline__ void stage_turn(float2* buf, const float2* __restrict__ tw, int tid,
+                                           const POST& post = POST())
+{
+    constexpr int SL = ct_n_stages(N, MAXR) - 1;
+    constexpr int R = ct_radix(N, SL, MAXR);
+    constexpr int NS = ct_ns(N, SL, MAXR);
+    static_assert(NS * R == N && ct_radix_rev(N, 0, MAXR) == R, "the turn's two stages");
+    constexpr int NSEQ = 1 << LGSEQ;
+    constexpr int T = (N * NSEQ) / EPT;
+    constexpr int PER = (EPT + R - 1) / R;
+    constexpr int NR = N / R;
+    constexpr int NB = NR * NSEQ;
+    constexpr int TWSTEP = N / (NS * R);
+    float2 v[PER][R];
+    int j_of[PER], m_of[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int b = tid + k * T;
+        j_of[k] = -1;
+        if (NB % T == 0 || b < NB) {
+            const int m = b & (NSEQ - 1);
+            const int j = b >> LGSEQ;   // j < NR = NS: j mod NS = j
+            const int base = m * SM;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[k][r] = buf[PAD::idx((j + r * NR) * SJ + base)];
+            if constexpr (NS > 1) {
+                float2 w = __ldg(&tw[j * TWSTEP]);
+                if (DIRF > 0) w.y = -w.y;
+                const float c2 = w.x + w.x;
+                constexpr int RREC = R > 8 ? 8 : R;
+                float2 wpow[RREC];
+                wpow[0] = make_float2(1.f, 0.f);
+                if constexpr (RREC > 1) wpow[1] = w;
+#pragma unroll
+                for (int r = 2; r < RREC; ++r)
+                    wpow[r] = make_float2(fmaf(c2, wpow[r - 1].x, -wpow[r - 2].x),
+                                          fmaf(c2, wpow[r - 1].y, -wpow[r - 2].y));
+#pragma unroll
+                for (int r = 1; r < RREC; ++r) v[k][r] = cmul(v[k][r], wpow[r]);
+                if constexpr (R > 8) {
+                    const float2 w8 = cmul(wpow[4], wpow[4]);
+                    v[k][8] = cmul(v[k][8], w8);
+#pragma unroll
+                    for (int r = 9; r < R; ++r) v[k][r] = cmul(v[k][r], cmul(w8, wpow[r - 8]));
+                }
+            }
+            j_of[k] = j;
+            m_of[k] = m;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (NB % T == 0 || j_of[k] >= 0) {
+            const int j = j_of[k], base = m_of[k] * SM;
+            dft<R, DIRF>(v[k]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[k][r] = post(v[k][r], (j + r * NS) * SJ + base);
+            dft<R, DIRI>(v[k]);
+            // the reversed plan's first stage writes element j R + r
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[PAD::idx((j * R + r) * SJ + base)] = v[k][r];
+        }
+    }
+    __syncthreads();
 }
 
 // The first stage with its operands in registers: for one sequence (nseq =

@@ -692,6 +692,55 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
     store_partials(A.part_a + (size_t)b * A.max_blocks, A.part_b + (size_t)b * A.max_blocks, da, db);
 }
 
+// The per-line step of the polychromatic update, applied to each result of
+// a line's last inverse stage (element e = m SM + x: rows 2m, 2m + 1 at
+// column x): w_s ln(I'_s / I_s) added to the pixel's sum in shared memory
+// (the element-to-thread map of the last stage is the same for every line,
+// so each thread reads and writes its own pixels only); on the last line
+// T' = T - sum is stored instead, with the kappa partial sums.
+template <int NX, int SM, int RP, bool XT>
+struct InvUpdatePoly {
+    const EprConsts& C;
+    const float* Tsh;      // [2 RP][NX] thickness rows of the block
+    float* acc;            // [2 RP][NX] sums over the lines so far
+    float* out;            // T at the block's first row
+    int s;                 // line of this pass
+    bool first, last;
+    float mus, w, om_f, omega, eps;
+    mutable float da, db;
+    __device__ __forceinline__ float2 operator()(float2 h, int e) const
+    {
+        const int m = RP == 1 ? 0 : e / SM;
+        const int x = e - m * SM;
+        const int i0 = (2 * m) * NX + x;
+        float wx = w, omx = om_f, mux = mus;
+        if constexpr (XT) {
+            wx = xt_get(C, EPR_XT_WPROJ, s, x);
+            mux = xt_get(C, EPR_XT_MU, s, x);
+            omx = omega / xt_get(C, EPR_XT_F, s, x);
+        }
+        const float t0 = Tsh[i0], t1 = Tsh[i0 + NX];
+        float l0 = wx * log_ratio(t0, h.x, omx, mux, eps);
+        float l1 = wx * log_ratio(t1, h.y, omx, mux, eps);
+        if (!first) {
+            l0 = acc[i0] + l0;
+            l1 = acc[i0 + NX] + l1;
+        }
+        if (last) {
+            const float n0 = t0 - l0, n1 = t1 - l1;
+            float* o = out + (size_t)(2 * m) * NX + x;
+            o[0] = n0;
+            o[NX] = n1;
+            da += l0 * l0 + l1 * l1;
+            db += n0 * n0 + n1 * n1;
+        } else {
+            acc[i0] = l0;
+            acc[i0 + NX] = l1;
+        }
+        return h;
+    }
+};
+
 // Polychromatic update on the compile-time engine: for each line, the C2R
 // rows of its filtered spectrum and w_s ln(I'_s / I_s), accumulated per
 // pixel in shared memory (each thread owns its pixels); then T' = T - sum
@@ -727,6 +776,8 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
         cp_async_wait_all();
         return;
     }
+    InvUpdatePoly<NX, SM, RP, XT> up{C, Tsh, acc, A.Out + pb + (size_t)yb * NX, 0, true, false,
+                                     0.f, 0.f, 0.f, A.omega, A.eps, 0.f, 0.f};
     for (int sl = 0; sl < A.nl; ++sl) {
         const int s = A.line0 + sl;
         const float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * HALF;
@@ -747,47 +798,23 @@ k_row_inv_poly(const EprConsts C, const RowArgs A)
             }
         }
         __syncthreads();
-        eprfft::fft_ct<PR, +1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
+        constexpr int NST = eprfft::ct_n_stages(NX);
+        eprfft::fft_ct_stages<PR, +1, NX, kEPT, LGRP, 1, SM, 0, NST - 1>(zs, A.tw, tid);
         if (sl == 0) {
             epr_grid_release();
-            cp_async_wait_all();
-            __syncthreads();
+            cp_async_wait_all();   // the thickness rows: visible after the last stage's barrier
         }
-        const float mus = line_const(C.mu, s), w = line_const(C.wproj, s);
-        const float om_f = A.omega / line_const(C.f, s);
-#pragma unroll 2
-        for (int k = 0; k < kEPT; ++k) {
-            const int e = tid + k * T;
-            const int m = row_of<NX, RP>(e), x = e - m * NX;
-            const float2 h = zs[PR::idx(m * SM + x)];
-            const int i0 = (2 * m) * NX + x;
-            float wx = w, omx = om_f, mux = mus;
-            if constexpr (XT) {
-                wx = xt_get(C, EPR_XT_WPROJ, s, x);
-                mux = xt_get(C, EPR_XT_MU, s, x);
-                omx = A.omega / xt_get(C, EPR_XT_F, s, x);
-            }
-            const float l0 = wx * log_ratio(Tsh[i0], h.x, omx, mux, A.eps);
-            const float l1 = wx * log_ratio(Tsh[i0 + NX], h.y, omx, mux, A.eps);
-            acc[i0] = sl == 0 ? l0 : acc[i0] + l0;
-            acc[i0 + NX] = sl == 0 ? l1 : acc[i0 + NX] + l1;
-        }
-        __syncthreads();   // the next line's unpack overwrites zs
+        // the last stage adds the line's term to each thread's own pixels;
+        // after its barrier nothing reads zs, so the next unpack may follow
+        up.s = s;
+        up.first = sl == 0;
+        up.last = sl == A.nl - 1;
+        up.mus = line_const(C.mu, s);
+        up.w = line_const(C.wproj, s);
+        up.om_f = A.omega / line_const(C.f, s);
+        eprfft::fft_ct_last<PR, false, false, PR, +1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid, up);
     }
-    float da = 0.f, db = 0.f;
-#pragma unroll 2
-    for (int k = 0; k < kEPT; ++k) {
-        const int e = tid + k * T;
-        const int m = row_of<NX, RP>(e), x = e - m * NX;
-        const int i0 = (2 * m) * NX + x;
-        const size_t q0 = pb + (size_t)(yb + 2 * m) * NX + x;
-        const float l0 = acc[i0], l1 = acc[i0 + NX];
-        const float n0 = Tsh[i0] - l0, n1 = Tsh[i0 + NX] - l1;
-        A.Out[q0] = n0;
-        A.Out[q0 + NX] = n1;
-        da += l0 * l0 + l1 * l1;
-        db += n0 * n0 + n1 * n1;
-    }
+    float da = up.da, db = up.db;
     block_sum2(da, db, red);   // kappa partials, finalised by the next forward pass
     store_partials(A.part_a + (size_t)b * A.max_blocks, A.part_b + (size_t)b * A.max_blocks, da, db);
 }
