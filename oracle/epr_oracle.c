@@ -574,6 +574,57 @@ int orc_forward(int ny, int nx, double p, double L, int n_lines,
     return st;
 }
 
+/* Non-local forward of an object whose phase and attenuation are not one
+ * thickness (several materials, the data side of a single-material
+ * retrieval): per line s the phase line integral Phi_s = sum_m delta_{m,s} t_m
+ * and the attenuation line integral A_s = sum_m mu_{m,s} t_m (maps
+ * [n_lines][ny][nx], t_m the chord through material m).  The object intensity
+ * is I_s = f_s exp(-A_s) and the phase phi_s = -k_s Phi_s (Eq. 6 before the
+ * single-material substitution of Eq. 7), so the shift in pixels is
+ * u_s = -(L / p^2) G[Phi_s] (Eq. 2, reading R2 without tau), and
+ * P = sum_s M_s[I_s] (Eqs. 3 and 5).  f_s = weights normalised to sum 1.
+ * With one material (Phi_s = delta_s tau, A_s = mu_s tau) this is the
+ * non-local orc_forward. */
+int orc_forward_fields(int ny, int nx, double p, double L, int n_lines, const double* weights,
+                       const double* Phi, const double* A, double* P, double* Ps,
+                       double* dropped)
+{
+    if (ny < 2 || nx < 2 || n_lines < 1 || L < 0.0 || !(p > 0.0)) return ORC_EINVAL;
+    double wsum = 0.0;
+    for (int s = 0; s < n_lines; ++s) {
+        if (weights[s] < 0.0) return ORC_EINVAL;
+        wsum += weights[s];
+    }
+    if (!(wsum > 0.0)) return ORC_EINVAL;
+    size_t n = (size_t)nx * (size_t)ny;
+    double *gy = alloc_n(n), *gx = alloc_n(n), *uy = alloc_n(n), *ux = alloc_n(n),
+           *I = alloc_n(n), *Pl = alloc_n(n);
+    int st = (!gy || !gx || !uy || !ux || !I || !Pl) ? ORC_ENOMEM : ORC_OK;
+    if (st == ORC_OK) {
+        const double c = -L / (p * p);
+        for (size_t i = 0; i < n; ++i) P[i] = 0.0;
+        for (int s = 0; s < n_lines; ++s) {
+            const double* ph = Phi + (size_t)s * n;
+            const double* at = A + (size_t)s * n;
+            const double fs = weights[s] / wsum;
+            orc_gradient(ny, nx, ph, gy, gx);
+            for (size_t i = 0; i < n; ++i) {
+                uy[i] = c * gy[i];
+                ux[i] = c * gx[i];
+                I[i] = fs * exp(-at[i]);
+                Pl[i] = 0.0;
+            }
+            double lost = 0.0;
+            orc_splat(ny, nx, I, uy, ux, Pl, &lost);
+            for (size_t i = 0; i < n; ++i) P[i] += Pl[i];
+            if (Ps) memcpy(Ps + (size_t)s * n, Pl, sizeof(double) * n);
+            if (dropped) dropped[s] = lost;
+        }
+    }
+    free(gy); free(gx); free(uy); free(ux); free(I); free(Pl);
+    return st;
+}
+
 /* Adjoint of the non-local forward for one line and fixed tau: the gather of
  * the detector map e at the line's mapped coordinates (Eq. 4). */
 int orc_adjoint(int ny, int nx, double p, double L, int n_lines,

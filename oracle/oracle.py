@@ -79,6 +79,7 @@ def _load():
             lib.orc_xspec_params.argtypes = [i, i, d, i, d, d, d, d, f, f, d, d, d, d, d]
             lib.orc_forward_x.argtypes = [i, i, i, d, d, d, d, d, d, d]
             lib.orc_solve_x.argtypes = [i, i, f, i, d, d, d, d, d, d, d, i, f, f, f, d, d, ip]
+            lib.orc_forward_fields.argtypes = [i, i, f, f, i, d, d, d, d, d, d]
             _lib = lib
     return _lib
 
@@ -314,6 +315,40 @@ class XSpec:
     @property
     def n(self):
         return int(self.E.size)
+
+
+def material_fields(lines: Lines, chords, delta_m, beta_m, e_ref_keV):
+    """Per-line phase and attenuation line integrals of an object made of
+    several materials (orc_forward_fields): ``chords`` [n_mat][ny][nx] are the
+    chord lengths (metres) through each material, whose indices at the
+    reference energy are ``delta_m``, ``beta_m``; at line s they scale as
+    (e_ref / E_s)^2 and (e_ref / E_s)^4 (the away-from-edge scalings of the
+    spectra here), mu_{m,s} = 2 k_s beta_{m,s}.  Returns (Phi, A), each
+    [n_lines][ny][nx]."""
+    chords = np.asarray(chords, dtype=np.float64)
+    _, _, k, _, _ = lines.params()
+    phi0 = np.tensordot(np.asarray(delta_m, dtype=np.float64), chords, axes=1)
+    bet0 = np.tensordot(np.asarray(beta_m, dtype=np.float64), chords, axes=1)
+    r = e_ref_keV / lines.E
+    Phi = np.stack([phi0 * r[s] ** 2 for s in range(lines.n)])
+    A = np.stack([2.0 * k[s] * bet0 * r[s] ** 4 for s in range(lines.n)])
+    return Phi, A
+
+
+def forward_fields(lines: Lines, Phi, A, per_line=False):
+    """Non-local forward from per-line phase and attenuation line integrals
+    (orc_forward_fields); the energies, delta and beta of ``lines`` are not
+    used, only its weights, L and pixel."""
+    Phi, A = _c(Phi), _c(A)
+    ns, ny, nx = Phi.shape
+    assert A.shape == Phi.shape and ns == lines.n
+    P = np.empty((ny, nx))
+    Ps = np.empty((ns, ny, nx)) if per_line else None
+    dropped = np.zeros(ns) if per_line else None
+    st = _load().orc_forward_fields(ny, nx, lines.p, lines.L, ns, _p(lines.w), _p(Phi), _p(A),
+                                    _p(P), _p(Ps), _p(dropped))
+    _check(st, "forward_fields")
+    return (P, Ps, dropped) if per_line else P
 
 
 def forward_x(xs: XSpec, T, per_line=False):
