@@ -849,6 +849,62 @@ def _oracle_sample(n_it: int, D) -> float:
     return time.perf_counter() - t0
 
 
+UNEVEN_SIZES = [(1024, 1024), (2048, 1536), (2048, 2048), (3072, 2048)]   # (nx, ny)
+
+
+def _oracle_other_configs(band: int = 128) -> dict:
+    """Single-threaded oracle timings of the other configurations, on bounded
+    samples: the 256^2 sphere solve in full (20 iterations); one iteration of
+    the 8-line 2048^2 solve on a band of rows, scaled by pixel count and to 50
+    iterations; one iteration of the 4-line solve of each uneven size on a band,
+    scaled by pixel count to a 2048^2-equivalent iteration of the uniform size
+    mix.  Every iteration of a solve does the same work, so the scaling is
+    linear."""
+    from oracle import oracle as O
+    from paper_2601_22793_gb300 import phantoms as ph
+    out = {}
+    wl, tau = ph.spheres_mono_256()
+    ln = O.Lines(wl.energy_keV, wl.delta, wl.beta, wl.weights, wl.L, wl.pixel)
+    D = ph.poisson(O.forward(ln, tau), wl.photons, 3)
+    t0 = time.perf_counter()
+    O.solve(ln, D, n_iter=wl.n_iter, omega=wl.omega)
+    t = time.perf_counter() - t0
+    out["spheres_mono_256"] = {"n_iter": wl.n_iter, "s_per_solve": round(t, 4),
+                               "projections_per_s": round(1.0 / t, 4), "cores": 1,
+                               "sample": "the full solve"}
+    wp, ells, angles = ph.ellipsoids_poly()
+    y0 = wp.ny // 2 - band // 2
+    tp = ph.project_ellipsoids(ells, wp.ny, wp.nx, wp.pixel, angles[0])[y0:y0 + band]
+    lp = O.Lines(wp.energy_keV, wp.delta, wp.beta, wp.weights, wp.L, wp.pixel)
+    Dp = ph.poisson(O.forward(lp, tp), wp.photons, 9)
+    t0 = time.perf_counter()
+    O.solve(lp, Dp, n_iter=1, omega=wp.omega)
+    it_full = (time.perf_counter() - t0) * wp.ny / band
+    out["ellipsoids_poly_2048x8"] = {
+        "n_lines": int(np.size(wp.energy_keV)), "s_per_iteration": round(it_full, 3),
+        "projections_per_s": round(1.0 / (it_full * wp.n_iter), 6), "cores": 1,
+        "sample": f"1 iteration on rows {y0}..{y0 + band - 1} of the 2048x2048 projection, "
+                  f"scaled by pixel count and to {wp.n_iter} iterations"}
+    Es, d, b, w = ph.spectrum(4, 60.0, 160.0, 95.0, 30.0, ph.BONE[0], ph.BONE[1], 80.0, 4000)
+    l4 = O.Lines(Es, d, b, w, L=30.0, pixel=20e-6)
+    per_px = []
+    for j, (nx, ny) in enumerate(UNEVEN_SIZES):
+        ells4 = ph.random_ellipsoids(band, nx, 20, 3.0, 40.0, margin=10.0, seed=4400 + j)
+        t4 = ph.project_ellipsoids(ells4, band, nx, 20e-6)
+        D4 = ph.poisson(O.forward(l4, t4), 1e4, 4500 + j)
+        t0 = time.perf_counter()
+        O.solve(l4, D4, n_iter=1, omega=0.4)
+        per_px.append((time.perf_counter() - t0) / (band * nx))
+    it_eq = float(np.mean(per_px)) * REF_PIX
+    out["uneven_4line"] = {
+        "sizes_nx_ny": [list(sz) for sz in UNEVEN_SIZES], "n_lines": 4,
+        "s_per_2048sq_equiv_iteration": round(it_eq, 3),
+        "equiv_2048sq_iterations_per_s": round(1.0 / it_eq, 4), "cores": 1,
+        "sample": f"1 iteration on a {band}-row band of each size, scaled by pixel count "
+                  f"(uniform size mix)"}
+    return out
+
+
 def cpu_baseline(n_it: int):
     """The FP64 oracle as it stands on the host cores, on a bounded sample of
     the headline workload: the first n_it of its 50 iterations, time scaled by
@@ -874,7 +930,8 @@ def cpu_baseline(n_it: int):
                      f"full solve; {ncores} independent solves, one per core in separate "
                      f"processes ({tn:.1f} s wall)",
            "single_thread": {"value": round(single, 6), "unit": UNIT, "cores": 1,
-                             "sample": f"{n_it} of {wl.n_iter} iterations ({t1:.1f} s), scaled"}}
+                             "sample": f"{n_it} of {wl.n_iter} iterations ({t1:.1f} s), scaled"},
+           "other_configs": _oracle_other_configs()}
     return rec, D
 
 

@@ -54,6 +54,10 @@ def test_cpu_baseline_leg_times_one_and_all_cores_and_returns_the_data():
     assert rec["kind"] == "oracle" and rec["cores"] == (os.cpu_count() or 1)
     assert rec["value"] > 0 and rec["single_thread"]["value"] > 0 and rec["cpu_model"]
     assert D.shape == (2048, 2048) and D.dtype.name == "float32"
+    oc = rec["other_configs"]   # the other configurations' oracle timings
+    assert oc["spheres_mono_256"]["projections_per_s"] > 0
+    assert oc["ellipsoids_poly_2048x8"]["s_per_iteration"] > 0
+    assert oc["uneven_4line"]["equiv_2048sq_iterations_per_s"] > 0
     # the reference arm solves the same data
     _, _, _, D2 = bench._oracle_workload()
     assert (D == D2).all()
