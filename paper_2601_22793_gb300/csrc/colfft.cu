@@ -317,17 +317,17 @@ EprColLaunch epr_col_config(const EprConsts& C, int cw_hint)
 
 // The column passes that move their tile by bulk tensor copies.
 // Column tile width of the bulk-copy pass: the plain pass's, except for
-// 8192-row columns (oversampled internal grids), whose bulk-copy tile is two
-// columns wide (a 128 KB tile, one 1024-thread block per SM) where the plain
-// pass takes one.
+// 4096- and 8192-row columns (oversampled internal grids), whose bulk-copy
+// tile is two columns wide (64 KB and 512 threads, or 128 KB and 1024
+// threads, radix-16 stages) where the plain pass takes one.
 static int col_tma_cw(const EprConsts& C, const EprColLaunch& L)
 {
-    return C.ny == 8192 ? 2 : L.CW;
+    return (C.ny == 4096 || C.ny == 8192) ? 2 : L.CW;
 }
 
 static bool col_tma_case(const EprConsts& C, const EprColLaunch& L)
 {
-    if (C.ny == 8192) return L.EPT == 8 && C.half % 2 == 0;
+    if (C.ny == 4096 || C.ny == 8192) return L.EPT == 8 && C.half % 2 == 0;
     if (L.EPT != 8) return false;
     return (L.CW == 4 && (C.ny == 256 || C.ny == 512 || C.ny == 1024)) ||
            (L.CW == 2 && (C.ny == 1536 || C.ny == 2048));
@@ -336,7 +336,7 @@ static bool col_tma_case(const EprConsts& C, const EprColLaunch& L)
 // elements per thread of the bulk-copy pass: 16 for 2048-point columns (256
 // threads and 37 KB per block, four blocks per SM, so the 512 blocks of a
 // 2048^2 projection are resident at once), 8 otherwise
-static int col_tma_ept(const EprConsts& C) { return (C.ny == 2048 || C.ny == 8192) ? 16 : 8; }
+static int col_tma_ept(const EprConsts& C) { return (C.ny == 2048 || C.ny >= 4096) ? 16 : 8; }
 
 static size_t col_tma_smem(const EprConsts& C, const EprColLaunch& L)
 {
@@ -428,6 +428,13 @@ cudaError_t epr_launch_col(const EprConsts& C, const EprWork& W, int line0, int 
                                   dim3(8192 * 2 / 16), smem, stream, C, A, map);
             done = true;
         }
+        if (!done && C.ny == 4096) {   // 2 columns per block, radix 16 (16, 16, 16), 2 blocks per SM
+            A.CW = 2;
+            A.lgCW = 1;
+            e = epr_launch_kernel(pdl, k_col_tma<4096, 2, 16, 16, 2>, dim3(C.half / 2, nl, batch),
+                                  dim3(4096 * 2 / 16), smem, stream, C, A, map);
+            done = true;
+        }
         EPR_COL_TMA_CASE(2048, 2, 16)
 #undef EPR_COL_TMA_CASE
     }
@@ -504,6 +511,7 @@ cudaError_t epr_col_init()
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 16, 16>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<2048, 2, 16, 16, 5>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<8192, 2, 16, 16>);
+    if (e == cudaSuccess) e = epr_allow_max_smem(k_col_tma<4096, 2, 16, 16, 2>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<1536, 2, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<3072, 1, 8>);
     if (e == cudaSuccess) e = epr_allow_max_smem(k_col_ct<4096, 1, 8>);

@@ -550,11 +550,11 @@ __device__ __forceinline__ void stage_turn(float2* buf, const float2* __restrict
 // buf (layout PAD) and synchronises; the caller has synchronised already if
 // buf aliases data that other threads still read.  Stages 1.. follow as
 // fft_ct<..., 1>.
-template <class PAD, int DIR, int N, int EPT, int SJ>
+template <class PAD, int DIR, int N, int EPT, int SJ, int MAXR = 8>
 __device__ __forceinline__ void stage0_regs(float2 (&v)[EPT], float2* buf, int tid)
 {
-    constexpr int R = ct_radix(N, 0);
-    static_assert(R == EPT && ct_n_stages(N) > 1, "operands of the first stage in registers");
+    constexpr int R = ct_radix(N, 0, MAXR);
+    static_assert(R == EPT && ct_n_stages(N, MAXR) > 1, "operands of the first stage in registers");
     dft<R, DIR>(v);
     const int dst = tid * R * SJ;   // (j / Ns) Ns R + (j mod Ns) with Ns = 1, j = tid
 #pragma unroll

@@ -446,11 +446,15 @@ __device__ __forceinline__ int row_of(int e) { return RP == 1 ? 0 : (int)((unsig
 // in a batch of projections, worse for one (the autotuner decides).
 // XT: an x-dependent spectrum, the shift constant of each object column from
 // the plan's table.
-template <int NX, int RP, bool POLY, bool GATHER, bool OCC6 = false, bool XT = false>
-__global__ void __launch_bounds__(NX * RP / kEPT, OCC6 ? 6 : (NX * RP / kEPT == 256 && !POLY) ? 5 : (65536 / 64) / (NX * RP / kEPT))
+template <int NX, int RP, bool POLY, bool GATHER, bool OCC6 = false, bool XT = false, int EPT = kEPT>
+__global__ void __launch_bounds__(NX * RP / EPT, OCC6 ? 6 : (NX * RP / EPT == 256 && !POLY) ? 5 : (65536 / 64) / (NX * RP / EPT))
 k_row_fwd_mono(const EprConsts C, const RowArgs A)
 {
-    constexpr int T = NX * RP / kEPT;
+    constexpr int T = NX * RP / EPT;
+    constexpr int MAXR = EPT >= 16 ? 16 : 8;   // radix-16 stages with 16 elements per thread
+    // 16 elements per thread (8192-point rows): the thickness is read through
+    // L1 instead of staged, which leaves room for two blocks per SM
+    constexpr bool kStageT = EPT == kEPT;
     constexpr int SM = NX + kPad;
     constexpr int HALF = NX / 2;
     constexpr int LGRP = ct_lg<NX>(RP);
@@ -463,7 +467,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     const size_t pb = (size_t)b * npix;
     const int yb = blockIdx.x * RP * 2;
     float* Ts = reinterpret_cast<float*>(zs);   // aliases the FFT rows (see above)
-    if constexpr (GATHER) {   // T is not written by the predecessor: fetch it before the wait
+    if constexpr (GATHER && kStageT) {   // T is not written by the predecessor: fetch it before the wait
         const float* Tb = A.T + pb;
         constexpr int Q4 = NX / 4;
         constexpr int NROWS = 2 * RP + 2;
@@ -492,9 +496,9 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
     const float* Rb = POLY ? A.Ps + (pb * C.ns + (size_t)(A.line0 + sl) * npix) : A.P + pb;
     const float* Rt = A.P + pb;   // D - P, for |D - P|^2
     float ra = 0.f;
-    float2 vk[kEPT];   // the packed row pair values, stored once the thickness is dead
+    float2 vk[EPT];   // the packed row pair values, stored once the thickness is dead
 #pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
+    for (int k = 0; k < EPT; ++k) {
         const int e = tid + k * T;
         const int m = row_of<NX, RP>(e), x = e - m * NX;
         const int y0 = yb + 2 * m;
@@ -505,13 +509,13 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
             if constexpr (!GATHER) {   // identity back-transport of the local closure
                 v[r0] = __ldg(Rb + (size_t)y * NX + x);
             } else {
-            const float* tr = Ts + (2 * m + r0 + 1) * NX;
-            const float t = tr[x];
+            const float* tr = kStageT ? Ts + (2 * m + r0 + 1) * NX : A.T + pb + (size_t)y * NX;
+            const float t = kStageT ? tr[x] : __ldg(tr + x);
             // edges (one-sided differences): with one row pair per block only
             // the first and last element of a thread can be an edge column,
             // and only the first (last) row of the pair the top (bottom) row
             const bool xlo = (RP > 1 || k == 0) && x == 0;
-            const bool xhi = (RP > 1 || k == kEPT - 1) && x == NX - 1;
+            const bool xhi = (RP > 1 || k == EPT - 1) && x == NX - 1;
             const bool ylo = r0 == 0 && y == 0, yhi = r0 == 1 && y == ny - 1;
             float gx, gy;
             if (xlo) gx = tr[1] - t;
@@ -519,7 +523,7 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
             else gx = 0.5f * (tr[x + 1] - tr[x - 1]);
             if (ylo) gy = tr[NX + x] - t;
             else if (yhi) gy = t - tr[x - NX];
-            else gy = 0.5f * (tr[NX + x] - tr[x - NX]);
+            else gy = 0.5f * (tr[NX + x] - tr[x - NX]);   // rows y - 1 and y + 1 exist here
             const float lim = 2.f * (float)(NX > ny ? NX : ny);
             const float csx = XT ? xt_get(C, EPR_XT_C, A.line0 + sl, x) : cs;
             const float ux = fminf(fmaxf(csx * gx, -lim), lim);
@@ -550,20 +554,20 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
         }
         vk[k] = make_float2(v[0], v[1]);
     }
-    if constexpr (GATHER) __syncthreads();   // every thickness read is done
-    if constexpr (RP == 1 && eprfft::ct_radix(NX, 0) == kEPT) {
+    if constexpr (GATHER && kStageT) __syncthreads();   // every thickness read is done
+    if constexpr (RP == 1 && eprfft::ct_radix(NX, 0, MAXR) == EPT) {
         // one row pair: vk[k] = element tid + k T, the first stage's operands
-        eprfft::stage0_regs<PR, -1, NX, kEPT, 1>(vk, zs, tid);
-        eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM, 1>(zs, A.tw, tid);
+        eprfft::stage0_regs<PR, -1, NX, EPT, 1, MAXR>(vk, zs, tid);
+        eprfft::fft_ct<PR, -1, NX, EPT, LGRP, 1, SM, 1, MAXR>(zs, A.tw, tid);
     } else {
 #pragma unroll
-        for (int k = 0; k < kEPT; ++k) {
+        for (int k = 0; k < EPT; ++k) {
             const int e = tid + k * T;
             const int m = row_of<NX, RP>(e), x = e - m * NX;
             zs[PR::idx(m * SM + x)] = vk[k];
         }
         __syncthreads();
-        eprfft::fft_ct<PR, -1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid);
+        eprfft::fft_ct<PR, -1, NX, EPT, LGRP, 1, SM, 0, MAXR>(zs, A.tw, tid);
     }
     epr_grid_release();
     float2* Sb = A.S + ((size_t)b * A.nl + sl) * (size_t)ny * HALF;
@@ -598,18 +602,20 @@ k_row_fwd_mono(const EprConsts C, const RowArgs A)
 // T' = T - w ln(I'/I) from the staged thickness rows, stored, with the kappa
 // partial sums kept in the functor (its call sites are inlined, so they stay
 // in registers).
-template <int NX, int SM, int RP, bool XT>
+template <int NX, int SM, int RP, bool XT, bool STAGED = true>
 struct InvUpdate1 {
     const EprConsts& C;
-    const float* Tsh;      // [2 RP][NX] thickness rows of the block
-    float* out;            // T at the block's first row
+    const float* Tsh;      // [2 RP][NX] thickness rows of the block (STAGED), else unused
+    float* out;            // T at the block's first row (read there when not STAGED)
     float mus, w, om_f, omega, eps;
     mutable float da, db;
     __device__ __forceinline__ float2 operator()(float2 h, int e) const
     {
         const int m = RP == 1 ? 0 : e / SM;
         const int x = e - m * SM;
-        const float t0 = Tsh[(2 * m) * NX + x], t1 = Tsh[(2 * m + 1) * NX + x];
+        float* o = out + (size_t)(2 * m) * NX + x;
+        const float t0 = STAGED ? Tsh[(2 * m) * NX + x] : o[0];
+        const float t1 = STAGED ? Tsh[(2 * m + 1) * NX + x] : o[NX];
         float wx = w, omx = om_f, mux = mus;
         if constexpr (XT) {
             wx = xt_get(C, EPR_XT_WPROJ, 0, x);
@@ -619,7 +625,6 @@ struct InvUpdate1 {
         const float l0 = wx * log_ratio(t0, h.x, omx, mux, eps);
         const float l1 = wx * log_ratio(t1, h.y, omx, mux, eps);
         const float n0 = t0 - l0, n1 = t1 - l1;
-        float* o = out + (size_t)(2 * m) * NX + x;
         o[0] = n0;
         o[NX] = n1;
         da += l0 * l0 + l1 * l1;
@@ -629,12 +634,16 @@ struct InvUpdate1 {
 };
 
 // five 256-thread blocks per SM (48 registers): its shared memory is the FFT
-// rows and 2 RP thickness rows only (row_inv_mono_smem)
-template <int NX, int RP, bool OCC6 = false, bool XT = false>
-__global__ void __launch_bounds__(NX * RP / kEPT, OCC6 ? 6 : NX * RP / kEPT == 256 ? 5 : (65536 / 64) / (NX * RP / kEPT))
+// rows and 2 RP thickness rows only (row_inv_mono_smem).  EPT = 16 (8192-point
+// rows): radix-16 stages, and the update reads T through L1 instead of staging
+// it, so two 512-thread blocks fit on an SM.
+template <int NX, int RP, bool OCC6 = false, bool XT = false, int EPT = kEPT>
+__global__ void __launch_bounds__(NX * RP / EPT, OCC6 ? 6 : NX * RP / EPT == 256 ? 5 : (65536 / 64) / (NX * RP / EPT))
 k_row_inv_mono(const EprConsts C, const RowArgs A)
 {
-    constexpr int T = NX * RP / kEPT;
+    constexpr int T = NX * RP / EPT;
+    constexpr int MAXR = EPT >= 16 ? 16 : 8;
+    constexpr bool kStageT = EPT == kEPT;
     constexpr int SM = NX + kPad;
     constexpr int HALF = NX / 2;
     constexpr int LGRP = ct_lg<NX>(RP);
@@ -646,7 +655,7 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
     const int yb = blockIdx.x * RP * 2;
     // rows yb .. yb + 2RP - 1 of T, copied while the spectrum is transformed
     float* Tsh = reinterpret_cast<float*>(zs + ((PR::len(RP * SM) + 1) & ~1));
-    {
+    if constexpr (kStageT) {
         constexpr int Q4 = 2 * RP * NX / 4;
         const float4* src = reinterpret_cast<const float4*>(A.Out + pb + (size_t)yb * NX);
 #pragma unroll
@@ -679,14 +688,15 @@ k_row_inv_mono(const EprConsts C, const RowArgs A)
         }
     }
     __syncthreads();
-    constexpr int NST = eprfft::ct_n_stages(NX);
-    eprfft::fft_ct_stages<PR, +1, NX, kEPT, LGRP, 1, SM, 0, NST - 1>(zs, A.tw, tid);
+    constexpr int NST = eprfft::ct_n_stages(NX, MAXR);
+    eprfft::fft_ct_stages<PR, +1, NX, EPT, LGRP, 1, SM, 0, NST - 1, MAXR>(zs, A.tw, tid);
     epr_grid_release();
     cp_async_wait_all();   // the thickness rows: visible to all after the last stage's barrier
     // the last stage hands each result to the update (no store, no barrier)
-    const InvUpdate1<NX, SM, RP, XT> up{C, Tsh, A.Out + pb + (size_t)yb * NX, C.mu[0], C.wproj[0],
-                                        A.omega / C.f[0], A.omega, A.eps, 0.f, 0.f};
-    eprfft::fft_ct_last<PR, false, false, PR, +1, NX, kEPT, LGRP, 1, SM>(zs, A.tw, tid, up);
+    const InvUpdate1<NX, SM, RP, XT, kStageT> up{C, Tsh, A.Out + pb + (size_t)yb * NX, C.mu[0],
+                                                 C.wproj[0], A.omega / C.f[0], A.omega, A.eps,
+                                                 0.f, 0.f};
+    eprfft::fft_ct_last<PR, false, false, PR, +1, NX, EPT, LGRP, 1, SM, MAXR>(zs, A.tw, tid, up);
     float da = up.da, db = up.db;
     block_sum2(da, db, red);   // kappa partials, finalised by the next forward pass
     store_partials(A.part_a + (size_t)b * A.max_blocks, A.part_b + (size_t)b * A.max_blocks, da, db);
@@ -828,6 +838,13 @@ size_t row_fwd_mono_smem(int nx, int rp)
     return fft > ts ? fft : ts;
 }
 
+// dynamic shared memory of the FFT rows alone (the 16-elements-per-thread
+// kernels, which stage no thickness rows)
+size_t row_fft_smem(int nx, int rp)
+{
+    return (size_t)((PR::len(rp * (nx + kPad)) + 1) & ~1) * sizeof(float2);
+}
+
 // dynamic shared memory of k_row_inv_mono: FFT rows, T rows
 size_t row_inv_mono_smem(int nx, int rp)
 {
@@ -917,6 +934,15 @@ bool launch_mono_ct(int nx, int rp, dim3 grid, size_t smem, cudaStream_t stream,
     EPR_MONO_CASE(2048, 1)
     EPR_MONO_CASE(3072, 1)
     EPR_MONO_CASE(4096, 1)
+    if (nx == 8192 && rp == 1 && !poly && (!FWD || GATHER)) {   // 16 per thread, two blocks per SM
+        if (FWD)
+            err = epr_launch_kernel(C.pdl != 0, k_row_fwd_mono<8192, 1, false, true, false, false, 16>,
+                                    grid, dim3(512), row_fft_smem(8192, 1), stream, C, A);
+        else
+            err = epr_launch_kernel(C.pdl != 0, k_row_inv_mono<8192, 1, false, false, 16>, grid,
+                                    dim3(512), row_fft_smem(8192, 1), stream, C, A);
+        return true;
+    }
     EPR_MONO_CASE(8192, 1)
 #undef EPR_MONO_CASE
     return false;
@@ -954,6 +980,8 @@ cudaError_t init_mono_ct()
     EPR_MONO_INIT(3072, 1)
     EPR_MONO_INIT(4096, 1)
     EPR_MONO_INIT(8192, 1)
+    if (e == cudaSuccess) e = allow(k_row_fwd_mono<8192, 1, false, true, false, false, 16>);
+    if (e == cudaSuccess) e = allow(k_row_inv_mono<8192, 1, false, false, 16>);
 #undef EPR_MONO_INIT
     return e;
 }

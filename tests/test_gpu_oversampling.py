@@ -50,7 +50,10 @@ def _data(oracle, nyd, nxd, os_, n_lines, model, seed, L=10.0):
 @pytest.mark.parametrize("nyd,nxd,os_,n_lines,model,det,L", [
     (48, 64, 2, 1, 0, False, 10.0), (48, 64, 2, 1, 0, True, 10.0), (32, 32, 4, 2, 0, False, 10.0),
     (64, 48, 2, 2, 2, False, 4.0), (32, 48, 2, 1, 1, False, 10.0),
-    (16, 2048, 4, 1, 0, False, 10.0), (2048, 16, 4, 2, 0, False, 10.0)])
+    (16, 2048, 4, 1, 0, False, 10.0), (2048, 16, 4, 2, 0, False, 10.0),
+    # 4096 internal rows: the bulk-copy column pass of two 4096-point columns
+    (1024, 16, 4, 1, 0, False, 10.0), (2048, 24, 2, 2, 0, False, 10.0),
+    (2048, 16, 2, 1, 2, False, 4.0)])
 def test_oversampled_solve_vs_oracle(torch, oracle, nyd, nxd, os_, n_lines, model, det, L):
     from paper_2601_22793_gb300 import epr as E
     D, _ = _data(oracle, nyd, nxd, os_, n_lines, model, 80 + nyd + os_, L)
