@@ -515,7 +515,9 @@ epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int bat
     p->tuned = true;
     const bool resid = p->C.ns == 1 && !p->C.det && p->C.os == 1 && !p->C.xt;
     const int tiles[4][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}};
-    const int reaches[3] = {3, 4, 6};
+    // the compile-time reaches, and the plan's own when it is none of them
+    const int own = p->C.smax;
+    const int reaches[4] = {3, 4, 6, (own == 3 || own == 4 || own == 6) ? 0 : own};
     const EprConsts saved = p->C;
     const int sTH = p->splat_TH, sTW = p->splat_TW;
     int optin = 0;
@@ -527,6 +529,7 @@ epr_status autotune_splat(epr_plan_s* p, const float* D, const float* T, int bat
     EPR_TRY(cudaEventCreate(&e1));
     for (const auto& t : tiles) {
         for (int r : reaches) for (int occ6 = 0; occ6 <= 1; ++occ6) {
+            if (r == 0) continue;
             if (occ6 && !(resid && epr_splat_has_occ6(t[0], t[1], r))) continue;
             p->C.smax = r;
             if ((size_t)p->C.ns * t[0] * t[1] * (p->C.det ? 8 : 4) > 65536) continue;
