@@ -259,10 +259,13 @@ def test_solve_poly_compile_time_row_kernels(torch, E, oracle, ny, nx, det):
 
 
 @pytest.mark.parametrize("ny,nx,n_lines", [(96, 1536, 1), (1536, 96, 1), (64, 3072, 2),
-                                           (3072, 64, 2)])
+                                           (3072, 64, 2), (32, 4096, 1), (32, 4096, 2),
+                                           (4096, 32, 1), (4096, 48, 2)])
 def test_solve_three_smooth_sizes(torch, E, oracle, ny, nx, n_lines):
     """Row and column lengths 3 * 2^k on the compile-time kernels (radix-3
-    stages; the 1536-row column pass moves its tile by TMA)."""
+    stages; the 1536-row column pass moves its tile by TMA), and the largest
+    detector side, 4096: the compile-time 4096-point row kernels and the
+    bulk-copy column pass of two 4096-point columns."""
     wl, T32 = small_poly(ny=ny, nx=nx, n_lines=n_lines, seed=13)
     ln = lines_of(oracle, wl)
     D = ph.poisson(oracle.forward(ln, T32.astype(np.float64)), wl.photons, 7).astype(np.float32)
